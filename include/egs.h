@@ -1,0 +1,177 @@
+/*
+ * egs.h - C ABI of the GB300 exact Gaussian log-likelihood library (libegs.so).
+ *
+ * The library evaluates Eq. 1 of Abdulah et al., "ExaGeoStat: A High
+ * Performance Unified Software for Geostatistics on Manycore Systems"
+ * (arXiv:1708.02835), Section 2:
+ *
+ *     l(theta) = -n/2 log(2 pi) - 1/2 log|Sigma(theta)| - 1/2 Z^T Sigma(theta)^-1 Z
+ *
+ * with Sigma_ij = C(||s_i - s_j||; theta) from the Matern covariance, Eq. 2
+ * (Section 2.2):
+ *
+ *     C(r; theta) = theta1 / (2^(theta3 - 1) Gamma(theta3)) (r/theta2)^theta3 K_theta3(r/theta2)
+ *
+ * following Algorithm 2 (Section 5.4): generate Sigma, factor Sigma = L L^T by
+ * tile Cholesky, solve L y = Z, reduce log|Sigma| = 2 sum_i log L_ii and
+ * y^T y, and assemble l.  Every step runs in the library's own sm_103a CUDA
+ * kernels.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Locations are passed as one array of 2n doubles: x[0..n) then y[0..n).
+ * - theta is a host array of 3 doubles (theta1 variance, theta2 range,
+ *   theta3 smoothness); each must be finite and > 0 (Section 2.2), otherwise
+ *   EGS_ERR_ARG.
+ * - n >= 1.  tile (the Cholesky tile size b) is a multiple of 64 in [64, 1024];
+ *   0 selects the library default for n and precision.
+ * - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Device buffers passed in are borrowed for the duration of the
+ *   call; the library keeps no pointer to them afterwards.
+ * - Errors are return codes; nothing aborts, traps or prints.  A thread-local
+ *   message is available from egs_last_error().  When the matrix is not
+ *   positive definite the call returns EGS_ERR_NOT_PD, the log-likelihood is
+ *   NaN and egs_info.fail_index holds the first failing row.
+ *
+ * Tile layout ("lower tiles")
+ * ---------------------------
+ * T = ceil(n / b).  Only tiles (i, j) with i >= j are stored, tile (i, j) at
+ * position i (i + 1) / 2 + j, each tile b x b contiguous and row-major
+ * (element (r, c) at r * b + c).  Rows and columns at or beyond n are padding:
+ * zero, except padded diagonal entries, which are one, so the padded matrix
+ * is positive definite with the same log-determinant and quadratic form.
+ * In EGS_FP64 every tile is double.  (Mixed-precision layouts are described
+ * at egs_tiles_bytes.)
+ */
+#ifndef EGS_H
+#define EGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EGS_OK = 0,
+    EGS_ERR_ARG = 1,           /* invalid argument (sizes, theta, pointers) */
+    EGS_ERR_NOT_PD = 2,        /* Cholesky met a pivot <= 0 (or NaN) */
+    EGS_ERR_OOM = 3,           /* device allocation failed or budget exceeded */
+    EGS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    EGS_ERR_TIMEOUT = 5,       /* a bounded wait expired */
+    EGS_ERR_BUSY = 6,          /* resource busy (serving: queue full) */
+    EGS_ERR_UNIMPLEMENTED = 7  /* feature not built */
+} egs_status;
+
+typedef enum {
+    EGS_FP64 = 0,     /* everything in double */
+    EGS_MIX_FP32 = 1, /* FP64 band; off-band tiles FP32, updates in FP32 */
+    EGS_MIX_TF32 = 2, /* FP64 band; off-band tiles FP32, updates on tcgen05 TF32 */
+    EGS_MIX_BF16 = 3  /* FP64 band; off-band operands BF16, FP32 accumulation */
+} egs_precision;
+
+/* Per-call diagnostics (all fields written by the call when non-NULL). */
+typedef struct {
+    double loglik;        /* l(theta), NaN on failure */
+    double logdet;        /* log|Sigma| = 2 sum_i log L_ii */
+    double quad;          /* Z^T Sigma^-1 Z */
+    int64_t fail_index;   /* first row whose pivot failed, or -1 */
+    int64_t fail_tile;    /* fail_index / tile, or -1 */
+    int32_t tile;         /* tile size used */
+    int32_t band;         /* FP64 band width in tiles (mixed modes) */
+    int32_t launches;     /* kernels this call launched */
+    int32_t refine_steps; /* FP64 refinement steps taken (mixed modes) */
+    double quad_unrefined;/* mixed modes: Z^T Sigma^-1 Z before refinement */
+    /* Device times in ms (CUDA events on the call's stream; zero unless
+     * egs_opts.timing is set).  timing = 1: per phase; timing = 2: also the
+     * summed duration of each kernel class (one event pair per launch). */
+    double ms_generate;   /* Sigma generation */
+    double ms_factor;     /* tile Cholesky */
+    double ms_solve;      /* solve, refinement and reductions */
+    double ms_total;      /* whole evaluation */
+    double ms_potrf;      /* timing = 2: diagonal-tile POTRF kernels */
+    double ms_trsm;       /* timing = 2: panel TRSM kernels */
+    double ms_update;     /* timing = 2: SYRK/GEMM trailing-update kernels */
+    double ms_trsv;       /* timing = 2: solve kernels */
+} egs_info;
+
+/* Optional knobs for egs_loglik_ex.  Zero-initialise for defaults. */
+typedef struct {
+    int32_t tile;          /* 0 = default */
+    int32_t band;          /* FP64 band width in tiles for mixed modes; 0 = 2 */
+    int32_t refine;        /* mixed modes: FP64 refinement steps (0 = default 1, -1 = none) */
+    int32_t timing;        /* nonzero: record per-phase CUDA events into egs_info */
+    void *workspace;       /* caller-owned device workspace, or NULL (library allocates) */
+    size_t workspace_bytes;
+} egs_opts;
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *egs_last_error(void);
+
+/* Library version string. */
+const char *egs_version(void);
+
+/* Default tile size for n in the given precision. */
+int32_t egs_default_tile(int64_t n, egs_precision p);
+
+/* Bytes of the lower-tile matrix for (n, tile, p, band).  EGS_FP64: all
+ * T (T + 1) / 2 tiles are double.  Returns 0 for invalid arguments. */
+size_t egs_tiles_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band);
+
+/* Bytes of device workspace egs_loglik_ex needs for (n, tile, p, band),
+ * including the tile matrix.  Returns 0 for invalid arguments. */
+size_t egs_loglik_workspace_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band);
+
+/*
+ * egs_matern_tiles - generate Sigma(theta) (Eq. 2; Algorithm 2, genCovMatrix)
+ * into the lower-tile layout.
+ *   locs   device, 2n doubles (x then y)
+ *   tiles  device, egs_tiles_bytes(n, tile, p, band) bytes, written
+ * Entries with r = 0 take the limit C(0) = theta1.  Asynchronous on stream.
+ * Only EGS_FP64 is accepted here.
+ */
+egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3], int32_t tile,
+                            egs_precision p, int32_t band, void *tiles, void *stream);
+
+/*
+ * egs_potrf_tiles - tile Cholesky Sigma = L L^T in place (Algorithm 2,
+ * dpotrf; the right-looking tile algorithm of Section 4.2: POTRF on the
+ * diagonal tile, TRSM on the panel, SYRK/GEMM on the trailing tiles).
+ *   tiles       device, lower tiles of Sigma in EGS_FP64 layout; on return L
+ *   fail_index  host; first failing row or -1.  The call synchronises stream.
+ */
+egs_status egs_potrf_tiles(void *tiles, int64_t n, int32_t tile, int64_t *fail_index, void *stream);
+
+/*
+ * egs_trsv_tiles - forward solve L y = Z (Algorithm 2, dtrsm; Section 5.4
+ * states it as L Z_new = Z_old) with the log-determinant (2 sum_i log L_ii,
+ * Section 5.1) and the dot product y^T y (Algorithm 2, computeDotProduct).
+ *   tiles  device, L in EGS_FP64 lower-tile layout
+ *   z      device, n doubles;  y  device, n doubles (may alias z)
+ *   logdet, quad  host; the call synchronises stream.
+ */
+egs_status egs_trsv_tiles(const void *tiles, int64_t n, int32_t tile, const double *z, double *y,
+                          double *logdet, double *quad, void *stream);
+
+/*
+ * egs_loglik - one evaluation of Eq. 1 (Algorithm 2) at theta.
+ *   locs  2n doubles (x then y), device or host memory
+ *   z     n doubles, device or host memory
+ *   out_loglik  host; info nullable.
+ * Host inputs are copied to the device inside the call.  Workspace comes
+ * from a stream-ordered device pool.  Synchronises stream before returning.
+ */
+egs_status egs_loglik(const double *locs, const double *z, const double theta[3], int64_t n,
+                      egs_precision p, double *out_loglik, egs_info *info, void *stream);
+
+/* egs_loglik with options (tile, band, refinement, caller workspace). */
+egs_status egs_loglik_ex(const double *locs, const double *z, const double theta[3], int64_t n,
+                         egs_precision p, const egs_opts *opts, double *out_loglik, egs_info *info,
+                         void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EGS_H */

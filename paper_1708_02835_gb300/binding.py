@@ -1,0 +1,197 @@
+"""ctypes binding of libegs.so with the same names as the C ABI.
+
+Tensors are torch CUDA tensors (device pointers are passed as-is) or, where
+the C ABI accepts host memory, NumPy arrays / CPU tensors.  The stream is
+torch's current CUDA stream unless one is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+EGS_OK, EGS_ERR_ARG, EGS_ERR_NOT_PD, EGS_ERR_OOM, EGS_ERR_CUDA, EGS_ERR_TIMEOUT, EGS_ERR_BUSY, \
+    EGS_ERR_UNIMPLEMENTED = range(8)
+EGS_FP64, EGS_MIX_FP32, EGS_MIX_TF32, EGS_MIX_BF16 = range(4)
+PRECISIONS = {"fp64": EGS_FP64, "fp32": EGS_MIX_FP32, "tf32": EGS_MIX_TF32, "bf16": EGS_MIX_BF16}
+
+_STATUS_NAMES = {0: "EGS_OK", 1: "EGS_ERR_ARG", 2: "EGS_ERR_NOT_PD", 3: "EGS_ERR_OOM", 4: "EGS_ERR_CUDA",
+                 5: "EGS_ERR_TIMEOUT", 6: "EGS_ERR_BUSY", 7: "EGS_ERR_UNIMPLEMENTED"}
+
+
+class EgsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+class NotPositiveDefinite(EgsError):
+    pass
+
+
+class egs_info(ctypes.Structure):
+    _fields_ = [("loglik", ctypes.c_double), ("logdet", ctypes.c_double), ("quad", ctypes.c_double),
+                ("fail_index", ctypes.c_int64), ("fail_tile", ctypes.c_int64), ("tile", ctypes.c_int32),
+                ("band", ctypes.c_int32), ("launches", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
+                ("quad_unrefined", ctypes.c_double), ("ms_generate", ctypes.c_double), ("ms_factor", ctypes.c_double),
+                ("ms_solve", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_potrf", ctypes.c_double),
+                ("ms_trsm", ctypes.c_double), ("ms_update", ctypes.c_double), ("ms_trsv", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class egs_opts(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("band", ctypes.c_int32), ("refine", ctypes.c_int32),
+                ("timing", ctypes.c_int32), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libegs.so (building it first if asked).  Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libegs.so is not built (%s); run paper_1708_02835_gb300/build.py" % path)
+    lib = ctypes.CDLL(path)
+    c = ctypes
+    vp, i64, i32, pd = c.c_void_p, c.c_int64, c.c_int32, c.POINTER(c.c_double)
+    sig = {
+        "egs_last_error": (c.c_char_p, []),
+        "egs_version": (c.c_char_p, []),
+        "egs_default_tile": (i32, [i64, c.c_int]),
+        "egs_tiles_bytes": (c.c_size_t, [i64, i32, c.c_int, i32]),
+        "egs_loglik_workspace_bytes": (c.c_size_t, [i64, i32, c.c_int, i32]),
+        "egs_matern_tiles": (c.c_int, [vp, i64, pd, i32, c.c_int, i32, vp, vp]),
+        "egs_potrf_tiles": (c.c_int, [vp, i64, i32, c.POINTER(i64), vp]),
+        "egs_trsv_tiles": (c.c_int, [vp, i64, i32, vp, vp, pd, pd, vp]),
+        "egs_loglik": (c.c_int, [vp, vp, pd, i64, c.c_int, pd, c.POINTER(egs_info), vp]),
+        "egs_loglik_ex": (c.c_int, [vp, vp, pd, i64, c.c_int, c.POINTER(egs_opts), pd, c.POINTER(egs_info), vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != EGS_OK:
+        msg = load_library().egs_last_error().decode()
+        if status == EGS_ERR_NOT_PD:
+            raise NotPositiveDefinite(status, msg)
+        raise EgsError(status, msg)
+
+
+def _ptr(t):
+    """Device or host address of a torch tensor or NumPy array (contiguous)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return t.ctypes.data
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _theta(theta):
+    th = (ctypes.c_double * 3)(*[float(v) for v in theta])
+    return ctypes.cast(th, ctypes.POINTER(ctypes.c_double)), th
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def egs_last_error() -> str:
+    return load_library().egs_last_error().decode()
+
+
+def egs_version() -> str:
+    return load_library().egs_version().decode()
+
+
+def egs_default_tile(n: int, precision="fp64") -> int:
+    return load_library().egs_default_tile(n, _prec(precision))
+
+
+def egs_tiles_bytes(n: int, tile: int, precision="fp64", band: int = 2) -> int:
+    return load_library().egs_tiles_bytes(n, tile, _prec(precision), band)
+
+
+def egs_loglik_workspace_bytes(n: int, tile: int = 0, precision="fp64", band: int = 2) -> int:
+    return load_library().egs_loglik_workspace_bytes(n, tile, _prec(precision), band)
+
+
+def egs_matern_tiles(locs, n: int, theta, tile: int, tiles, precision="fp64", band: int = 2, stream=None):
+    """Sigma(theta) (Eq. 2) into the lower-tile layout (asynchronous)."""
+    tp, _keep = _theta(theta)
+    _check(load_library().egs_matern_tiles(_ptr(locs), n, tp, tile, _prec(precision), band, _ptr(tiles),
+                                           _stream(stream)))
+
+
+def egs_potrf_tiles(tiles, n: int, tile: int, stream=None) -> int:
+    """Tile Cholesky in place; returns -1 or raises NotPositiveDefinite."""
+    fi = ctypes.c_int64(-1)
+    _check(load_library().egs_potrf_tiles(_ptr(tiles), n, tile, ctypes.byref(fi), _stream(stream)))
+    return fi.value
+
+
+def egs_trsv_tiles(tiles, n: int, tile: int, z, y, stream=None) -> tuple:
+    """Forward solve L y = z; returns (logdet, quad)."""
+    ld, q = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().egs_trsv_tiles(_ptr(tiles), n, tile, _ptr(z), _ptr(y), ctypes.byref(ld), ctypes.byref(q),
+                                         _stream(stream)))
+    return ld.value, q.value
+
+
+def egs_loglik_ex(locs, z, theta, n: int, precision="fp64", tile: int = 0, band: int = 0, refine: int = 0,
+                  timing: int = 0, workspace=None, stream=None) -> tuple:
+    """One evaluation of Eq. 1; returns (loglik, info dict)."""
+    tp, _keep = _theta(theta)
+    opts = egs_opts(tile=tile, band=band, refine=refine, timing=int(timing),
+                    workspace=_ptr(workspace) if workspace is not None else None,
+                    workspace_bytes=(workspace.numel() * workspace.element_size()) if workspace is not None else 0)
+    out = ctypes.c_double()
+    info = egs_info()
+    st = load_library().egs_loglik_ex(_ptr(locs), _ptr(z), tp, n, _prec(precision), ctypes.byref(opts),
+                                      ctypes.byref(out), ctypes.byref(info), _stream(stream))
+    _check(st)
+    return out.value, info.as_dict()
+
+
+def egs_loglik(locs, z, theta, n: int, precision="fp64", stream=None) -> float:
+    """One evaluation of Eq. 1 with default options; returns l(theta)."""
+    tp, _keep = _theta(theta)
+    out = ctypes.c_double()
+    info = egs_info()
+    _check(load_library().egs_loglik(_ptr(locs), _ptr(z), tp, n, _prec(precision), ctypes.byref(out),
+                                     ctypes.byref(info), _stream(stream)))
+    return out.value

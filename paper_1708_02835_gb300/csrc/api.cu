@@ -1,0 +1,303 @@
+// C ABI of libegs (declared in include/egs.h): argument checking, workspace
+// layout, host<->device staging and the order of the kernel launches that
+// make up one evaluation of Eq. 1 by Algorithm 2.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "egs_internal.cuh"
+
+namespace egs {
+
+static thread_local char g_err[512];
+
+egs_status set_error(egs_status code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+egs_status cuda_error(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) return set_error(EGS_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return set_error(EGS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static bool tile_ok(int32_t b) { return b >= 64 && b <= 1024 && (b % 64) == 0; }
+
+static bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static egs_status check_theta(const double *theta)
+{
+    if (!theta) return set_error(EGS_ERR_ARG, "theta is NULL");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(theta[i]) || !(theta[i] > 0.0))
+            return set_error(EGS_ERR_ARG, "theta[%d] = %g must be finite and > 0", i, theta[i]);
+    return EGS_OK;
+}
+
+// Workspace layout of one evaluation.
+struct Layout {
+    size_t tiles, locs, z, zpad, partials, status, total;
+};
+
+static Layout make_layout(const TileGeom &g)
+{
+    Layout L;
+    size_t off = 0;
+    L.tiles = off;
+    off += align256(g.ntiles() * g.tile_elems() * sizeof(double));
+    L.locs = off;
+    off += align256((size_t)2 * g.n * sizeof(double));
+    L.z = off;
+    off += align256((size_t)g.n * sizeof(double));
+    L.zpad = off;
+    off += align256((size_t)g.T * g.b * sizeof(double));
+    L.partials = off;
+    off += align256((size_t)2 * g.T * sizeof(double));
+    L.status = off;
+    off += align256(sizeof(DevStatus));
+    L.total = off;
+    return L;
+}
+
+static void status_init(DevStatus *st, cudaStream_t s)
+{
+    cudaMemsetAsync(st, 0xFF, sizeof(unsigned long long), s);
+    cudaMemsetAsync(&st->timeout, 0, sizeof(DevStatus) - sizeof(unsigned long long), s);
+}
+
+}  // namespace egs
+
+using namespace egs;
+
+extern "C" {
+
+const char *egs_last_error(void) { return g_err; }
+
+const char *egs_version(void) { return "egs 0.1 (sm_103a)"; }
+
+int32_t egs_default_tile(int64_t n, egs_precision p)
+{
+    (void)p;
+    if (n <= 4096) return 128;
+    if (n <= 16384) return 256;
+    return 512;
+}
+
+size_t egs_tiles_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band)
+{
+    (void)band;
+    if (n < 1 || !tile_ok(tile) || p != EGS_FP64) return 0;
+    TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
+    return g.ntiles() * g.tile_elems() * sizeof(double);
+}
+
+size_t egs_loglik_workspace_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band)
+{
+    (void)band;
+    if (tile == 0) tile = egs_default_tile(n, p);
+    if (n < 1 || !tile_ok(tile) || p != EGS_FP64) return 0;
+    TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
+    return make_layout(g).total;
+}
+
+egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3], int32_t tile,
+                            egs_precision p, int32_t band, void *tiles, void *stream)
+{
+    (void)band;
+    g_err[0] = 0;
+    if (n < 1) return set_error(EGS_ERR_ARG, "n = %lld must be >= 1", (long long)n);
+    if (!tile_ok(tile)) return set_error(EGS_ERR_ARG, "tile = %d must be a multiple of 64 in [64, 1024]", tile);
+    if (p != EGS_FP64) return set_error(EGS_ERR_UNIMPLEMENTED, "egs_matern_tiles: only EGS_FP64 layout");
+    if (!locs || !tiles) return set_error(EGS_ERR_ARG, "NULL pointer");
+    egs_status st = check_theta(theta);
+    if (st != EGS_OK) return st;
+    egs_matern_params P;
+    egs_matern_params_init(theta, &P);
+    TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
+    cudaError_t e = launch_matern_tiles_f64(locs, locs + n, g, P, (double *)tiles, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_error(e, "egs_matern_tiles launch");
+    return EGS_OK;
+}
+
+egs_status egs_potrf_tiles(void *tiles, int64_t n, int32_t tile, int64_t *fail_index, void *stream)
+{
+    g_err[0] = 0;
+    if (n < 1) return set_error(EGS_ERR_ARG, "n = %lld must be >= 1", (long long)n);
+    if (!tile_ok(tile)) return set_error(EGS_ERR_ARG, "tile = %d must be a multiple of 64 in [64, 1024]", tile);
+    if (!tiles) return set_error(EGS_ERR_ARG, "NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
+    DevStatus *st = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&st, sizeof(DevStatus), s);
+    if (e != cudaSuccess) return cuda_error(e, "egs_potrf_tiles workspace");
+    status_init(st, s);
+    e = launch_potrf_tiles_f64((double *)tiles, g, st, s);
+    DevStatus h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(st, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "egs_potrf_tiles");
+    const int64_t fi = (h.fail_index == kNoFail) ? -1 : (int64_t)h.fail_index;
+    if (fail_index) *fail_index = fi;
+    if (fi >= 0) return set_error(EGS_ERR_NOT_PD, "not positive definite at row %lld", (long long)fi);
+    return EGS_OK;
+}
+
+egs_status egs_trsv_tiles(const void *tiles, int64_t n, int32_t tile, const double *z, double *y,
+                          double *logdet, double *quad, void *stream)
+{
+    g_err[0] = 0;
+    if (n < 1) return set_error(EGS_ERR_ARG, "n = %lld must be >= 1", (long long)n);
+    if (!tile_ok(tile)) return set_error(EGS_ERR_ARG, "tile = %d must be a multiple of 64 in [64, 1024]", tile);
+    if (!tiles || !z || !y) return set_error(EGS_ERR_ARG, "NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
+    const size_t npad = (size_t)g.T * g.b;
+    char *ws = nullptr;
+    const size_t bytes = align256(npad * sizeof(double)) + align256(2 * g.T * sizeof(double)) + align256(sizeof(DevStatus));
+    cudaError_t e = cudaMallocAsync((void **)&ws, bytes, s);
+    if (e != cudaSuccess) return cuda_error(e, "egs_trsv_tiles workspace");
+    double *zpad = (double *)ws;
+    double *partials = (double *)(ws + align256(npad * sizeof(double)));
+    DevStatus *st = (DevStatus *)(ws + align256(npad * sizeof(double)) + align256(2 * g.T * sizeof(double)));
+    status_init(st, s);
+    e = launch_pad_vector(z, n, zpad, (int64_t)npad, s);
+    if (e == cudaSuccess) e = launch_trsv_tiles_f64((const double *)tiles, g, zpad, partials, st, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, zpad, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    DevStatus h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(ws, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "egs_trsv_tiles");
+    if (logdet) *logdet = h.result[1];
+    if (quad) *quad = h.result[2];
+    return EGS_OK;
+}
+
+egs_status egs_loglik_ex(const double *locs, const double *z, const double theta[3], int64_t n,
+                         egs_precision p, const egs_opts *opts, double *out_loglik, egs_info *info,
+                         void *stream)
+{
+    g_err[0] = 0;
+    if (out_loglik) *out_loglik = NAN;
+    if (n < 1) return set_error(EGS_ERR_ARG, "n = %lld must be >= 1", (long long)n);
+    if (!locs || !z) return set_error(EGS_ERR_ARG, "NULL pointer");
+    egs_status sc = check_theta(theta);
+    if (sc != EGS_OK) return sc;
+    if (p != EGS_FP64) return set_error(EGS_ERR_UNIMPLEMENTED, "precision %d not built", (int)p);
+    int32_t tile = (opts && opts->tile) ? opts->tile : egs_default_tile(n, p);
+    if (!tile_ok(tile)) return set_error(EGS_ERR_ARG, "tile = %d must be a multiple of 64 in [64, 1024]", tile);
+    const bool timing = opts && opts->timing;
+    KernelTimer kt;
+    kt.on = opts && opts->timing >= 2;
+    cudaStream_t s = (cudaStream_t)stream;
+    TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
+    Layout L = make_layout(g);
+
+    char *ws = nullptr;
+    bool own = false;
+    cudaError_t e = cudaSuccess;
+    if (opts && opts->workspace) {
+        if (opts->workspace_bytes < L.total)
+            return set_error(EGS_ERR_ARG, "workspace of %zu bytes < %zu needed", opts->workspace_bytes, L.total);
+        ws = (char *)opts->workspace;
+    } else {
+        e = cudaMallocAsync((void **)&ws, L.total, s);
+        if (e != cudaSuccess) return cuda_error(e, "egs_loglik workspace");
+        own = true;
+    }
+    double *tiles = (double *)(ws + L.tiles);
+    double *zpad = (double *)(ws + L.zpad);
+    double *partials = (double *)(ws + L.partials);
+    DevStatus *st = (DevStatus *)(ws + L.status);
+
+    const double *dlocs = locs, *dz = z;
+    if (!is_device_ptr(locs)) {
+        dlocs = (const double *)(ws + L.locs);
+        e = cudaMemcpyAsync((void *)dlocs, locs, (size_t)2 * n * sizeof(double), cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess && !is_device_ptr(z)) {
+        dz = (const double *)(ws + L.z);
+        e = cudaMemcpyAsync((void *)dz, z, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s);
+    }
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (timing)
+        for (int i = 0; i < 4; ++i) cudaEventCreate(&ev[i]);
+    egs_matern_params P;
+    egs_matern_params_init(theta, &P);
+    if (e == cudaSuccess) {
+        status_init(st, s);
+        if (timing) cudaEventRecord(ev[0], s);
+        e = launch_matern_tiles_f64(dlocs, dlocs + n, g, P, tiles, s, &kt);
+    }
+    if (e == cudaSuccess) {
+        if (timing) cudaEventRecord(ev[1], s);
+        e = launch_potrf_tiles_f64(tiles, g, st, s, &kt);
+    }
+    if (e == cudaSuccess) {
+        if (timing) cudaEventRecord(ev[2], s);
+        e = launch_pad_vector(dz, n, zpad, (int64_t)g.T * g.b, s, &kt);
+    }
+    if (e == cudaSuccess) e = launch_trsv_tiles_f64(tiles, g, zpad, partials, st, s, &kt);
+    if (e == cudaSuccess && timing) cudaEventRecord(ev[3], s);
+    DevStatus h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (own) cudaFreeAsync(ws, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float ms[3] = {0, 0, 0};
+    if (timing) {
+        if (e == cudaSuccess)
+            for (int i = 0; i < 3; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+        for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+    }
+    if (e != cudaSuccess) return cuda_error(e, "egs_loglik");
+    const int64_t fi = (h.fail_index == kNoFail) ? -1 : (int64_t)h.fail_index;
+    if (info) {
+        info->loglik = h.result[0];
+        info->logdet = h.result[1];
+        info->quad = h.result[2];
+        info->fail_index = fi;
+        info->fail_tile = fi >= 0 ? fi / tile : -1;
+        info->tile = tile;
+        info->band = 0;
+        info->launches = kt.launches;
+        info->refine_steps = 0;
+        info->quad_unrefined = h.result[2];
+        info->ms_generate = ms[0];
+        info->ms_factor = ms[1];
+        info->ms_solve = ms[2];
+        info->ms_total = (double)ms[0] + ms[1] + ms[2];
+        info->ms_potrf = kt.ms(KC_POTRF);
+        info->ms_trsm = kt.ms(KC_TRSM);
+        info->ms_update = kt.ms(KC_UPDATE);
+        info->ms_trsv = kt.ms(KC_TRSV);
+    }
+    if (fi >= 0) return set_error(EGS_ERR_NOT_PD, "not positive definite at row %lld (tile %lld)", (long long)fi,
+                                  (long long)(fi / tile));
+    if (out_loglik) *out_loglik = h.result[0];
+    return EGS_OK;
+}
+
+egs_status egs_loglik(const double *locs, const double *z, const double theta[3], int64_t n, egs_precision p,
+                      double *out_loglik, egs_info *info, void *stream)
+{
+    return egs_loglik_ex(locs, z, theta, n, p, nullptr, out_loglik, info, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Matern tile generator (Eq. 2; Algorithm 2, genCovMatrix): writes Sigma(theta)
+// directly into the lower-tile layout.  The distance matrix of Algorithm 2
+// (genDistanceMatrix) is never stored: each entry's distance is formed in
+// registers from the SoA coordinates.
+//
+// One CTA writes a 64 x 64 sub-block of one tile; a warp writes 32 consecutive
+// columns of one row (256 contiguous bytes), so stores are fully coalesced.
+#include "egs_internal.cuh"
+#include "matern.cuh"
+
+namespace egs {
+
+// Copy the per-launch constants into shared memory (all later reads are
+// warp-uniform broadcasts).
+__device__ __forceinline__ void stage_params(const egs_matern_params *src, egs_matern_params *dst)
+{
+    const double *s = reinterpret_cast<const double *>(src);
+    double *d = reinterpret_cast<double *>(dst);
+    constexpr int words = (int)(sizeof(egs_matern_params) / sizeof(double));
+    for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+}
+
+// Decode lower-tile linear index t -> (i, j), i >= j.
+__device__ __forceinline__ void tile_decode(int64_t t, int &i, int &j)
+{
+    int ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((int64_t)ii * (ii + 1) / 2 > t) --ii;
+    while ((int64_t)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
+    i = ii;
+    j = (int)(t - (int64_t)ii * (ii + 1) / 2);
+}
+
+__global__ void __launch_bounds__(256)
+k_matern_tiles_f64(const double *__restrict__ X, const double *__restrict__ Y, int64_t n, int b,
+                   const __grid_constant__ egs_matern_params Pg, double *__restrict__ tiles)
+{
+    __shared__ egs_matern_params Ps;
+    stage_params(&Pg, &Ps);
+    const egs_matern_params *P = &Ps;
+    int ti, tj;
+    tile_decode((int64_t)blockIdx.x, ti, tj);
+    const int nsub = b >> 6;
+    const int sr = (int)blockIdx.y / nsub, sc = (int)blockIdx.y % nsub;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    const int64_t gj = (int64_t)tj * b + sc * 64 + tx;
+    double xj = 0.0, yj = 0.0;
+    if (gj < n) {
+        xj = X[gj];
+        yj = Y[gj];
+    }
+    const double inv_th2 = P->inv_th2;
+    double *tile = tiles + (size_t)blockIdx.x * (size_t)b * (size_t)b;
+    for (int rr = 0; rr < 16; ++rr) {
+        const int r = sr * 64 + ty + 4 * rr;
+        const int64_t gi = (int64_t)ti * b + r;
+        double v;
+        if (gi >= n || gj >= n) {
+            v = (gi == gj) ? 1.0 : 0.0;
+        } else if (gi == gj) {
+            v = P->th1;
+        } else {
+            const double dx = X[gi] - xj, dy = Y[gi] - yj;
+            const double rdist = sqrt(fma(dx, dx, dy * dy));
+            v = matern_eval(P, rdist * inv_th2);
+        }
+        tile[(size_t)r * b + sc * 64 + tx] = v;
+    }
+}
+
+cudaError_t launch_matern_tiles_f64(const double *X, const double *Y, const TileGeom &g,
+                                    const egs_matern_params &P, double *tiles, cudaStream_t s, KernelTimer *kt)
+{
+    dim3 grid((unsigned)g.ntiles(), (unsigned)((g.b / 64) * (g.b / 64)));
+    EGS_LAUNCH(kt, KC_GEN, s, k_matern_tiles_f64<<<grid, 256, 0, s>>>(X, Y, g.n, g.b, P, tiles));
+    return cudaGetLastError();
+}
+
+}  // namespace egs

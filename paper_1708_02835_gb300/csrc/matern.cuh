@@ -1,0 +1,143 @@
+// Device evaluation of the Matern covariance, Eq. 2 (Section 2.2):
+//   C(r) = theta1 / (2^(nu-1) Gamma(nu)) x^nu K_nu(x),  x = r / theta2,  nu = theta3,
+// with C(0) = theta1 (the limit x^nu K_nu(x) -> 2^(nu-1) Gamma(nu), DLMF 10.30.2).
+//
+// Half-integer smoothness has closed forms (Section 2.2 names nu = 1/2, the
+// exponential model; nu = 3/2 and 5/2 follow from K_{n+1/2}, DLMF 10.39.2 and
+// 10.49.12).  Any other nu is evaluated as nu = mu + N, |mu| <= 1/2:
+//   x <= 1.25: Temme's series for K_mu and K_{mu+1};
+//   x >  1.25: Miller's backward recurrence for the minimal solution of the
+//              confluent hypergeometric recurrence, giving e^x K_mu and
+//              e^x K_{mu+1} (Temme 1975; Thompson & Barnett 1986);
+//   then N steps of K_{m+1} = K_{m-1} + (2m/x) K_m.
+// The loop lengths are made warp-uniform (the maximum over the active lanes),
+// so the per-k constants, staged in shared memory, are read as broadcasts.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "matern_params.h"
+
+namespace egs {
+
+__device__ __forceinline__ int warp_max_active(int v)
+{
+    return __reduce_max_sync(__activemask(), v);
+}
+
+// Terms of Temme's series needed for ~1e-17 truncation at x <= 1.25.
+__device__ __forceinline__ int temme_terms(double x)
+{
+    return x <= 0.1 ? 8 : (x <= 0.5 ? 12 : 16);
+}
+
+// Depth of the backward recurrence for full double accuracy at x > 1.25.
+__device__ __forceinline__ int cf_depth(double x)
+{
+    int k = (int)(14.0 + 152.0 / x) + 1;
+    return k > EGS_CF_MAX ? EGS_CF_MAX : k;
+}
+
+// x^nu K_nu(x) * c for the general case, x > 0.
+// Pp points to the constants staged in shared memory.
+__device__ __forceinline__ double matern_general(const egs_matern_params *__restrict__ Pp, double x)
+{
+    const egs_matern_params &P = *Pp;
+    const double mu = P.mu;
+    double kmu, kmu1;  // K_mu, K_{mu+1}   (scaled by e^x in the recurrence branch)
+    double front;      // c * x^nu (times e^-x in the recurrence branch)
+    if (x <= 1.25) {
+        // Temme's series.  lx = log(2/x), sigma = mu lx.
+        const double lx = -log(0.5 * x);
+        const double sig = mu * lx;
+        const double es = exp(sig);  // (2/x)^mu
+        const double ies = 1.0 / es; // (x/2)^mu
+        const double ch = 0.5 * (es + ies);
+        double shs;                  // sinh(sigma) / sigma
+        if (fabs(sig) < 0.1) {
+            const double s2 = sig * sig;
+            shs = 1.0 + s2 / 6.0 * (1.0 + s2 / 20.0 * (1.0 + s2 / 42.0 * (1.0 + s2 / 72.0)));
+        } else {
+            shs = 0.5 * (es - ies) / sig;
+        }
+        double f = P.fact * (ch * P.g1 + shs * lx * P.g2);
+        double p = 0.5 * es * P.gp;
+        double q = 0.5 * ies * P.gm;
+        const double d = 0.25 * x * x;
+        double ck = 1.0;
+        double s0 = f, s1 = p;
+        const int nt = warp_max_active(temme_terms(x));
+        for (int k = 1; k <= nt; ++k) {
+            const double kd = (double)k;
+            f = (kd * f + p + q) * P.t_k2[k];
+            p *= P.t_km[k];
+            q *= P.t_kp[k];
+            ck *= d * P.t_k[k];
+            s0 = fma(ck, f, s0);
+            s1 = fma(ck, p - kd * f, s1);
+        }
+        kmu = s0;
+        kmu1 = s1 * 2.0 / x;
+        // x^nu = x^N * 2^mu * (x/2)^mu
+        double xn = 1.0;
+        for (int j = 0; j < P.N; ++j) xn *= x;
+        front = P.c * P.two_mu * ies * xn;
+    } else {
+        // Backward recurrence z_{k-1} = 2(k + x) z_k - q_k z_{k+1}, z_{K+1} = 0,
+        // accumulating s = sum_k C_k z_k; S = s / z_0 and z_1 / z_0 are
+        // independent of the starting scale.  The start z_K = 1 / C_K keeps
+        // s near 1; every 8 steps all three are rescaled by 2^-512 when they
+        // grow past 2^512 (exact, so the ratios are unchanged).
+        double S = 1.0, r1 = 0.0;
+        if (!P.half_mu) {
+            const int K = warp_max_active(cf_depth(x));
+            const double x2 = 2.0 * x;
+            double zk1 = 0.0, zk = P.cf_ic[K];
+            double s = 1.0;
+            for (int k = K; k >= 1; --k) {
+                const double zm1 = fma(2.0 * (double)k + x2, zk, -P.cf_q[k] * zk1);
+                zk1 = zk;
+                zk = zm1;
+                s = fma(P.cf_c[k - 1], zk, s);
+                if ((k & 7) == 0 && fmax(fabs(zk), fabs(s)) > 0x1p512) {
+                    zk *= 0x1p-512;
+                    zk1 *= 0x1p-512;
+                    s *= 0x1p-512;
+                }
+            }
+            const double inv_z0 = 1.0 / zk;
+            S = s * inv_z0;
+            r1 = zk1 * inv_z0;
+        }
+        // e^x K_mu = sqrt(pi / (2x)) / S
+        kmu = 1.2533141373155002512 * rsqrt(x) / S;
+        kmu1 = kmu * (mu + x + 0.5 - (0.25 - mu * mu) * r1) / x;
+        front = P.c * exp(P.nu * log(x) - x);
+    }
+    double knu = kmu;
+    if (P.N >= 1) {
+        double km = kmu, kc = kmu1;
+        const double ix = 1.0 / x;
+        for (int j = 1; j < P.N; ++j) {
+            const double kn = fma(2.0 * (mu + (double)j) * ix, kc, km);
+            km = kc;
+            kc = kn;
+        }
+        knu = kc;
+    }
+    return front * knu;
+}
+
+// C(x * theta2) for x = r / theta2 >= 0.
+__device__ __forceinline__ double matern_eval(const egs_matern_params *__restrict__ Pp, double x)
+{
+    const egs_matern_params &P = *Pp;
+    if (x == 0.0) return P.th1;
+    switch (P.kind) {
+    case EGS_MATERN_HALF: return P.th1 * exp(-x);
+    case EGS_MATERN_3HALF: return P.th1 * (1.0 + x) * exp(-x);
+    case EGS_MATERN_5HALF: return P.th1 * fma(x, fma(x, 1.0 / 3.0, 1.0), 1.0) * exp(-x);
+    default: return matern_general(Pp, x);
+    }
+}
+
+}  // namespace egs

@@ -1,0 +1,49 @@
+/*
+ * Per-launch constants of the Matern covariance generator (Eq. 2).  Filled on
+ * the host by egs_matern_params_init (matern_host.c) and read by the device
+ * kernels in matern.cuh.  Plain C so both gcc and nvcc compile it.
+ */
+#ifndef EGS_MATERN_PARAMS_H
+#define EGS_MATERN_PARAMS_H
+
+#define EGS_TEMME_MAX 24 /* terms of Temme's series (x <= 1.25) */
+#define EGS_CF_MAX 140   /* depth of the backward recurrence (x > 1.25) */
+
+/* kind of covariance evaluation */
+#define EGS_MATERN_GENERAL 0 /* any theta3: Temme / backward recurrence */
+#define EGS_MATERN_HALF 1    /* theta3 = 1/2: theta1 exp(-x) */
+#define EGS_MATERN_3HALF 2   /* theta3 = 3/2: theta1 (1 + x) exp(-x) */
+#define EGS_MATERN_5HALF 3   /* theta3 = 5/2: theta1 (1 + x + x^2/3) exp(-x) */
+
+typedef struct {
+    double th1, th2, inv_th2, nu, mu;
+    double c;      /* theta1 / (2^(nu-1) Gamma(nu)) */
+    double two_mu; /* 2^mu */
+    double fact;   /* mu pi / sin(mu pi), 1 at mu = 0 */
+    double g1;     /* Gamma_1(mu) = (1/Gamma(1-mu) - 1/Gamma(1+mu)) / (2 mu) */
+    double g2;     /* Gamma_2(mu) = (1/Gamma(1-mu) + 1/Gamma(1+mu)) / 2 */
+    double gp;     /* Gamma(1 + mu) */
+    double gm;     /* Gamma(1 - mu) */
+    int kind;
+    int N;         /* nu = mu + N */
+    int half_mu;   /* |mu| = 1/2: C_k = 0 for k >= 1, the recurrence is not needed */
+    int pad1;
+    double t_k2[EGS_TEMME_MAX + 1]; /* 1 / (k^2 - mu^2) */
+    double t_km[EGS_TEMME_MAX + 1]; /* 1 / (k - mu) */
+    double t_kp[EGS_TEMME_MAX + 1]; /* 1 / (k + mu) */
+    double t_k[EGS_TEMME_MAX + 1];  /* 1 / k */
+    double cf_q[EGS_CF_MAX + 2];    /* (k + 1/2)^2 - mu^2 */
+    double cf_c[EGS_CF_MAX + 2];    /* C_k = prod_{j=1..k} ((j - 1/2)^2 - mu^2) / j, C_0 = 1 */
+    double cf_ic[EGS_CF_MAX + 2];   /* 1 / C_k (unused when half_mu) */
+} egs_matern_params;
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+/* Returns 0 on success, -1 if theta is not finite and positive. */
+int egs_matern_params_init(const double theta[3], egs_matern_params *P);
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,144 @@
+// Forward solve L y = Z on the lower-tile layout (Algorithm 2, dtrsm; the
+// text of Section 5.4 writes it as L Z_new = Z_old), fused with the
+// log-determinant log|Sigma| = 2 sum_i log L_ii (Section 5.1, taken in log
+// form) and the dot product y^T y (Algorithm 2, computeDotProduct), then the
+// assembly l = -1/2 y^T y - 1/2 log|Sigma| - n/2 log(2 pi) (Eq. 1).
+//
+// Column-oriented block substitution: for k = 0..T-1, the diagonal kernel
+// solves tile k in place and records its two partial sums; the panel kernel
+// then subtracts L_mk y_k from every later block (one CTA owns each output
+// row, so the update order is fixed).  The whole solve reads each stored
+// tile of L exactly once.  Reductions are fixed-order trees, so results are
+// bitwise reproducible.
+#include "egs_internal.cuh"
+
+namespace egs {
+
+__device__ __forceinline__ bool failed_s(const DevStatus *st)
+{
+    return *(volatile const unsigned long long *)&st->fail_index != kNoFail;
+}
+
+__global__ void k_pad_vector(const double *__restrict__ z, int64_t n, double *__restrict__ zpad, int64_t npad)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < npad) zpad[i] = (i < n) ? z[i] : 0.0;
+}
+
+// Fixed-order tree reduction of one value per thread (any blockDim.x <= 1024).
+// Returns the total (valid in every thread after the last barrier).
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    red[tid] = v;
+    __syncthreads();
+    int p2 = 1;
+    while (p2 < nt) p2 <<= 1;
+    for (int s = p2 >> 1; s > 0; s >>= 1) {
+        if (tid < s && tid + s < nt) red[tid] += red[tid + s];
+        __syncthreads();
+    }
+    return red[0];
+}
+
+// Diagonal block: y_k = L_kk^-1 r_k in place, blockDim.x = b threads.
+__global__ void __launch_bounds__(1024) k_trsv_diag_f64(const double *__restrict__ tiles, int b, int k,
+                                                        double *__restrict__ zpad, double *__restrict__ partials,
+                                                        int T, DevStatus *st)
+{
+    if (failed_s(st)) return;
+    __shared__ double yv[1024];
+    __shared__ double red[1024];
+    const int i = threadIdx.x;
+    const double *L = tiles + (size_t)tile_linear(k, k) * (size_t)b * (size_t)b;
+    const double *Li = L + (size_t)i * b;
+    double r = zpad[(size_t)k * b + i];
+    for (int c = 0; c < b; ++c) {
+        if (i == c) yv[c] = r / Li[c];
+        __syncthreads();
+        if (i > c) r = fma(-Li[c], yv[c], r);
+    }
+    const double y = yv[i];
+    zpad[(size_t)k * b + i] = y;
+    const double ld = block_sum(log(Li[i]), red);
+    __syncthreads();
+    const double q = block_sum(y * y, red);
+    if (i == 0) {
+        partials[k] = ld;
+        partials[T + k] = q;
+    }
+}
+
+// Panel: z_m -= L_mk y_k for m = k+1..T-1.  grid = (T-k-1, b/64), 256
+// threads; each warp owns 8 rows and reduces each row's dot product with a
+// fixed shuffle tree.
+__global__ void __launch_bounds__(256) k_gemv_panel_f64(const double *__restrict__ tiles, int b, int k,
+                                                        double *__restrict__ zpad, DevStatus *st)
+{
+    if (failed_s(st)) return;
+    extern __shared__ double ys[];
+    const int m = k + 1 + (int)blockIdx.x;
+    const int r0 = (int)blockIdx.y * 64;
+    for (int c = threadIdx.x; c < b; c += 256) ys[c] = zpad[(size_t)k * b + c];
+    __syncthreads();
+    const double *A = tiles + (size_t)tile_linear(m, k) * (size_t)b * (size_t)b;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rr = 0; rr < 8; ++rr) {
+        const int r = r0 + warp * 8 + rr;
+        const double *row = A + (size_t)r * b;
+        double s = 0.0;
+        for (int c = lane; c < b; c += 32) s = fma(row[c], ys[c], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) zpad[(size_t)m * b + r] -= s;
+    }
+}
+
+// l = -1/2 quad - 1/2 logdet - n/2 log(2 pi) from the per-tile partials.
+__global__ void k_finalize(const double *__restrict__ partials, int T, int64_t n, DevStatus *st)
+{
+    __shared__ double red[256];
+    double a = 0.0, q = 0.0;
+    for (int t = threadIdx.x; t < T; t += 256) {
+        a += partials[t];
+        q += partials[T + t];
+    }
+    const double lsum = block_sum(a, red);
+    __syncthreads();
+    const double qsum = block_sum(q, red);
+    if (threadIdx.x == 0) {
+        if (failed_s(st)) {
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            st->result[0] = st->result[1] = st->result[2] = nan;
+        } else {
+            const double logdet = 2.0 * lsum;
+            st->result[0] = -0.5 * qsum - 0.5 * logdet - 0.5 * (double)n * 1.8378770664093454836;  // log(2 pi)
+            st->result[1] = logdet;
+            st->result[2] = qsum;
+        }
+    }
+}
+
+cudaError_t launch_pad_vector(const double *z, int64_t n, double *zpad, int64_t npad, cudaStream_t s, KernelTimer *kt)
+{
+    const unsigned blocks = (unsigned)((npad + 255) / 256);
+    EGS_LAUNCH(kt, KC_OTHER, s, k_pad_vector<<<blocks, 256, 0, s>>>(z, n, zpad, npad));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trsv_tiles_f64(const double *tiles, const TileGeom &g, double *zpad, double *partials,
+                                  DevStatus *st, cudaStream_t s, KernelTimer *kt)
+{
+    const int b = g.b, T = g.T;
+    for (int k = 0; k < T; ++k) {
+        EGS_LAUNCH(kt, KC_TRSV, s, k_trsv_diag_f64<<<1, b, 0, s>>>(tiles, b, k, zpad, partials, T, st));
+        if (k + 1 < T)
+            EGS_LAUNCH(kt, KC_TRSV, s,
+                       k_gemv_panel_f64<<<dim3((unsigned)(T - k - 1), (unsigned)(b / 64)), 256,
+                                          (size_t)b * sizeof(double), s>>>(tiles, b, k, zpad, st));
+    }
+    EGS_LAUNCH(kt, KC_OTHER, s, k_finalize<<<1, 256, 0, s>>>(partials, T, g.n, st));
+    return cudaGetLastError();
+}
+
+}  // namespace egs
