@@ -170,6 +170,20 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
                          egs_precision p, const egs_opts *opts, double *out_loglik, egs_info *info,
                          void *stream);
 
+/*
+ * egs_tc_gemm_test - the tensor-core pipeline of the trailing update on its
+ * own: C = A B^T with tcgen05.mma (FP32 accumulation in TMEM), operands
+ * streamed by TMA.  Exposed so that the MMA/descriptor path can be checked in
+ * isolation; the factorisation calls the same kernel template.
+ *   A  device, M x K row-major, FP32 (EGS_MIX_TF32: read as TF32) or BF16
+ *   B  device, N x K row-major, same type
+ *   C  device, M x N row-major FP32, written
+ * M % 128 == 0, N % 256 == 0, K % 64 == 0.  Synchronises stream.
+ * EGS_ERR_TIMEOUT if a pipeline wait expired (the kernel unwinds cleanly).
+ */
+egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, int32_t N, int32_t K, egs_precision p, float *C,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

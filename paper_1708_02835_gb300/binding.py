@@ -80,6 +80,7 @@ def load_library(build_if_missing: bool = True):
         "egs_trsv_tiles": (c.c_int, [vp, i64, i32, vp, vp, pd, pd, vp]),
         "egs_loglik": (c.c_int, [vp, vp, pd, i64, c.c_int, pd, c.POINTER(egs_info), vp]),
         "egs_loglik_ex": (c.c_int, [vp, vp, pd, i64, c.c_int, c.POINTER(egs_opts), pd, c.POINTER(egs_info), vp]),
+        "egs_tc_gemm_test": (c.c_int, [vp, vp, i32, i32, i32, c.c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -195,3 +196,10 @@ def egs_loglik(locs, z, theta, n: int, precision="fp64", stream=None) -> float:
     _check(load_library().egs_loglik(_ptr(locs), _ptr(z), tp, n, _prec(precision), ctypes.byref(out),
                                      ctypes.byref(info), _stream(stream)))
     return out.value
+
+
+def egs_tc_gemm_test(A, B, C, precision="tf32", stream=None):
+    """C = A B^T on the tcgen05 pipeline (A: M x K, B: N x K, C: M x N FP32)."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(load_library().egs_tc_gemm_test(_ptr(A), _ptr(B), M, N, K, _prec(precision), _ptr(C), _stream(stream)))

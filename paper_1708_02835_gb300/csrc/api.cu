@@ -75,6 +75,46 @@ static Layout make_layout(const TileGeom &g)
     return L;
 }
 
+// Workspace layout of one mixed-precision evaluation.
+struct MixedLayout {
+    size_t f64, f32, sig, panel, locs, z, vec, partials, status, err, total;
+};
+
+static int mix_fmt(egs_precision p) { return p == EGS_MIX_TF32 ? 2 : 1; }
+
+static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision p)
+{
+    MixedLayout L;
+    const size_t bb = g.tile_elems();
+    const size_t npad = (size_t)g.T * g.b;
+    const size_t esz = (mix_fmt(p) == 2) ? 4 : 2;
+    size_t off = 0;
+    L.f64 = off;
+    off += align256(Tiles::f64_tiles(g.T, band) * bb * sizeof(double));
+    L.f32 = off;
+    off += align256(Tiles::f32_tiles(g.T, band) * bb * sizeof(float));
+    L.sig = off;
+    off += align256(g.ntiles() * bb * sizeof(double));
+    L.panel = off;
+    off += align256((size_t)(g.T > 1 ? g.T - 1 : 1) * bb * esz);
+    L.locs = off;
+    off += align256((size_t)2 * g.n * sizeof(double));
+    L.z = off;
+    off += align256((size_t)g.n * sizeof(double));
+    L.vec = off;
+    off += 7 * align256(npad * sizeof(double));
+    L.partials = off;
+    off += align256((size_t)2 * g.T * sizeof(double));
+    L.status = off;
+    off += align256(sizeof(DevStatus));
+    L.err = off;
+    off += 256;
+    L.total = off;
+    return L;
+}
+
+static bool mixed_p(egs_precision p) { return p == EGS_MIX_TF32 || p == EGS_MIX_BF16; }
+
 static void status_init(DevStatus *st, cudaStream_t s)
 {
     cudaMemsetAsync(st, 0xFF, sizeof(unsigned long long), s);
@@ -93,7 +133,7 @@ const char *egs_version(void) { return "egs 0.1 (sm_103a)"; }
 
 int32_t egs_default_tile(int64_t n, egs_precision p)
 {
-    (void)p;
+    if (mixed_p(p)) return n <= 16384 ? 256 : 512;
     if (n <= 4096) return 128;
     if (n <= 16384) return 256;
     return 512;
@@ -109,11 +149,16 @@ size_t egs_tiles_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band)
 
 size_t egs_loglik_workspace_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band)
 {
-    (void)band;
     if (tile == 0) tile = egs_default_tile(n, p);
-    if (n < 1 || !tile_ok(tile) || p != EGS_FP64) return 0;
+    if (band <= 0) band = 2;
+    if (n < 1 || !tile_ok(tile)) return 0;
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
-    return make_layout(g).total;
+    if (p == EGS_FP64 || (mixed_p(p) && g.T <= band)) return make_layout(g).total;
+    if (mixed_p(p) && tile % 256 == 0) {
+        const size_t a = make_mixed_layout(g, band, p).total, b = make_layout(g).total;
+        return a > b ? a : b;
+    }
+    return 0;
 }
 
 egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3], int32_t tile,
@@ -200,40 +245,48 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
     if (!locs || !z) return set_error(EGS_ERR_ARG, "NULL pointer");
     egs_status sc = check_theta(theta);
     if (sc != EGS_OK) return sc;
-    if (p != EGS_FP64) return set_error(EGS_ERR_UNIMPLEMENTED, "precision %d not built", (int)p);
+    if (p != EGS_FP64 && !mixed_p(p)) return set_error(EGS_ERR_UNIMPLEMENTED, "precision %d not built", (int)p);
     int32_t tile = (opts && opts->tile) ? opts->tile : egs_default_tile(n, p);
     if (!tile_ok(tile)) return set_error(EGS_ERR_ARG, "tile = %d must be a multiple of 64 in [64, 1024]", tile);
+    const int band = (opts && opts->band > 0) ? opts->band : 2;
+    const int refine = (opts && opts->refine) ? (opts->refine < 0 ? 0 : opts->refine) : 1;
+    if (mixed_p(p) && tile % 256 != 0)
+        return set_error(EGS_ERR_ARG, "mixed precision needs tile %% 256 == 0 (got %d)", tile);
     const bool timing = opts && opts->timing;
     KernelTimer kt;
     kt.on = opts && opts->timing >= 2;
     cudaStream_t s = (cudaStream_t)stream;
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
+    const bool mixed = mixed_p(p) && g.T > band;
     Layout L = make_layout(g);
+    MixedLayout ML = make_mixed_layout(g, band, p);
+    const size_t need = mixed ? ML.total : L.total;
+    const size_t locs_off = mixed ? ML.locs : L.locs, z_off = mixed ? ML.z : L.z;
 
     char *ws = nullptr;
     bool own = false;
     cudaError_t e = cudaSuccess;
     if (opts && opts->workspace) {
-        if (opts->workspace_bytes < L.total)
-            return set_error(EGS_ERR_ARG, "workspace of %zu bytes < %zu needed", opts->workspace_bytes, L.total);
+        if (opts->workspace_bytes < need)
+            return set_error(EGS_ERR_ARG, "workspace of %zu bytes < %zu needed", opts->workspace_bytes, need);
         ws = (char *)opts->workspace;
     } else {
-        e = cudaMallocAsync((void **)&ws, L.total, s);
+        e = cudaMallocAsync((void **)&ws, need, s);
         if (e != cudaSuccess) return cuda_error(e, "egs_loglik workspace");
         own = true;
     }
     double *tiles = (double *)(ws + L.tiles);
     double *zpad = (double *)(ws + L.zpad);
     double *partials = (double *)(ws + L.partials);
-    DevStatus *st = (DevStatus *)(ws + L.status);
+    DevStatus *st = (DevStatus *)(ws + (mixed ? ML.status : L.status));
 
     const double *dlocs = locs, *dz = z;
     if (!is_device_ptr(locs)) {
-        dlocs = (const double *)(ws + L.locs);
+        dlocs = (const double *)(ws + locs_off);
         e = cudaMemcpyAsync((void *)dlocs, locs, (size_t)2 * n * sizeof(double), cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess && !is_device_ptr(z)) {
-        dz = (const double *)(ws + L.z);
+        dz = (const double *)(ws + z_off);
         e = cudaMemcpyAsync((void *)dz, z, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s);
     }
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -241,21 +294,43 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
         for (int i = 0; i < 4; ++i) cudaEventCreate(&ev[i]);
     egs_matern_params P;
     egs_matern_params_init(theta, &P);
-    if (e == cudaSuccess) {
-        status_init(st, s);
+    if (e == cudaSuccess) status_init(st, s);
+    if (e == cudaSuccess && mixed) {
+        const size_t npad = (size_t)g.T * g.b;
+        MixedBuffers mb;
+        mb.tl = Tiles{(double *)(ws + ML.f64), (float *)(ws + ML.f32), g.b, g.T, band};
+        mb.sig = (double *)(ws + ML.sig);
+        mb.panel = ws + ML.panel;
+        double *v = (double *)(ws + ML.vec);
+        const size_t stride = align256(npad * sizeof(double)) / sizeof(double);
+        mb.zp = v;
+        mb.y = v + stride;
+        mb.x = v + 2 * stride;
+        mb.d = v + 3 * stride;
+        mb.res = v + 4 * stride;
+        mb.rows = v + 5 * stride;
+        mb.cols = v + 6 * stride;
+        mb.partials = (double *)(ws + ML.partials);
+        mb.err = (int *)(ws + ML.err);
+        cudaMemsetAsync(mb.err, 0, sizeof(int), s);
+        e = run_loglik_mixed(dlocs, dlocs + n, dz, n, P, mix_fmt(p), refine, mb, st, s, &kt, timing ? ev : nullptr);
+    } else if (e == cudaSuccess) {
         if (timing) cudaEventRecord(ev[0], s);
         e = launch_matern_tiles_f64(dlocs, dlocs + n, g, P, tiles, s, &kt);
+        if (e == cudaSuccess) {
+            if (timing) cudaEventRecord(ev[1], s);
+            e = launch_potrf_tiles_f64(tiles, g, st, s, &kt);
+        }
+        if (e == cudaSuccess) {
+            if (timing) cudaEventRecord(ev[2], s);
+            e = launch_pad_vector(dz, n, zpad, (int64_t)g.T * g.b, s, &kt);
+        }
+        if (e == cudaSuccess) e = launch_trsv_tiles_f64(tiles, g, zpad, partials, st, s, &kt);
+        if (e == cudaSuccess && timing) cudaEventRecord(ev[3], s);
     }
-    if (e == cudaSuccess) {
-        if (timing) cudaEventRecord(ev[1], s);
-        e = launch_potrf_tiles_f64(tiles, g, st, s, &kt);
-    }
-    if (e == cudaSuccess) {
-        if (timing) cudaEventRecord(ev[2], s);
-        e = launch_pad_vector(dz, n, zpad, (int64_t)g.T * g.b, s, &kt);
-    }
-    if (e == cudaSuccess) e = launch_trsv_tiles_f64(tiles, g, zpad, partials, st, s, &kt);
-    if (e == cudaSuccess && timing) cudaEventRecord(ev[3], s);
+    int herr = 0;
+    if (e == cudaSuccess && mixed)
+        e = cudaMemcpyAsync(&herr, ws + ML.err, sizeof(int), cudaMemcpyDeviceToHost, s);
     DevStatus h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (own) cudaFreeAsync(ws, s);
@@ -267,6 +342,7 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
         for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
     }
     if (e != cudaSuccess) return cuda_error(e, "egs_loglik");
+    if (herr) return set_error(EGS_ERR_TIMEOUT, "egs_loglik: a tensor-core pipeline wait timed out");
     const int64_t fi = (h.fail_index == kNoFail) ? -1 : (int64_t)h.fail_index;
     if (info) {
         info->loglik = h.result[0];
@@ -275,10 +351,10 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
         info->fail_index = fi;
         info->fail_tile = fi >= 0 ? fi / tile : -1;
         info->tile = tile;
-        info->band = 0;
+        info->band = mixed ? band : g.T;
         info->launches = kt.launches;
-        info->refine_steps = 0;
-        info->quad_unrefined = h.result[2];
+        info->refine_steps = mixed ? refine : 0;
+        info->quad_unrefined = mixed ? h.result[3] : h.result[2];
         info->ms_generate = ms[0];
         info->ms_factor = ms[1];
         info->ms_solve = ms[2];

@@ -3,6 +3,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <vector>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/egs.h"
@@ -23,6 +24,35 @@ struct DevStatus {
 constexpr unsigned long long kNoFail = 0xFFFFFFFFFFFFFFFFull;
 
 __host__ __device__ inline int64_t tile_linear(int64_t i, int64_t j) { return i * (i + 1) / 2 + j; }
+
+// Storage of the lower tiles.  Dense FP64 mode (band >= T): every tile is
+// double, tile (i, j) at position i (i + 1) / 2 + j of f64.  Mixed mode:
+// tiles with i - j < band are double in f64 at position i * band + (i - j);
+// the others are float in f32 at position (i - band)(i - band + 1) / 2 + j.
+struct Tiles {
+    double *f64;
+    float *f32;
+    int b, T, band;
+    __host__ __device__ bool dense() const { return band >= T; }
+    __host__ __device__ bool is64(int i, int j) const { return i - j < band; }
+    __host__ __device__ size_t bb() const { return (size_t)b * (size_t)b; }
+    __host__ __device__ double *t64(int i, int j) const
+    {
+        return dense() ? f64 + (size_t)tile_linear(i, j) * bb() : f64 + ((size_t)i * band + (i - j)) * bb();
+    }
+    __host__ __device__ float *t32(int i, int j) const
+    {
+        const int64_t r = i - band;
+        return f32 + ((size_t)(r * (r + 1) / 2) + (size_t)j) * bb();
+    }
+    static size_t f64_tiles(int T, int band) { return band >= T ? (size_t)T * (T + 1) / 2 : (size_t)T * band; }
+    static size_t f32_tiles(int T, int band)
+    {
+        if (band >= T) return 0;
+        const size_t r = (size_t)(T - band);
+        return r * (r + 1) / 2;
+    }
+};
 
 // Geometry of a lower-tile matrix.
 struct TileGeom {
@@ -84,6 +114,10 @@ struct KernelTimer {
         if (kt) (kt)->end((cls), (s));   \
     } while (0)
 
+// Error reporting (api.cu): thread-local message, returns code.
+egs_status set_error(egs_status code, const char *fmt, ...);
+egs_status cuda_error(cudaError_t e, const char *what);
+
 // ---- launchers (stream-ordered, no synchronisation) ----
 // Sigma(theta) into FP64 lower tiles.
 cudaError_t launch_matern_tiles_f64(const double *X, const double *Y, const TileGeom &g,
@@ -99,8 +133,43 @@ cudaError_t launch_potrf_tiles_f64(double *tiles, const TileGeom &g, DevStatus *
 cudaError_t launch_trsv_tiles_f64(const double *tiles, const TileGeom &g, double *zpad, double *partials,
                                   DevStatus *st, cudaStream_t s, KernelTimer *kt = nullptr);
 
+// Sigma(theta) into any Tiles storage (+ optional dense FP64 copy sig).
+cudaError_t launch_matern_tiles(const double *X, const double *Y, int64_t n, const Tiles &tl,
+                                const egs_matern_params &P, double *sig, cudaStream_t s, KernelTimer *kt);
+
+// Mixed-precision evaluation buffers (all device, sized by mixed_layout).
+struct MixedBuffers {
+    Tiles tl;
+    double *sig;      // dense FP64 lower tiles of Sigma (for the refinement residual)
+    void *panel;      // (T-1) * b * b operands (FP32 for TF32, BF16)
+    double *zp, *y, *x, *d, *res, *rows, *cols;  // T*b vectors
+    double *partials; // 2T
+    int *err;
+};
+
+// One mixed-precision evaluation (fmt 2 = TF32, 1 = BF16 operands); the
+// result lands in st->result (loglik, logdet, quad refined, quad unrefined).
+cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, int64_t n, const egs_matern_params &P,
+                             int fmt, int refine, const MixedBuffers &mb, DevStatus *st, cudaStream_t s, KernelTimer *kt,
+                             cudaEvent_t *phase_ev);
+
+// Building blocks shared by the FP64 and mixed drivers.
+cudaError_t launch_potrf_diag(const Tiles &tl, int k, DevStatus *st, cudaStream_t s, KernelTimer *kt);
+cudaError_t launch_trsm_f64(const Tiles &tl, int k, int nrows, DevStatus *st, cudaStream_t s, KernelTimer *kt);
+// FP64 update of the first ntri tiles of step k's trailing triangle (row order).
+cudaError_t launch_update_f64(const Tiles &tl, int k, int64_t ntri, DevStatus *st, cudaStream_t s, KernelTimer *kt);
+cudaError_t launch_forward_solve(const Tiles &tl, double *zpad, double *partials, DevStatus *st, cudaStream_t s,
+                                 KernelTimer *kt);
+cudaError_t launch_finalize(const double *partials, int T, int64_t n, DevStatus *st, cudaStream_t s, KernelTimer *kt);
+
 // Copy z (n doubles) into zpad (T*b doubles), zero padding.
 cudaError_t launch_pad_vector(const double *z, int64_t n, double *zpad, int64_t npad, cudaStream_t s,
                               KernelTimer *kt = nullptr);
+
+// Tensor maps over the panel operand buffer ((T-1)*b rows of b elements;
+// fmt 2 = FP32/TF32, 1 = BF16) and the tcgen05 trailing update of step k.
+cudaError_t make_panel_maps(const void *panel, int fmt, int b, int T, CUtensorMap *mapA, CUtensorMap *mapB);
+cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, int fmt, const Tiles &tl, int k,
+                             int *err, cudaStream_t s, KernelTimer *kt);
 
 }  // namespace egs

@@ -31,10 +31,15 @@ __device__ __forceinline__ void tile_decode(int64_t t, int &i, int &j)
     j = (int)(t - (int64_t)ii * (ii + 1) / 2);
 }
 
+// Writes tile blockIdx.x (lower-tile order) of Sigma into tl: as double when
+// the tile is FP64 in tl, else rounded to float.  If sig is not NULL the
+// double values are also written to sig in the dense lower-tile layout (the
+// FP64 copy the mixed-precision refinement multiplies with).
 __global__ void __launch_bounds__(256)
-k_matern_tiles_f64(const double *__restrict__ X, const double *__restrict__ Y, int64_t n, int b,
-                   const __grid_constant__ egs_matern_params Pg, double *__restrict__ tiles)
+k_matern_tiles(const double *__restrict__ X, const double *__restrict__ Y, int64_t n, Tiles tl,
+               const __grid_constant__ egs_matern_params Pg, double *__restrict__ sig)
 {
+    const int b = tl.b;
     __shared__ egs_matern_params Ps;
     stage_params(&Pg, &Ps);
     const egs_matern_params *P = &Ps;
@@ -50,7 +55,10 @@ k_matern_tiles_f64(const double *__restrict__ X, const double *__restrict__ Y, i
         yj = Y[gj];
     }
     const double inv_th2 = P->inv_th2;
-    double *tile = tiles + (size_t)blockIdx.x * (size_t)b * (size_t)b;
+    const bool is64 = tl.is64(ti, tj);
+    double *t64 = is64 ? tl.t64(ti, tj) : nullptr;
+    float *t32 = is64 ? nullptr : tl.t32(ti, tj);
+    double *tsig = sig ? sig + (size_t)blockIdx.x * (size_t)b * (size_t)b : nullptr;
     for (int rr = 0; rr < 16; ++rr) {
         const int r = sr * 64 + ty + 4 * rr;
         const int64_t gi = (int64_t)ti * b + r;
@@ -64,16 +72,27 @@ k_matern_tiles_f64(const double *__restrict__ X, const double *__restrict__ Y, i
             const double rdist = sqrt(fma(dx, dx, dy * dy));
             v = matern_eval(P, rdist * inv_th2);
         }
-        tile[(size_t)r * b + sc * 64 + tx] = v;
+        const size_t off = (size_t)r * b + sc * 64 + tx;
+        if (is64) t64[off] = v;
+        else t32[off] = (float)v;
+        if (tsig) tsig[off] = v;
     }
+}
+
+cudaError_t launch_matern_tiles(const double *X, const double *Y, int64_t n, const Tiles &tl,
+                                const egs_matern_params &P, double *sig, cudaStream_t s, KernelTimer *kt)
+{
+    const size_t ntiles = (size_t)tl.T * (tl.T + 1) / 2;
+    dim3 grid((unsigned)ntiles, (unsigned)((tl.b / 64) * (tl.b / 64)));
+    EGS_LAUNCH(kt, KC_GEN, s, k_matern_tiles<<<grid, 256, 0, s>>>(X, Y, n, tl, P, sig));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_matern_tiles_f64(const double *X, const double *Y, const TileGeom &g,
                                     const egs_matern_params &P, double *tiles, cudaStream_t s, KernelTimer *kt)
 {
-    dim3 grid((unsigned)g.ntiles(), (unsigned)((g.b / 64) * (g.b / 64)));
-    EGS_LAUNCH(kt, KC_GEN, s, k_matern_tiles_f64<<<grid, 256, 0, s>>>(X, Y, g.n, g.b, P, tiles));
-    return cudaGetLastError();
+    const Tiles tl{tiles, nullptr, g.b, g.T, g.T};
+    return launch_matern_tiles(X, Y, g.n, tl, P, nullptr, s, kt);
 }
 
 }  // namespace egs

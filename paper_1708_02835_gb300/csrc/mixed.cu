@@ -1,0 +1,361 @@
+// Mixed-precision evaluation of Eq. 1 (Algorithm 2) with an FP64 diagonal band.
+//
+// Storage: tiles with i - j < band (the diagonal band) stay FP64; the others
+// are FP32.  Per step k of the right-looking tile Cholesky (Section 4.2):
+//   POTRF  L_kk in FP64;
+//   TRSM   band rows (m - k < band) in FP64, the other rows in FP32 with
+//          L_kk rounded to FP32; every solved tile is also written to the
+//          panel buffer in the tensor-core operand format (TF32-rounded FP32
+//          or BF16);
+//   UPDATE C_mn -= P_m P_n^T: when both P_m and P_n are FP64 band tiles the
+//          update runs in FP64 (DFMA) on the unrounded values; every other
+//          update runs on tcgen05 with FP32 accumulation (tc_gemm.cu) and is
+//          subtracted in FP64 from band tiles and in FP32 from the others.
+// The log-determinant 2 sum log L_ii is reduced in FP64 from the FP64
+// diagonal tiles.  The quadratic form Z^T Sigma^-1 Z is won back in FP64 by
+// iterative refinement: x0 = L^-T L^-1 Z, r = Z - Sigma x0 with Sigma the FP64
+// copy written by the generator, x1 = x0 + L^-T L^-1 r, quad = Z^T x1.
+#include "egs_internal.cuh"
+
+#include <cuda_bf16.h>
+
+namespace egs {
+
+namespace {
+
+__device__ __forceinline__ bool mfailed(const DevStatus *st)
+{
+    return *(volatile const unsigned long long *)&st->fail_index != kNoFail;
+}
+
+__device__ __forceinline__ float to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int FMT>
+__device__ __forceinline__ void panel_store(void *panel, size_t idx, float v)
+{
+    if (FMT == 2) reinterpret_cast<float *>(panel)[idx] = to_tf32(v);
+    else reinterpret_cast<__nv_bfloat16 *>(panel)[idx] = __float2bfloat16_rn(v);
+}
+
+// FP64 band panel tiles (m = k+1..k+nrows) -> operand format.
+template <int FMT>
+__global__ void __launch_bounds__(256) k_panel_from_f64(Tiles tl, int k, int nrows, void *panel, const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    const size_t bb = tl.bb();
+    const size_t total = (size_t)nrows * bb;
+    for (size_t e = (size_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (size_t)gridDim.x * 256) {
+        const int t = (int)(e / bb);
+        const size_t off = e % bb;
+        const int m = k + 1 + t;
+        panel_store<FMT>(panel, (size_t)(m - k - 1) * bb + off, (float)tl.t64(m, k)[off]);
+    }
+}
+
+// TRSM of the FP32 panel rows m = m0 + blockIdx.x: X L_kk^T = A_mk in FP32
+// (L_kk rounded to FP32), 64 rows per CTA, 32-column blocks; the result
+// overwrites A_mk and is written to the panel buffer.
+template <int FMT>
+__global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0, void *panel, const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    const int b = tl.b;
+    const int m = m0 + (int)blockIdx.x;
+    const int r0 = (int)blockIdx.y * 64;
+    const double *L = tl.t64(k, k);
+    float *A = tl.t32(m, k) + (size_t)r0 * b;
+    const size_t pbase = (size_t)(m - k - 1) * tl.bb() + (size_t)r0 * b;
+    __shared__ float Xs[64][17];
+    __shared__ float Ls[32][17];
+    __shared__ float Ab[64][33];
+    __shared__ float Ld[32][33];
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    for (int c0 = 0; c0 < b; c0 += 32) {
+        float acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = A[(size_t)(ty * 8 + i) * b + c0 + tx];
+        for (int p = 0; p < c0; p += 16) {
+            for (int e = tid; e < 64 * 16; e += 256) {
+                const int r = e >> 4, l = e & 15;
+                Xs[r][l] = A[(size_t)r * b + p + l];
+            }
+            for (int e = tid; e < 32 * 16; e += 256) {
+                const int c = e >> 4, l = e & 15;
+                Ls[c][l] = (float)L[(size_t)(c0 + c) * b + p + l];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int l = 0; l < 16; ++l) {
+                const float lv = Ls[tx][l];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc[i] = fmaf(-Xs[ty * 8 + i][l], lv, acc[i]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) Ab[ty * 8 + i][tx] = acc[i];
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int r = e >> 5, c = e & 31;
+            Ld[r][c] = (c <= r) ? (float)L[(size_t)(c0 + r) * b + c0 + c] : 0.0f;
+        }
+        __syncthreads();
+        if (tid < 64) {
+            for (int j = 0; j < 32; ++j) {
+                float s = Ab[tid][j];
+                for (int l = 0; l < j; ++l) s = fmaf(-Ab[tid][l], Ld[j][l], s);
+                Ab[tid][j] = s / Ld[j][j];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float v = Ab[ty * 8 + i][tx];
+            const size_t off = (size_t)(ty * 8 + i) * b + c0 + tx;
+            A[off] = v;
+            panel_store<FMT>(panel, pbase + off, v);
+        }
+        __syncthreads();
+    }
+}
+
+// Backward substitution on a diagonal tile: L_kk^T x = r in place, b threads.
+__global__ void __launch_bounds__(1024) k_trsv_diag_T(Tiles tl, int k, double *__restrict__ v, const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    __shared__ double xv[1024];
+    const int i = threadIdx.x, b = tl.b;
+    const double *L = tl.t64(k, k);
+    double r = v[(size_t)k * b + i];
+    for (int c = b - 1; c >= 0; --c) {
+        if (i == c) xv[c] = r / L[(size_t)c * b + c];
+        __syncthreads();
+        if (i < c) r = fma(-L[(size_t)c * b + i], xv[c], r);
+    }
+    v[(size_t)k * b + i] = xv[i];
+}
+
+template <typename E>
+__device__ __forceinline__ double col_dot(const E *__restrict__ A, int b, int c, int g, const double *xs)
+{
+    double s = 0.0;
+    for (int r = g; r < b; r += 4) s = fma((double)A[(size_t)r * b + c], xs[r], s);
+    return s;
+}
+
+// r_j -= L_kj^T x_k for j < k.  grid = (k, b/64); 64 columns x 4 row groups,
+// reduced in a fixed order.
+__global__ void __launch_bounds__(256) k_gemv_T(Tiles tl, int k, double *__restrict__ v, const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    __shared__ double xs[1024];
+    __shared__ double red[4][64];
+    const int b = tl.b, j = (int)blockIdx.x, c0 = (int)blockIdx.y * 64;
+    const int tx = threadIdx.x & 63, g = threadIdx.x >> 6;
+    for (int c = threadIdx.x; c < b; c += 256) xs[c] = v[(size_t)k * b + c];
+    __syncthreads();
+    const double s = tl.is64(k, j) ? col_dot(tl.t64(k, j), b, c0 + tx, g, xs) : col_dot(tl.t32(k, j), b, c0 + tx, g, xs);
+    red[g][tx] = s;
+    __syncthreads();
+    if (g == 0) v[(size_t)j * b + c0 + tx] -= ((red[0][tx] + red[1][tx]) + red[2][tx]) + red[3][tx];
+}
+
+// Sigma x, row part: rows[i*b + r] = sum_{j <= i} Sigma_ij[r][:] . x_j over the
+// dense FP64 copy (diagonal tiles are stored whole).  grid = (T, b/8), warp per row.
+__global__ void __launch_bounds__(256) k_symv_rows(const double *__restrict__ sig, int b, int T,
+                                                   const double *__restrict__ x, double *__restrict__ out,
+                                                   const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    const int i = (int)blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = (int)blockIdx.y * 8 + warp;
+    const size_t bb = (size_t)b * b;
+    double s = 0.0;
+    for (int j = 0; j <= i; ++j) {
+        const double *row = sig + (size_t)tile_linear(i, j) * bb + (size_t)r * b;
+        const double *xj = x + (size_t)j * b;
+        for (int c = lane; c < b; c += 32) s = fma(row[c], xj[c], s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) out[(size_t)i * b + r] = s;
+}
+
+// Sigma x, column part: cols[i*b + c] = sum_{m > i} Sigma_mi[:, c] . x_m.
+// grid = (T, b/64); 64 columns x 4 row groups, fixed-order reduction.
+__global__ void __launch_bounds__(256) k_symv_cols(const double *__restrict__ sig, int b, int T,
+                                                   const double *__restrict__ x, double *__restrict__ out,
+                                                   const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    __shared__ double red[4][64];
+    const int i = (int)blockIdx.x, c0 = (int)blockIdx.y * 64;
+    const int tx = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const size_t bb = (size_t)b * b;
+    double s = 0.0;
+    for (int m = i + 1; m < T; ++m) {
+        const double *A = sig + (size_t)tile_linear(m, i) * bb + c0 + tx;
+        const double *xm = x + (size_t)m * b;
+        for (int r = g; r < b; r += 4) s = fma(A[(size_t)r * b], xm[r], s);
+    }
+    red[g][tx] = s;
+    __syncthreads();
+    if (g == 0) out[(size_t)i * b + c0 + tx] = ((red[0][tx] + red[1][tx]) + red[2][tx]) + red[3][tx];
+}
+
+// res = z - (rows + cols); d = res (the right-hand side of the correction solve)
+__global__ void k_residual(const double *__restrict__ zp, const double *__restrict__ rows,
+                           const double *__restrict__ cols, double *__restrict__ d, int64_t npad, const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < npad) d[i] = zp[i] - (rows[i] + cols[i]);
+}
+
+__global__ void k_axpy(double *__restrict__ x, const double *__restrict__ d, int64_t npad, const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < npad) x[i] += d[i];
+}
+
+__global__ void k_copy(double *__restrict__ dst, const double *__restrict__ src, int64_t npad)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < npad) dst[i] = src[i];
+}
+
+// l from log-det partials, quad0 = y.y (partials) and quad = z.x (fixed order).
+__global__ void __launch_bounds__(1024) k_finalize_mixed(const double *__restrict__ partials, int T,
+                                                         const double *__restrict__ zp, const double *__restrict__ x,
+                                                         int64_t npad, int64_t n, int refined, DevStatus *st)
+{
+    __shared__ double red[1024];
+    const int tid = threadIdx.x;
+    double a = 0.0, q0 = 0.0, q = 0.0;
+    for (int t = tid; t < T; t += 1024) {
+        a += partials[t];
+        q0 += partials[T + t];
+    }
+    for (int64_t i = tid; i < npad; i += 1024) q = fma(zp[i], x[i], q);
+    double vals[3] = {a, q0, q};
+    double tot[3];
+    for (int v = 0; v < 3; ++v) {
+        red[tid] = vals[v];
+        __syncthreads();
+        for (int s = 512; s > 0; s >>= 1) {
+            if (tid < s) red[tid] += red[tid + s];
+            __syncthreads();
+        }
+        tot[v] = red[0];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (mfailed(st)) {
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            st->result[0] = st->result[1] = st->result[2] = st->result[3] = nan;
+        } else {
+            const double logdet = 2.0 * tot[0];
+            const double quad = refined ? tot[2] : tot[1];
+            st->result[0] = -0.5 * quad - 0.5 * logdet - 0.5 * (double)n * 1.8378770664093454836;
+            st->result[1] = logdet;
+            st->result[2] = quad;
+            st->result[3] = tot[1];
+        }
+    }
+}
+
+cudaError_t backward_solve(const Tiles &tl, double *v, const DevStatus *st, cudaStream_t s, KernelTimer *kt)
+{
+    for (int k = tl.T - 1; k >= 0; --k) {
+        EGS_LAUNCH(kt, KC_TRSV, s, k_trsv_diag_T<<<1, tl.b, 0, s>>>(tl, k, v, st));
+        if (k > 0) EGS_LAUNCH(kt, KC_TRSV, s, k_gemv_T<<<dim3((unsigned)k, (unsigned)(tl.b / 64)), 256, 0, s>>>(tl, k, v, st));
+    }
+    return cudaGetLastError();
+}
+
+template <int FMT>
+cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap &ma, const CUtensorMap &mbm, DevStatus *st,
+                         cudaStream_t s, KernelTimer *kt)
+{
+    const Tiles &tl = mb.tl;
+    const int T = tl.T, b = tl.b;
+    for (int k = 0; k < T; ++k) {
+        cudaError_t e = launch_potrf_diag(tl, k, st, s, kt);
+        if (e != cudaSuccess) return e;
+        if (k + 1 == T) break;
+        const int nb = (tl.band - 1 < T - k - 1) ? tl.band - 1 : T - k - 1;  // FP64 rows below k
+        const int nf = T - k - 1 - nb;                                       // FP32 rows
+        e = launch_trsm_f64(tl, k, nb, st, s, kt);
+        if (e != cudaSuccess) return e;
+        // updates whose two operands are FP64 band tiles stay in FP64 (they
+        // carry the nearest-neighbour entries that set the diagonal pivots)
+        e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, s, kt);
+        if (e != cudaSuccess) return e;
+        if (nb > 0) {
+            const size_t total = (size_t)nb * tl.bb();
+            const unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+            EGS_LAUNCH(kt, KC_TRSM, s, k_panel_from_f64<FMT><<<blocks, 256, 0, s>>>(tl, k, nb, mb.panel, st));
+        }
+        if (nf > 0)
+            EGS_LAUNCH(kt, KC_TRSM, s,
+                       k_trsm_panel_f32<FMT><<<dim3((unsigned)nf, (unsigned)(b / 64)), 256, 0, s>>>(tl, k, k + 1 + nb,
+                                                                                                    mb.panel, st));
+        e = launch_update_tc(ma, mbm, FMT, tl, k, mb.err, s, kt);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, int64_t n, const egs_matern_params &P,
+                             int fmt, int refine, const MixedBuffers &mb, DevStatus *st, cudaStream_t s, KernelTimer *kt,
+                             cudaEvent_t *ev)
+{
+    const Tiles &tl = mb.tl;
+    const int b = tl.b, T = tl.T;
+    const int64_t npad = (int64_t)T * b;
+    const unsigned vb = (unsigned)((npad + 255) / 256);
+    if (ev) cudaEventRecord(ev[0], s);
+    cudaError_t e = launch_matern_tiles(X, Y, n, tl, P, mb.sig, s, kt);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s);
+    CUtensorMap ma, mbm;
+    e = make_panel_maps(mb.panel, fmt, b, T, &ma, &mbm);
+    if (e != cudaSuccess) return e;
+    e = (fmt == 2) ? factor_mixed<2>(mb, ma, mbm, st, s, kt) : factor_mixed<1>(mb, ma, mbm, st, s, kt);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[2], s);
+    // y = L^-1 z (log-det and y.y partials), x = L^-T y
+    e = launch_pad_vector(z, n, mb.zp, npad, s, kt);
+    if (e != cudaSuccess) return e;
+    EGS_LAUNCH(kt, KC_OTHER, s, k_copy<<<vb, 256, 0, s>>>(mb.y, mb.zp, npad));
+    e = launch_forward_solve(tl, mb.y, mb.partials, st, s, kt);
+    if (e != cudaSuccess) return e;
+    EGS_LAUNCH(kt, KC_OTHER, s, k_copy<<<vb, 256, 0, s>>>(mb.x, mb.y, npad));
+    e = backward_solve(tl, mb.x, st, s, kt);
+    if (e != cudaSuccess) return e;
+    for (int it = 0; it < refine; ++it) {
+        EGS_LAUNCH(kt, KC_OTHER, s,
+                   k_symv_rows<<<dim3((unsigned)T, (unsigned)(b / 8)), 256, 0, s>>>(mb.sig, b, T, mb.x, mb.rows, st));
+        EGS_LAUNCH(kt, KC_OTHER, s,
+                   k_symv_cols<<<dim3((unsigned)T, (unsigned)(b / 64)), 256, 0, s>>>(mb.sig, b, T, mb.x, mb.cols, st));
+        EGS_LAUNCH(kt, KC_OTHER, s, k_residual<<<vb, 256, 0, s>>>(mb.zp, mb.rows, mb.cols, mb.d, npad, st));
+        e = launch_forward_solve(tl, mb.d, nullptr, st, s, kt);
+        if (e != cudaSuccess) return e;
+        e = backward_solve(tl, mb.d, st, s, kt);
+        if (e != cudaSuccess) return e;
+        EGS_LAUNCH(kt, KC_OTHER, s, k_axpy<<<vb, 256, 0, s>>>(mb.x, mb.d, npad, st));
+    }
+    EGS_LAUNCH(kt, KC_OTHER, s,
+               k_finalize_mixed<<<1, 1024, 0, s>>>(mb.partials, T, mb.zp, mb.x, npad, n, refine > 0 ? 1 : 0, st));
+    if (ev) cudaEventRecord(ev[3], s);
+    return cudaGetLastError();
+}
+
+}  // namespace egs

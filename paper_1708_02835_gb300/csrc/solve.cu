@@ -42,15 +42,14 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 }
 
 // Diagonal block: y_k = L_kk^-1 r_k in place, blockDim.x = b threads.
-__global__ void __launch_bounds__(1024) k_trsv_diag_f64(const double *__restrict__ tiles, int b, int k,
-                                                        double *__restrict__ zpad, double *__restrict__ partials,
-                                                        int T, DevStatus *st)
+__global__ void __launch_bounds__(1024) k_trsv_diag_f64(Tiles tl, int k, double *__restrict__ zpad,
+                                                        double *__restrict__ partials, DevStatus *st)
 {
     if (failed_s(st)) return;
     __shared__ double yv[1024];
     __shared__ double red[1024];
-    const int i = threadIdx.x;
-    const double *L = tiles + (size_t)tile_linear(k, k) * (size_t)b * (size_t)b;
+    const int i = threadIdx.x, b = tl.b, T = tl.T;
+    const double *L = tl.t64(k, k);
     const double *Li = L + (size_t)i * b;
     double r = zpad[(size_t)k * b + i];
     for (int c = 0; c < b; ++c) {
@@ -60,38 +59,47 @@ __global__ void __launch_bounds__(1024) k_trsv_diag_f64(const double *__restrict
     }
     const double y = yv[i];
     zpad[(size_t)k * b + i] = y;
-    const double ld = block_sum(log(Li[i]), red);
-    __syncthreads();
-    const double q = block_sum(y * y, red);
-    if (i == 0) {
-        partials[k] = ld;
-        partials[T + k] = q;
+    if (partials) {
+        const double ld = block_sum(log(Li[i]), red);
+        __syncthreads();
+        const double q = block_sum(y * y, red);
+        if (i == 0) {
+            partials[k] = ld;
+            partials[T + k] = q;
+        }
+    }
+}
+
+template <typename E>
+__device__ __forceinline__ void gemv_rows(const E *__restrict__ A, int b, int r0, const double *ys,
+                                          double *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rr = 0; rr < 8; ++rr) {
+        const int r = r0 + warp * 8 + rr;
+        const E *row = A + (size_t)r * b;
+        double s = 0.0;
+        for (int c = lane; c < b; c += 32) s = fma((double)row[c], ys[c], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) out[r] -= s;
     }
 }
 
 // Panel: z_m -= L_mk y_k for m = k+1..T-1.  grid = (T-k-1, b/64), 256
 // threads; each warp owns 8 rows and reduces each row's dot product with a
-// fixed shuffle tree.
-__global__ void __launch_bounds__(256) k_gemv_panel_f64(const double *__restrict__ tiles, int b, int k,
-                                                        double *__restrict__ zpad, DevStatus *st)
+// fixed shuffle tree.  Tiles may be FP64 or (mixed mode) FP32.
+__global__ void __launch_bounds__(256) k_gemv_panel(Tiles tl, int k, double *__restrict__ zpad, DevStatus *st)
 {
     if (failed_s(st)) return;
     extern __shared__ double ys[];
+    const int b = tl.b;
     const int m = k + 1 + (int)blockIdx.x;
     const int r0 = (int)blockIdx.y * 64;
     for (int c = threadIdx.x; c < b; c += 256) ys[c] = zpad[(size_t)k * b + c];
     __syncthreads();
-    const double *A = tiles + (size_t)tile_linear(m, k) * (size_t)b * (size_t)b;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rr = 0; rr < 8; ++rr) {
-        const int r = r0 + warp * 8 + rr;
-        const double *row = A + (size_t)r * b;
-        double s = 0.0;
-        for (int c = lane; c < b; c += 32) s = fma(row[c], ys[c], s);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) zpad[(size_t)m * b + r] -= s;
-    }
+    if (tl.is64(m, k)) gemv_rows(tl.t64(m, k), b, r0, ys, zpad + (size_t)m * b);
+    else gemv_rows(tl.t32(m, k), b, r0, ys, zpad + (size_t)m * b);
 }
 
 // l = -1/2 quad - 1/2 logdet - n/2 log(2 pi) from the per-tile partials.
@@ -126,19 +134,33 @@ cudaError_t launch_pad_vector(const double *z, int64_t n, double *zpad, int64_t 
     return cudaGetLastError();
 }
 
+cudaError_t launch_forward_solve(const Tiles &tl, double *zpad, double *partials, DevStatus *st, cudaStream_t s,
+                                 KernelTimer *kt)
+{
+    const int b = tl.b, T = tl.T;
+    for (int k = 0; k < T; ++k) {
+        EGS_LAUNCH(kt, KC_TRSV, s, k_trsv_diag_f64<<<1, b, 0, s>>>(tl, k, zpad, partials, st));
+        if (k + 1 < T)
+            EGS_LAUNCH(kt, KC_TRSV, s,
+                       k_gemv_panel<<<dim3((unsigned)(T - k - 1), (unsigned)(b / 64)), 256, (size_t)b * sizeof(double),
+                                      s>>>(tl, k, zpad, st));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double *partials, int T, int64_t n, DevStatus *st, cudaStream_t s, KernelTimer *kt)
+{
+    EGS_LAUNCH(kt, KC_OTHER, s, k_finalize<<<1, 256, 0, s>>>(partials, T, n, st));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_trsv_tiles_f64(const double *tiles, const TileGeom &g, double *zpad, double *partials,
                                   DevStatus *st, cudaStream_t s, KernelTimer *kt)
 {
-    const int b = g.b, T = g.T;
-    for (int k = 0; k < T; ++k) {
-        EGS_LAUNCH(kt, KC_TRSV, s, k_trsv_diag_f64<<<1, b, 0, s>>>(tiles, b, k, zpad, partials, T, st));
-        if (k + 1 < T)
-            EGS_LAUNCH(kt, KC_TRSV, s,
-                       k_gemv_panel_f64<<<dim3((unsigned)(T - k - 1), (unsigned)(b / 64)), 256,
-                                          (size_t)b * sizeof(double), s>>>(tiles, b, k, zpad, st));
-    }
-    EGS_LAUNCH(kt, KC_OTHER, s, k_finalize<<<1, 256, 0, s>>>(partials, T, g.n, st));
-    return cudaGetLastError();
+    const Tiles tl{const_cast<double *>(tiles), nullptr, g.b, g.T, g.T};
+    cudaError_t e = launch_forward_solve(tl, zpad, partials, st, s, kt);
+    if (e != cudaSuccess) return e;
+    return launch_finalize(partials, g.T, g.n, st, s, kt);
 }
 
 }  // namespace egs

@@ -1,0 +1,300 @@
+// Tensor-core (tcgen05) trailing update of the mixed-precision tile Cholesky,
+// the dominant contraction of Algorithm 2's dpotrf (Section 4.2, GEMM/SYRK
+// tasks):  C_mn -= P_m P_n^T  for every tile T > m >= n > k at step k, where
+// P_m is the factored panel tile (m, k) stored in the MMA operand format
+// (TF32-rounded FP32 or BF16) by the TRSM stage.
+//
+// One CTA computes a 128 x 256 block of one output tile: a single elected
+// thread of warp 0 streams 128-byte-wide K slices of the two operands into a
+// 4-stage shared-memory ring with TMA (128-byte swizzle); one thread of warp 1
+// issues tcgen05.mma (M = 128, N = 256) into a 256-column FP32 accumulator in
+// TMEM and releases each stage with tcgen05.commit; then all four warps read
+// the accumulator back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31)
+// and subtract it from the output tile, in FP64 for band tiles and FP32 for
+// the others.  No cluster multicast is used.
+#include "egs_internal.cuh"
+#include "tc_common.cuh"
+
+#include <cudaTypedefs.h>
+
+namespace egs {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, STAGES = 4;
+constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr uint32_t TMEM_COLS = 256;
+
+struct WorkItem {
+    int m, n;    // output tile (update) / unused (dense)
+    int rb, cb;  // 128-row block, 256-column block
+    int ya, yb;  // TMA row coordinates of the A and B boxes
+};
+
+// Trailing update of step k over the lower-tile storage.
+struct UpdateWork {
+    Tiles tl;
+    int k;
+    __device__ bool decode(int64_t bid, WorkItem &w) const
+    {
+        const int nrb = tl.b / BM, ncb = tl.b / BN, per = nrb * ncb;
+        const int64_t t = bid / per;
+        const int blk = (int)(bid % per);
+        int ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((int64_t)ii * (ii + 1) / 2 > t) --ii;
+        while ((int64_t)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
+        const int jj = (int)(t - (int64_t)ii * (ii + 1) / 2);
+        w.m = k + 1 + ii;
+        w.n = k + 1 + jj;
+        w.rb = blk / ncb;
+        w.cb = blk % ncb;
+        if (w.m - k < tl.band && w.n - k < tl.band) return false;         // FP64 band x band: done in FP64
+        if (w.m == w.n && w.cb * BN > w.rb * BM + BM - 1) return false;  // strictly above the diagonal
+        w.ya = (w.m - k - 1) * tl.b + w.rb * BM;
+        w.yb = (w.n - k - 1) * tl.b + w.cb * BN;
+        return true;
+    }
+    __device__ void store(const WorkItem &w, int r, int c0, const float (&v)[32]) const
+    {
+        const size_t row = (size_t)(w.rb * BM + r), col = (size_t)(w.cb * BN + c0);
+        if (tl.is64(w.m, w.n)) {
+            double *C = tl.t64(w.m, w.n) + row * tl.b + col;
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+                double2 c = *reinterpret_cast<double2 *>(C + i);
+                c.x -= (double)v[i];
+                c.y -= (double)v[i + 1];
+                *reinterpret_cast<double2 *>(C + i) = c;
+            }
+        } else {
+            float *C = tl.t32(w.m, w.n) + row * tl.b + col;
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
+                float4 c = *reinterpret_cast<float4 *>(C + i);
+                c.x -= v[i];
+                c.y -= v[i + 1];
+                c.z -= v[i + 2];
+                c.w -= v[i + 3];
+                *reinterpret_cast<float4 *>(C + i) = c;
+            }
+        }
+    }
+};
+
+// Plain C = A B^T (A: M x K, B: N x K, row-major), used to test the pipeline.
+struct DenseWork {
+    float *C;
+    int N;  // columns of C
+    int nrb, ncb;
+    __device__ bool decode(int64_t bid, WorkItem &w) const
+    {
+        w.rb = (int)(bid / ncb);
+        w.cb = (int)(bid % ncb);
+        w.m = w.n = 0;
+        w.ya = w.rb * BM;
+        w.yb = w.cb * BN;
+        return true;
+    }
+    __device__ void store(const WorkItem &w, int r, int c0, const float (&v)[32]) const
+    {
+        float *Cp = C + (size_t)(w.rb * BM + r) * N + w.cb * BN + c0;
+#pragma unroll
+        for (int i = 0; i < 32; i += 4) *reinterpret_cast<float4 *>(Cp + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    }
+};
+
+// FMT: 2 = TF32 (K-slice 8 per MMA), 1 = BF16 (K-slice 16 per MMA).
+template <int FMT, class Work>
+__global__ void __launch_bounds__(128, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Work work, int kchunks,
+          int *err)
+{
+    WorkItem wi;
+    if (!work.decode((int64_t)blockIdx.x, wi)) return;  // uniform across the CTA
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full[STAGES], empty[STAGES], accum;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ int last_chunk[STAGES];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+            last_chunk[s] = -1;
+        }
+        tc::mbar_init(&accum, 1);
+        abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, TMEM_COLS);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tacc = tmem_base;
+    constexpr int KELEMS = (FMT == 2) ? 32 : 64;  // elements per 128-byte row slice
+
+    if (warp == 0 && lane == 0) {
+        tc::prefetch_tmap(&mapA);
+        tc::prefetch_tmap(&mapB);
+        for (int c = 0; c < kchunks; ++c) {
+            const int s = c % STAGES;
+            const uint32_t ph = (uint32_t)(c / STAGES) & 1u;
+            if (!tc::mbar_wait(&empty[s], ph ^ 1u, &abort_flag)) break;
+            tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+            tc::tma_load_2d(&mapA, &full[s], smem + s * STAGE_BYTES, c * KELEMS, wi.ya);
+            tc::tma_load_2d(&mapB, &full[s], smem + s * STAGE_BYTES + A_BYTES, c * KELEMS, wi.yb);
+            last_chunk[s] = c;
+        }
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = tc::idesc_f32acc(BM, BN, FMT);
+        for (int c = 0; c < kchunks; ++c) {
+            const int s = c % STAGES;
+            const uint32_t ph = (uint32_t)(c / STAGES) & 1u;
+            if (!tc::mbar_wait(&full[s], ph, &abort_flag)) break;
+            tc::tc_fence_after();
+            const uint32_t a0 = tc::smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t b0 = a0 + A_BYTES;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t ad = tc::desc_sw128(a0 + 32 * j);
+                const uint64_t bd = tc::desc_sw128(b0 + 32 * j);
+                if (FMT == 2) tc::mma_tf32(tacc, ad, bd, idesc, (c | j) != 0);
+                else tc::mma_f16(tacc, ad, bd, idesc, (c | j) != 0);
+            }
+            tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(&accum);
+    }
+    __syncwarp();
+    const bool ok = tc::mbar_wait(&accum, 0, &abort_flag);
+    tc::tc_fence_after();
+    // warp-uniform decision: the TMEM loads below are .sync.aligned
+    if (__all_sync(0xffffffffu, ok && !abort_flag)) {
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+        for (int cc = 0; cc < BN / 32; ++cc) {
+            float v[32];
+            tc::tmem_ld32(tacc + lane_base + (uint32_t)(cc * 32), v);
+            work.store(wi, warp * 32 + lane, cc * 32, v);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0) {
+        // let every TMA load that was issued land before the CTA exits
+        for (int s = 0; s < STAGES; ++s)
+            if (last_chunk[s] >= 0) {
+                volatile int dummy = 0;
+                tc::mbar_wait(&full[s], (uint32_t)(last_chunk[s] / STAGES) & 1u, &dummy);
+            }
+        atomicExch(err, 1);
+    }
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tacc, TMEM_COLS);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D map over a row-major [rows][inner] array, box {128 bytes of K, box_rows}.
+cudaError_t make_map(CUtensorMap *m, const void *base, int fmt, uint64_t inner, uint64_t rows, uint32_t box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const uint32_t esz = (fmt == 2) ? 4 : 2;
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {inner * esz};
+    cuuint32_t box[2] = {128u / esz, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, fmt == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int FMT, class Work>
+cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const Work &w, int64_t blocks, int kchunks,
+                        int *err, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<FMT, Work>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<FMT, Work><<<(unsigned)blocks, 128, SMEM_BYTES, s>>>(ma, mb, w, kchunks, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Panel maps for the trailing update: the panel buffer holds rows
+// (T - 1) * b of K = b operand elements.
+cudaError_t make_panel_maps(const void *panel, int fmt, int b, int T, CUtensorMap *mapA, CUtensorMap *mapB)
+{
+    const uint64_t rows = (uint64_t)(T > 1 ? T - 1 : 1) * (uint64_t)b;
+    cudaError_t e = make_map(mapA, panel, fmt, (uint64_t)b, rows, BM);
+    if (e == cudaSuccess) e = make_map(mapB, panel, fmt, (uint64_t)b, rows, BN);
+    return e;
+}
+
+cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, int fmt, const Tiles &tl, int k,
+                             int *err, cudaStream_t s, KernelTimer *kt)
+{
+    const int64_t ntiles = (int64_t)(tl.T - k - 1) * (tl.T - k) / 2;
+    if (ntiles <= 0) return cudaSuccess;
+    const int64_t blocks = ntiles * (tl.b / BM) * (tl.b / BN);
+    UpdateWork w{tl, k};
+    const int kchunks = tl.b / (fmt == 2 ? 32 : 64);
+    cudaError_t e;
+    if (kt) kt->begin(KC_UPDATE, s);
+    if (fmt == 2) e = launch_gemm<2>(mapA, mapB, w, blocks, kchunks, err, s);
+    else e = launch_gemm<1>(mapA, mapB, w, blocks, kchunks, err, s);
+    if (kt) kt->end(KC_UPDATE, s);
+    return e;
+}
+
+}  // namespace egs
+
+using namespace egs;
+
+extern "C" egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, int32_t N, int32_t K, egs_precision p,
+                                       float *C, void *stream)
+{
+    if (M <= 0 || N <= 0 || K <= 0 || M % BM || N % BN || K % 64)
+        return set_error(EGS_ERR_ARG, "egs_tc_gemm_test: M %% 128, N %% 256, K %% 64 must be 0");
+    if (p != EGS_MIX_TF32 && p != EGS_MIX_BF16)
+        return set_error(EGS_ERR_ARG, "egs_tc_gemm_test: precision must be EGS_MIX_TF32 or EGS_MIX_BF16");
+    const int fmt = (p == EGS_MIX_TF32) ? 2 : 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUtensorMap ma, mb;
+    cudaError_t e = make_map(&ma, A, fmt, (uint64_t)K, (uint64_t)M, BM);
+    if (e == cudaSuccess) e = make_map(&mb, B, fmt, (uint64_t)K, (uint64_t)N, BN);
+    if (e != cudaSuccess) return set_error(EGS_ERR_CUDA, "egs_tc_gemm_test: tensor map encoding failed");
+    int *err = nullptr;
+    e = cudaMallocAsync((void **)&err, sizeof(int), s);
+    if (e != cudaSuccess) return set_error(EGS_ERR_OOM, "egs_tc_gemm_test: workspace");
+    cudaMemsetAsync(err, 0, sizeof(int), s);
+    DenseWork w{C, N, M / BM, N / BN};
+    const int kchunks = K / (fmt == 2 ? 32 : 64);
+    if (fmt == 2) e = launch_gemm<2>(ma, mb, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s);
+    else e = launch_gemm<1>(ma, mb, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(err, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error(EGS_ERR_CUDA, "egs_tc_gemm_test: %s", cudaGetErrorString(e));
+    if (herr) return set_error(EGS_ERR_TIMEOUT, "egs_tc_gemm_test: a pipeline wait timed out");
+    return EGS_OK;
+}

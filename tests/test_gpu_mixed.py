@@ -1,0 +1,92 @@
+"""Mixed precision (FP64 band, TF32 / BF16 off-band on tcgen05, one FP64
+refinement step of the quadratic form) against the FP64 CPU oracle.
+
+Stated bars per result (Eq. 1 assembled from the mixed factor's FP64
+log-determinant and the refined quadratic form):
+  TF32: |dl|/|l| <= 1e-6;  BF16: |dl|/|l| <= 5e-5 (BF16 keeps 8 significant
+  bits, so the off-band factor carries ~4e-3 relative rounding per entry).
+Single-precision off-band tiles cannot factor very smooth, long-range fields
+(condition numbers beyond 1/eps_FP32); there the mixed path must report
+EGS_ERR_NOT_PD cleanly rather than return a wrong number.
+With TF32 the refined quadratic form must be closer to the oracle's than the
+unrefined one (with BF16 one refinement step need not contract).
+"""
+import numpy as np
+import pytest
+
+import egs_inputs as ei
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"tf32": 1e-6, "bf16": 5e-5}
+
+
+@pytest.fixture(scope="module")
+def egs():
+    import paper_1708_02835_gb300 as m
+    m.load_library()
+    return m
+
+
+def _case(n, theta, seed):
+    p = ei.Problem(n=n, theta=theta, seed=seed)
+    locs = p.locations()
+    z = oracle.simulate_z(locs, theta, p.e())
+    return locs, z, oracle.loglik_lapack(locs, z, theta)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("n,theta,tile,band", [
+    (4096, (1.0, 0.1, 0.5), 256, 2),
+    (3000, (1.0, 0.05, 0.8), 256, 2),    # ragged tail, general nu
+    (4600, (1.5, 0.05, 0.6), 512, 2),    # tile 512 as at n = 102,400
+    (4096, (1.0, 0.1, 0.5), 256, 3),     # wider FP64 band
+])
+def test_mixed_loglik_vs_oracle(egs, prec, n, theta, tile, band):
+    from gpu_util import locs_dev, dev
+    locs, z, ref = _case(n, theta, 3)
+    ll, info = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, prec, tile=tile, band=band)
+    rel = abs(ll - ref["loglik"]) / abs(ref["loglik"])
+    print("%s n=%d rel l %.2e  logdet %.3e  quad %.2e (unrefined %.2e)" % (
+        prec, n, rel, info["logdet"] - ref["logdet"], abs(info["quad"] - ref["quad"]) / ref["quad"],
+        abs(info["quad_unrefined"] - ref["quad"]) / ref["quad"]))
+    assert info["band"] == band and info["refine_steps"] == 1
+    assert rel <= TOL[prec], rel
+    if prec == "tf32":
+        # one FP64 refinement step contracts when kappa * eps(factor) < 1; the
+        # BF16 factor is too inexact for that to hold on these fields
+        assert abs(info["quad"] - ref["quad"]) <= abs(info["quad_unrefined"] - ref["quad"]) + 1e-12 * ref["quad"]
+
+
+def test_mixed_smooth_field_reports_not_pd(egs):
+    from gpu_util import locs_dev, dev
+    n, theta = 3000, (1.0, 0.15, 1.3)
+    locs, z, ref = _case(n, theta, 3)
+    ll, _ = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "fp64", tile=256)
+    assert abs(ll - ref["loglik"]) <= 1e-10 * abs(ref["loglik"])
+    with pytest.raises(egs.NotPositiveDefinite):
+        egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "tf32", tile=256)
+
+
+def test_mixed_deterministic(egs):
+    from gpu_util import locs_dev, dev
+    n, theta = 3000, (1.0, 0.1, 0.5)
+    locs, z, _ = _case(n, theta, 5)
+    a = [egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "tf32", tile=256)[0] for _ in range(3)]
+    assert a[0] == a[1] == a[2]
+
+
+def test_mixed_small_n_falls_back_to_fp64(egs):
+    from gpu_util import locs_dev, dev
+    n, theta = 400, (1.0, 0.1, 0.5)
+    locs, z, ref = _case(n, theta, 1)
+    ll, info = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "tf32", tile=256)
+    assert abs(ll - ref["loglik"]) <= 1e-10 * abs(ref["loglik"])
+
+
+def test_mixed_tile_must_be_multiple_of_256(egs):
+    from gpu_util import locs_dev, dev
+    locs = ei.jittered_grid(1000)
+    with pytest.raises(egs.EgsError):
+        egs.egs_loglik_ex(locs_dev(locs), dev(np.ones(1000)), (1, 0.1, 0.5), 1000, "tf32", tile=320)
