@@ -171,6 +171,87 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
                          void *stream);
 
 /*
+ * Batched evaluation (independent problems: uneven n, own theta each).
+ *
+ * Each problem is Eq. 1 evaluated by Algorithm 2 exactly as egs_loglik does
+ * in EGS_FP64; the batch runs the tile algorithm of Section 4.2 for all
+ * problems at once: every kernel launch covers one step of every problem, so
+ * the whole batch is a few hundred launches, captured into a CUDA graph on the
+ * first egs_batch_run and replayed afterwards.
+ *
+ * egs_batch_create  plan for nprob problems of sizes n[0..nprob) with one tile
+ *                   size for the batch (0 = chosen from the largest n); owns
+ *                   all device memory of the batch (egs_batch_workspace_bytes).
+ * egs_batch_run     locs[i] (2 n[i] doubles, x then y) and z[i] (n[i]
+ *                   doubles), device or host memory; theta: nprob x 3 host
+ *                   doubles.  out[i] = l_i (NaN if problem i is not positive
+ *                   definite), per_status[i] its status (both nullable).
+ *                   Synchronises stream.  Returns EGS_ERR_NOT_PD if any
+ *                   problem failed (the others are still valid).
+ * egs_loglik_batched  create + run + destroy in one call.
+ * Only EGS_FP64 is built for batches.
+ */
+typedef struct egs_batch egs_batch;
+egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_precision p, egs_batch **out);
+egs_status egs_batch_run(egs_batch *batch, const double *const *locs, const double *const *z, const double *theta,
+                         double *out, egs_status *per_status, void *stream);
+egs_status egs_batch_destroy(egs_batch *batch);
+int32_t egs_batch_launches(const egs_batch *batch);     /* kernels per run (in the graph) */
+int32_t egs_batch_tile(const egs_batch *batch);
+size_t egs_batch_workspace_bytes(const egs_batch *batch);
+egs_status egs_loglik_batched(int32_t nprob, const int64_t *n, const double *const *locs, const double *const *z,
+                              const double *theta, egs_precision p, double *out, egs_status *per_status,
+                              void *stream);
+
+/*
+ * Serving loop: likelihood requests from concurrent optimisers.
+ *
+ * Fields (locations + measurements) are copied to the device once and stay
+ * resident.  Requests (field, theta, precision) enter a FIFO queue; a
+ * scheduler thread admits the head request as soon as an execution slot is
+ * free and its workspace fits in the HBM budget (resident fields plus
+ * workspaces in flight <= hbm_budget_bytes), and enqueues it on the slot's own
+ * stream, so requests that arrive while others run overlap with them on the
+ * GPU.  Each evaluation is exactly egs_loglik's (deterministic kernels), so a
+ * result is the same alone and in the mix.  Latency is measured from submit
+ * to completion on the host clock.
+ *   egs_serve_create    config: budget in bytes, 1..64 slots, tile/band for
+ *                       the evaluations (0 = defaults).
+ *   egs_serve_add_field locs (2n doubles, x then y) and z (n doubles), host or
+ *                       device; the server copies them.  EGS_ERR_OOM if the
+ *                       field does not fit in the budget.
+ *   egs_serve_submit    non-blocking; returns a ticket.
+ *   egs_serve_wait      timeout_ms < 0 waits forever; EGS_ERR_TIMEOUT if not
+ *                       done in time (the request stays queued / running);
+ *                       EGS_ERR_NOT_PD etc. from the evaluation.  A ticket is
+ *                       consumed by the successful or failed wait that
+ *                       returns its result.
+ *   egs_serve_stats     p50 / p99 / mean latency, throughput, counters.
+ *   egs_serve_destroy   drains in-flight work and frees everything.
+ */
+typedef struct egs_server egs_server;
+typedef struct {
+    size_t hbm_budget_bytes;
+    int32_t max_inflight;
+    int32_t tile;
+    int32_t band;
+    int32_t pad;
+} egs_serve_config;
+typedef struct {
+    double p50_ms, p99_ms, mean_ms, evals_per_s;
+    int64_t completed, failed, rejected, inflight_peak, queued;
+    size_t bytes_in_use;  /* fields + workspaces in flight now */
+    size_t bytes_peak;    /* maximum of bytes_in_use so far (<= the budget) */
+} egs_serve_stats_t;
+egs_status egs_serve_create(const egs_serve_config *cfg, egs_server **out);
+egs_status egs_serve_add_field(egs_server *server, const double *locs, const double *z, int64_t n, int64_t *field_id);
+egs_status egs_serve_submit(egs_server *server, int64_t field_id, const double theta[3], egs_precision p,
+                            int64_t *ticket);
+egs_status egs_serve_wait(egs_server *server, int64_t ticket, int32_t timeout_ms, double *out_loglik, egs_info *info);
+egs_status egs_serve_stats(egs_server *server, egs_serve_stats_t *stats);
+egs_status egs_serve_destroy(egs_server *server);
+
+/*
  * egs_tc_gemm_test - the tensor-core pipeline of the trailing update on its
  * own: C = A B^T with tcgen05.mma (FP32 accumulation in TMEM), operands
  * streamed by TMA.  Exposed so that the MMA/descriptor path can be checked in

@@ -49,6 +49,21 @@ class egs_opts(ctypes.Structure):
                 ("timing", ctypes.c_int32), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
+class egs_serve_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("band", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class egs_serve_stats(ctypes.Structure):
+    _fields_ = [("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("evals_per_s", ctypes.c_double), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("inflight_peak", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -81,6 +96,20 @@ def load_library(build_if_missing: bool = True):
         "egs_loglik": (c.c_int, [vp, vp, pd, i64, c.c_int, pd, c.POINTER(egs_info), vp]),
         "egs_loglik_ex": (c.c_int, [vp, vp, pd, i64, c.c_int, c.POINTER(egs_opts), pd, c.POINTER(egs_info), vp]),
         "egs_tc_gemm_test": (c.c_int, [vp, vp, i32, i32, i32, c.c_int, vp, vp]),
+        "egs_batch_create": (c.c_int, [i32, c.POINTER(i64), i32, c.c_int, c.POINTER(vp)]),
+        "egs_batch_run": (c.c_int, [vp, c.POINTER(vp), c.POINTER(vp), pd, pd, c.POINTER(c.c_int), vp]),
+        "egs_batch_destroy": (c.c_int, [vp]),
+        "egs_batch_launches": (i32, [vp]),
+        "egs_batch_tile": (i32, [vp]),
+        "egs_batch_workspace_bytes": (c.c_size_t, [vp]),
+        "egs_loglik_batched": (c.c_int, [i32, c.POINTER(i64), c.POINTER(vp), c.POINTER(vp), pd, c.c_int, pd,
+                                         c.POINTER(c.c_int), vp]),
+        "egs_serve_create": (c.c_int, [c.POINTER(egs_serve_config), c.POINTER(vp)]),
+        "egs_serve_add_field": (c.c_int, [vp, vp, vp, i64, c.POINTER(i64)]),
+        "egs_serve_submit": (c.c_int, [vp, i64, pd, c.c_int, c.POINTER(i64)]),
+        "egs_serve_wait": (c.c_int, [vp, i64, i32, pd, c.POINTER(egs_info)]),
+        "egs_serve_stats": (c.c_int, [vp, c.POINTER(egs_serve_stats)]),
+        "egs_serve_destroy": (c.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -203,3 +232,108 @@ def egs_tc_gemm_test(A, B, C, precision="tf32", stream=None):
     M, K = A.shape
     N = B.shape[0]
     _check(load_library().egs_tc_gemm_test(_ptr(A), _ptr(B), M, N, K, _prec(precision), _ptr(C), _stream(stream)))
+
+
+class egs_batch:
+    """A planned batch of independent problems (sizes fixed at creation)."""
+
+    def __init__(self, ns, tile: int = 0, precision="fp64"):
+        lib = load_library()
+        self.ns = [int(v) for v in ns]
+        arr = (ctypes.c_int64 * len(self.ns))(*self.ns)
+        h = ctypes.c_void_p()
+        _check(lib.egs_batch_create(len(self.ns), arr, int(tile), _prec(precision), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def launches(self) -> int:
+        return load_library().egs_batch_launches(self._h)
+
+    @property
+    def tile(self) -> int:
+        return load_library().egs_batch_tile(self._h)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return load_library().egs_batch_workspace_bytes(self._h)
+
+    def run(self, locs, z, thetas, stream=None, raise_on_not_pd=False):
+        """locs[i], z[i]: per-problem arrays (device tensors or host arrays);
+        thetas: nprob x 3.  Returns (loglik array, status array)."""
+        lib = load_library()
+        npb = len(self.ns)
+        lp = (ctypes.c_void_p * npb)(*[_ptr(a) for a in locs])
+        zp = (ctypes.c_void_p * npb)(*[_ptr(a) for a in z])
+        th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(npb, 3))
+        out = np.empty(npb)
+        stat = (ctypes.c_int * npb)()
+        st = lib.egs_batch_run(self._h, lp, zp, th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), stat, _stream(stream))
+        if st != EGS_OK and (st != EGS_ERR_NOT_PD or raise_on_not_pd):
+            _check(st)
+        return out, np.array(list(stat))
+
+    def close(self):
+        if self._h:
+            load_library().egs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def egs_loglik_batched(locs, z, thetas, ns, precision="fp64", stream=None):
+    """One-shot batched evaluation; returns (loglik array, status array)."""
+    b = egs_batch(ns, 0, precision)
+    try:
+        return b.run(locs, z, thetas, stream)
+    finally:
+        b.close()
+
+
+class egs_server:
+    """Serving loop (C ABI egs_serve_*): resident fields, budgeted admission."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 4, tile: int = 0, band: int = 0):
+        cfg = egs_serve_config(hbm_budget_bytes=int(hbm_budget_bytes), max_inflight=int(max_inflight),
+                               tile=int(tile), band=int(band), pad=0)
+        h = ctypes.c_void_p()
+        _check(load_library().egs_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def add_field(self, locs, z, n: int) -> int:
+        fid = ctypes.c_int64()
+        _check(load_library().egs_serve_add_field(self._h, _ptr(locs), _ptr(z), int(n), ctypes.byref(fid)))
+        return fid.value
+
+    def submit(self, field_id: int, theta, precision="fp64") -> int:
+        tp, _keep = _theta(theta)
+        t = ctypes.c_int64()
+        _check(load_library().egs_serve_submit(self._h, int(field_id), tp, _prec(precision), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        out = ctypes.c_double()
+        info = egs_info()
+        st = load_library().egs_serve_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(out), ctypes.byref(info))
+        _check(st)
+        return out.value, info.as_dict()
+
+    def stats(self) -> dict:
+        s = egs_serve_stats()
+        _check(load_library().egs_serve_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self._h:
+            load_library().egs_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -50,10 +50,6 @@ static egs_status check_theta(const double *theta)
     return EGS_OK;
 }
 
-// Workspace layout of one evaluation.
-struct Layout {
-    size_t tiles, locs, z, zpad, partials, status, total;
-};
 
 static Layout make_layout(const TileGeom &g)
 {
@@ -75,10 +71,6 @@ static Layout make_layout(const TileGeom &g)
     return L;
 }
 
-// Workspace layout of one mixed-precision evaluation.
-struct MixedLayout {
-    size_t f64, f32, sig, panel, locs, z, vec, partials, status, err, total;
-};
 
 static int mix_fmt(egs_precision p) { return p == EGS_MIX_TF32 ? 2 : 1; }
 
@@ -121,7 +113,103 @@ static void status_init(DevStatus *st, cudaStream_t s)
     cudaMemsetAsync(&st->timeout, 0, sizeof(DevStatus) - sizeof(unsigned long long), s);
 }
 
+int32_t default_tile(int64_t n, egs_precision p)
+{
+    if (mixed_p(p)) return n <= 16384 ? 256 : 512;
+    if (n <= 4096) return 128;
+    if (n <= 16384) return 256;
+    return 512;
+}
+
+egs_status eval_setup(int64_t n, const double *theta, egs_precision p, const egs_opts *opts, EvalSetup *es)
+{
+    if (n < 1) return set_error(EGS_ERR_ARG, "n = %lld must be >= 1", (long long)n);
+    egs_status sc = check_theta(theta);
+    if (sc != EGS_OK) return sc;
+    if (p != EGS_FP64 && !mixed_p(p)) return set_error(EGS_ERR_UNIMPLEMENTED, "precision %d not built", (int)p);
+    int32_t tile = (opts && opts->tile) ? opts->tile : default_tile(n, p);
+    if (!tile_ok(tile)) return set_error(EGS_ERR_ARG, "tile = %d must be a multiple of 64 in [64, 1024]", tile);
+    es->band = (opts && opts->band > 0) ? opts->band : 2;
+    es->refine = (opts && opts->refine) ? (opts->refine < 0 ? 0 : opts->refine) : 1;
+    if (mixed_p(p) && tile % 256 != 0)
+        return set_error(EGS_ERR_ARG, "mixed precision needs tile %% 256 == 0 (got %d)", tile);
+    es->p = p;
+    es->g = TileGeom{n, tile, (int)((n + tile - 1) / tile)};
+    es->mixed = mixed_p(p) && es->g.T > es->band;
+    es->L = make_layout(es->g);
+    es->ML = make_mixed_layout(es->g, es->band, p);
+    es->need = es->mixed ? es->ML.total : es->L.total;
+    es->locs_off = es->mixed ? es->ML.locs : es->L.locs;
+    es->z_off = es->mixed ? es->ML.z : es->L.z;
+    egs_matern_params_init(theta, &es->P);
+    return EGS_OK;
+}
+
+DevStatus *eval_status(const EvalSetup &es, char *ws) { return (DevStatus *)(ws + (es.mixed ? es.ML.status : es.L.status)); }
+
+cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double *dz, char *ws, cudaStream_t s,
+                         KernelTimer *kt, cudaEvent_t *ev)
+{
+    const TileGeom &g = es.g;
+    const int64_t n = g.n;
+    DevStatus *st = eval_status(es, ws);
+    status_init(st, s);
+    if (es.mixed) {
+        const size_t npad = (size_t)g.T * g.b;
+        MixedBuffers mb;
+        const MixedLayout &ML = es.ML;
+        mb.tl = Tiles{(double *)(ws + ML.f64), (float *)(ws + ML.f32), g.b, g.T, es.band};
+        mb.sig = (double *)(ws + ML.sig);
+        mb.panel = ws + ML.panel;
+        double *v = (double *)(ws + ML.vec);
+        const size_t stride = align256(npad * sizeof(double)) / sizeof(double);
+        mb.zp = v;
+        mb.y = v + stride;
+        mb.x = v + 2 * stride;
+        mb.d = v + 3 * stride;
+        mb.res = v + 4 * stride;
+        mb.rows = v + 5 * stride;
+        mb.cols = v + 6 * stride;
+        mb.partials = (double *)(ws + ML.partials);
+        mb.err = (int *)(ws + ML.err);
+        cudaMemsetAsync(mb.err, 0, sizeof(int), s);
+        return run_loglik_mixed(dlocs, dlocs + n, dz, n, es.P, mix_fmt(es.p), es.refine, mb, st, s, kt, ev);
+    }
+    double *tiles = (double *)(ws + es.L.tiles);
+    double *zpad = (double *)(ws + es.L.zpad);
+    double *partials = (double *)(ws + es.L.partials);
+    if (ev) cudaEventRecord(ev[0], s);
+    cudaError_t e = launch_matern_tiles_f64(dlocs, dlocs + n, g, es.P, tiles, s, kt);
+    if (e == cudaSuccess) {
+        if (ev) cudaEventRecord(ev[1], s);
+        e = launch_potrf_tiles_f64(tiles, g, st, s, kt);
+    }
+    if (e == cudaSuccess) {
+        if (ev) cudaEventRecord(ev[2], s);
+        e = launch_pad_vector(dz, n, zpad, (int64_t)g.T * g.b, s, kt);
+    }
+    if (e == cudaSuccess) e = launch_trsv_tiles_f64(tiles, g, zpad, partials, st, s, kt);
+    if (e == cudaSuccess && ev) cudaEventRecord(ev[3], s);
+    return e;
+}
+
+void fill_info(const EvalSetup &es, const DevStatus &h, egs_info *info)
+{
+    const int64_t fi = (h.fail_index == kNoFail) ? -1 : (int64_t)h.fail_index;
+    std::memset(info, 0, sizeof(*info));
+    info->loglik = h.result[0];
+    info->logdet = h.result[1];
+    info->quad = h.result[2];
+    info->fail_index = fi;
+    info->fail_tile = fi >= 0 ? fi / es.g.b : -1;
+    info->tile = es.g.b;
+    info->band = es.mixed ? es.band : es.g.T;
+    info->refine_steps = es.mixed ? es.refine : 0;
+    info->quad_unrefined = es.mixed ? h.result[3] : h.result[2];
+}
+
 }  // namespace egs
+
 
 using namespace egs;
 
@@ -131,13 +219,7 @@ const char *egs_last_error(void) { return g_err; }
 
 const char *egs_version(void) { return "egs 0.1 (sm_103a)"; }
 
-int32_t egs_default_tile(int64_t n, egs_precision p)
-{
-    if (mixed_p(p)) return n <= 16384 ? 256 : 512;
-    if (n <= 4096) return 128;
-    if (n <= 16384) return 256;
-    return 512;
-}
+int32_t egs_default_tile(int64_t n, egs_precision p) { return default_tile(n, p); }
 
 size_t egs_tiles_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band)
 {
@@ -149,7 +231,7 @@ size_t egs_tiles_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band)
 
 size_t egs_loglik_workspace_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band)
 {
-    if (tile == 0) tile = egs_default_tile(n, p);
+    if (tile == 0) tile = default_tile(n, p);
     if (band <= 0) band = 2;
     if (n < 1 || !tile_ok(tile)) return 0;
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
@@ -241,98 +323,44 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
 {
     g_err[0] = 0;
     if (out_loglik) *out_loglik = NAN;
-    if (n < 1) return set_error(EGS_ERR_ARG, "n = %lld must be >= 1", (long long)n);
     if (!locs || !z) return set_error(EGS_ERR_ARG, "NULL pointer");
-    egs_status sc = check_theta(theta);
+    EvalSetup es;
+    egs_status sc = eval_setup(n, theta, p, opts, &es);
     if (sc != EGS_OK) return sc;
-    if (p != EGS_FP64 && !mixed_p(p)) return set_error(EGS_ERR_UNIMPLEMENTED, "precision %d not built", (int)p);
-    int32_t tile = (opts && opts->tile) ? opts->tile : egs_default_tile(n, p);
-    if (!tile_ok(tile)) return set_error(EGS_ERR_ARG, "tile = %d must be a multiple of 64 in [64, 1024]", tile);
-    const int band = (opts && opts->band > 0) ? opts->band : 2;
-    const int refine = (opts && opts->refine) ? (opts->refine < 0 ? 0 : opts->refine) : 1;
-    if (mixed_p(p) && tile % 256 != 0)
-        return set_error(EGS_ERR_ARG, "mixed precision needs tile %% 256 == 0 (got %d)", tile);
     const bool timing = opts && opts->timing;
     KernelTimer kt;
     kt.on = opts && opts->timing >= 2;
     cudaStream_t s = (cudaStream_t)stream;
-    TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
-    const bool mixed = mixed_p(p) && g.T > band;
-    Layout L = make_layout(g);
-    MixedLayout ML = make_mixed_layout(g, band, p);
-    const size_t need = mixed ? ML.total : L.total;
-    const size_t locs_off = mixed ? ML.locs : L.locs, z_off = mixed ? ML.z : L.z;
 
     char *ws = nullptr;
     bool own = false;
     cudaError_t e = cudaSuccess;
     if (opts && opts->workspace) {
-        if (opts->workspace_bytes < need)
-            return set_error(EGS_ERR_ARG, "workspace of %zu bytes < %zu needed", opts->workspace_bytes, need);
+        if (opts->workspace_bytes < es.need)
+            return set_error(EGS_ERR_ARG, "workspace of %zu bytes < %zu needed", opts->workspace_bytes, es.need);
         ws = (char *)opts->workspace;
     } else {
-        e = cudaMallocAsync((void **)&ws, need, s);
+        e = cudaMallocAsync((void **)&ws, es.need, s);
         if (e != cudaSuccess) return cuda_error(e, "egs_loglik workspace");
         own = true;
     }
-    double *tiles = (double *)(ws + L.tiles);
-    double *zpad = (double *)(ws + L.zpad);
-    double *partials = (double *)(ws + L.partials);
-    DevStatus *st = (DevStatus *)(ws + (mixed ? ML.status : L.status));
-
     const double *dlocs = locs, *dz = z;
     if (!is_device_ptr(locs)) {
-        dlocs = (const double *)(ws + locs_off);
+        dlocs = (const double *)(ws + es.locs_off);
         e = cudaMemcpyAsync((void *)dlocs, locs, (size_t)2 * n * sizeof(double), cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess && !is_device_ptr(z)) {
-        dz = (const double *)(ws + z_off);
+        dz = (const double *)(ws + es.z_off);
         e = cudaMemcpyAsync((void *)dz, z, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s);
     }
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (timing)
         for (int i = 0; i < 4; ++i) cudaEventCreate(&ev[i]);
-    egs_matern_params P;
-    egs_matern_params_init(theta, &P);
-    if (e == cudaSuccess) status_init(st, s);
-    if (e == cudaSuccess && mixed) {
-        const size_t npad = (size_t)g.T * g.b;
-        MixedBuffers mb;
-        mb.tl = Tiles{(double *)(ws + ML.f64), (float *)(ws + ML.f32), g.b, g.T, band};
-        mb.sig = (double *)(ws + ML.sig);
-        mb.panel = ws + ML.panel;
-        double *v = (double *)(ws + ML.vec);
-        const size_t stride = align256(npad * sizeof(double)) / sizeof(double);
-        mb.zp = v;
-        mb.y = v + stride;
-        mb.x = v + 2 * stride;
-        mb.d = v + 3 * stride;
-        mb.res = v + 4 * stride;
-        mb.rows = v + 5 * stride;
-        mb.cols = v + 6 * stride;
-        mb.partials = (double *)(ws + ML.partials);
-        mb.err = (int *)(ws + ML.err);
-        cudaMemsetAsync(mb.err, 0, sizeof(int), s);
-        e = run_loglik_mixed(dlocs, dlocs + n, dz, n, P, mix_fmt(p), refine, mb, st, s, &kt, timing ? ev : nullptr);
-    } else if (e == cudaSuccess) {
-        if (timing) cudaEventRecord(ev[0], s);
-        e = launch_matern_tiles_f64(dlocs, dlocs + n, g, P, tiles, s, &kt);
-        if (e == cudaSuccess) {
-            if (timing) cudaEventRecord(ev[1], s);
-            e = launch_potrf_tiles_f64(tiles, g, st, s, &kt);
-        }
-        if (e == cudaSuccess) {
-            if (timing) cudaEventRecord(ev[2], s);
-            e = launch_pad_vector(dz, n, zpad, (int64_t)g.T * g.b, s, &kt);
-        }
-        if (e == cudaSuccess) e = launch_trsv_tiles_f64(tiles, g, zpad, partials, st, s, &kt);
-        if (e == cudaSuccess && timing) cudaEventRecord(ev[3], s);
-    }
-    int herr = 0;
-    if (e == cudaSuccess && mixed)
-        e = cudaMemcpyAsync(&herr, ws + ML.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = eval_enqueue(es, dlocs, dz, ws, s, &kt, timing ? ev : nullptr);
     DevStatus h;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
+    int herr = 0;
+    if (e == cudaSuccess && es.mixed) e = cudaMemcpyAsync(&herr, ws + es.ML.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, eval_status(es, ws), sizeof(h), cudaMemcpyDeviceToHost, s);
     if (own) cudaFreeAsync(ws, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     float ms[3] = {0, 0, 0};
@@ -343,18 +371,9 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
     }
     if (e != cudaSuccess) return cuda_error(e, "egs_loglik");
     if (herr) return set_error(EGS_ERR_TIMEOUT, "egs_loglik: a tensor-core pipeline wait timed out");
-    const int64_t fi = (h.fail_index == kNoFail) ? -1 : (int64_t)h.fail_index;
     if (info) {
-        info->loglik = h.result[0];
-        info->logdet = h.result[1];
-        info->quad = h.result[2];
-        info->fail_index = fi;
-        info->fail_tile = fi >= 0 ? fi / tile : -1;
-        info->tile = tile;
-        info->band = mixed ? band : g.T;
+        fill_info(es, h, info);
         info->launches = kt.launches;
-        info->refine_steps = mixed ? refine : 0;
-        info->quad_unrefined = mixed ? h.result[3] : h.result[2];
         info->ms_generate = ms[0];
         info->ms_factor = ms[1];
         info->ms_solve = ms[2];
@@ -364,8 +383,9 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
         info->ms_update = kt.ms(KC_UPDATE);
         info->ms_trsv = kt.ms(KC_TRSV);
     }
+    const int64_t fi = (h.fail_index == kNoFail) ? -1 : (int64_t)h.fail_index;
     if (fi >= 0) return set_error(EGS_ERR_NOT_PD, "not positive definite at row %lld (tile %lld)", (long long)fi,
-                                  (long long)(fi / tile));
+                                  (long long)(fi / es.g.b));
     if (out_loglik) *out_loglik = h.result[0];
     return EGS_OK;
 }

@@ -1,0 +1,500 @@
+// Batched evaluation of many independent likelihood problems (uneven n, own
+// theta each) in FP64: the same tile algorithm as the single-problem path
+// (Algorithm 2 with the tile Cholesky of Section 4.2), but every kernel
+// launch covers one step of *all* problems at once.  A launch's work items
+// are the concatenation of every problem's items for that step; the CTA finds
+// its problem by binary search in a per-launch prefix table, so a batch of
+// 512 problems with tiles of 128 needs a few hundred launches in total, and
+// the whole sequence is captured once into a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "blocks.cuh"
+#include "matern.cuh"
+
+namespace egs {
+
+struct BatchProblem {
+    const double *X, *Y, *z;
+    int64_t n;
+    int T, pad;
+    double *tiles;     // T(T+1)/2 lower tiles of b x b
+    double *zpad;      // T*b
+    double *partials;  // 2T
+    DevStatus *st;
+    const egs_matern_params *P;
+};
+
+struct BatchArgs {
+    const BatchProblem *probs;
+    const int64_t *prefix;  // nprob + 1 item offsets for this launch
+    int nprob, b;
+};
+
+// Largest p with prefix[p] <= bid (that problem owns item bid).
+__device__ __forceinline__ int find_problem(const BatchArgs &a, int64_t bid, int64_t &local)
+{
+    int lo = 0, hi = a.nprob;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a.prefix[mid] <= bid) lo = mid;
+        else hi = mid;
+    }
+    local = bid - a.prefix[lo];
+    return lo;
+}
+
+__device__ __forceinline__ Tiles dense_tiles(const BatchProblem &p, int b) { return Tiles{p.tiles, nullptr, b, p.T, p.T}; }
+
+// Matern tiles: item = (tile, 64 x 64 sub-block).
+__global__ void __launch_bounds__(256) kb_gen(BatchArgs a)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    __shared__ egs_matern_params Ps;
+    {
+        const double *s = reinterpret_cast<const double *>(pr.P);
+        double *d = reinterpret_cast<double *>(&Ps);
+        for (int i = threadIdx.x; i < (int)(sizeof(egs_matern_params) / sizeof(double)); i += blockDim.x) d[i] = s[i];
+        __syncthreads();
+    }
+    const int b = a.b, nsub = b >> 6;
+    const int64_t t = local / (nsub * nsub);
+    const int sub = (int)(local % (nsub * nsub));
+    int ti, tj;
+    tri_decode(t, ti, tj);
+    const int sr = sub / nsub, sc = sub % nsub;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    const int64_t n = pr.n;
+    const int64_t gj = (int64_t)tj * b + sc * 64 + tx;
+    const double xj = gj < n ? pr.X[gj] : 0.0, yj = gj < n ? pr.Y[gj] : 0.0;
+    double *tile = pr.tiles + (size_t)t * b * b;
+    for (int rr = 0; rr < 16; ++rr) {
+        const int r = sr * 64 + ty + 4 * rr;
+        const int64_t gi = (int64_t)ti * b + r;
+        double v;
+        if (gi >= n || gj >= n) v = (gi == gj) ? 1.0 : 0.0;
+        else if (gi == gj) v = Ps.th1;
+        else {
+            const double dx = pr.X[gi] - xj, dy = pr.Y[gi] - yj;
+            v = matern_eval(&Ps, sqrt(fma(dx, dx, dy * dy)) * Ps.inv_th2);
+        }
+        tile[(size_t)r * b + sc * 64 + tx] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) kb_potrf_sub(BatchArgs a, int k, int p)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    __shared__ double pan[kIB * (kPW + 1)];
+    const int b = a.b;
+    double *A = dense_tiles(pr, b).t64(k, k) + (size_t)p * b + p;
+    if (!potrf_block(A, kIB, b, (int64_t)k * b + p, pr.st, pan)) return;
+    for (int e = threadIdx.x; e < kIB * (b - p - kIB); e += 256) {
+        const int r = e / (b - p - kIB), c = e % (b - p - kIB);
+        A[(size_t)r * b + kIB + c] = 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) kb_trsm_sub(BatchArgs a, int k, int p)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    const int b = a.b;
+    double *A = dense_tiles(pr, b).t64(k, k);
+    const int r0 = p + kIB + 64 * (int)local;
+    trsm_rows<64>(A + (size_t)p * b + p, b, A + (size_t)r0 * b + p, b, kIB);
+}
+
+__global__ void __launch_bounds__(256) kb_syrk_sub(BatchArgs a, int k, int p)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    const int b = a.b;
+    double *A = dense_tiles(pr, b).t64(k, k);
+    int bi, bj;
+    tri_decode(local, bi, bj);
+    const int q = p + kIB;
+    const int ri = q + 64 * bi, rj = q + 64 * bj;
+    gemm_sub64(A + (size_t)ri * b + p, b, A + (size_t)rj * b + p, b, kIB, A + (size_t)ri * b + rj, b);
+}
+
+__global__ void __launch_bounds__(256) kb_trsm_panel(BatchArgs a, int k)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    const int b = a.b, per = b / 64;
+    const Tiles tl = dense_tiles(pr, b);
+    const int m = k + 1 + (int)(local / per);
+    const int r0 = (int)(local % per) * 64;
+    trsm_rows<64>(tl.t64(k, k), b, tl.t64(m, k) + (size_t)r0 * b, b, b);
+}
+
+__global__ void __launch_bounds__(256) kb_update(BatchArgs a, int k)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    const int b = a.b, nsub = b >> 6;
+    const Tiles tl = dense_tiles(pr, b);
+    int mm, nn;
+    tri_decode(local / (nsub * nsub), mm, nn);
+    const int sub = (int)(local % (nsub * nsub));
+    const int m = k + 1 + mm, nc = k + 1 + nn;
+    const int sr = sub / nsub, sc = sub % nsub;
+    if (m == nc && sc > sr) return;
+    gemm_sub64(tl.t64(m, k) + (size_t)sr * 64 * b, b, tl.t64(nc, k) + (size_t)sc * 64 * b, b, b,
+               tl.t64(m, nc) + (size_t)sr * 64 * b + sc * 64, b);
+}
+
+__global__ void kb_pad(BatchArgs a)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    const int64_t i = local * 256 + threadIdx.x;
+    if (i < (int64_t)pr.T * a.b) pr.zpad[i] = i < pr.n ? pr.z[i] : 0.0;
+}
+
+__global__ void __launch_bounds__(1024) kb_trsv_diag(BatchArgs a, int k)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    __shared__ double ldq[2];
+    trsv_fwd_tile(dense_tiles(pr, a.b).t64(k, k), a.b, pr.zpad + (size_t)k * a.b, ldq);
+    if (threadIdx.x == 0) {
+        pr.partials[k] = ldq[0];
+        pr.partials[pr.T + k] = ldq[1];
+    }
+}
+
+__global__ void __launch_bounds__(256) kb_gemv_panel(BatchArgs a, int k)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    extern __shared__ double ys[];
+    const int b = a.b, per = b / 64;
+    const int m = k + 1 + (int)(local / per);
+    const int r0 = (int)(local % per) * 64;
+    for (int c = threadIdx.x; c < b; c += 256) ys[c] = pr.zpad[(size_t)k * b + c];
+    __syncthreads();
+    gemv_rows(dense_tiles(pr, b).t64(m, k), b, r0, ys, pr.zpad + (size_t)m * b);
+}
+
+__global__ void __launch_bounds__(256) kb_finalize(BatchArgs a)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    __shared__ double red[256];
+    double s = 0.0, q = 0.0;
+    for (int t = threadIdx.x; t < pr.T; t += 256) {
+        s += pr.partials[t];
+        q += pr.partials[pr.T + t];
+    }
+    const double lsum = block_sum(s, red);
+    __syncthreads();
+    const double qsum = block_sum(q, red);
+    if (threadIdx.x == 0) {
+        DevStatus *st = pr.st;
+        if (failed(st)) {
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            st->result[0] = st->result[1] = st->result[2] = nan;
+        } else {
+            const double logdet = 2.0 * lsum;
+            st->result[0] = -0.5 * qsum - 0.5 * logdet - 0.5 * (double)pr.n * 1.8378770664093454836;
+            st->result[1] = logdet;
+            st->result[2] = qsum;
+        }
+    }
+}
+
+}  // namespace egs
+
+// ---------------------------------------------------------------------------
+// Host side: plan, graph capture and the C ABI.
+// ---------------------------------------------------------------------------
+using namespace egs;
+
+struct egs_batch {
+    int nprob = 0, b = 0;
+    std::vector<int64_t> n;
+    std::vector<int> T;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    BatchProblem *d_probs = nullptr;
+    egs_matern_params *d_params = nullptr;
+    DevStatus *d_status = nullptr;
+    int64_t *d_prefix = nullptr;
+    double *d_inputs = nullptr;  // staged locations and z (3 n per problem)
+    std::vector<size_t> in_off;  // offset of problem p's inputs in d_inputs (doubles)
+    BatchProblem *h_probs = nullptr;     // pinned
+    egs_matern_params *h_params = nullptr;  // pinned
+    DevStatus *h_status = nullptr;          // pinned
+    struct Launch {
+        int kind, k, p;
+        size_t prefix_off;
+        int64_t items;
+    };
+    std::vector<Launch> launches;
+    cudaStream_t cs = nullptr;  // capture / replay stream
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int launches_per_run = 0;
+};
+
+namespace {
+
+enum { L_GEN, L_POTRF, L_TRSM_SUB, L_SYRK_SUB, L_TRSM, L_UPDATE, L_PAD, L_TRSV, L_GEMV, L_FINAL };
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void plan_launches(egs_batch *B, std::vector<int64_t> &prefix)
+{
+    const int b = B->b, nsub = b / 64, np = B->nprob;
+    int Tmax = 0;
+    for (int t : B->T) Tmax = std::max(Tmax, t);
+    auto add = [&](int kind, int k, int p, auto count) {
+        B->launches.push_back({kind, k, p, prefix.size(), 0});
+        int64_t acc = 0;
+        for (int q = 0; q < np; ++q) {
+            prefix.push_back(acc);
+            acc += count(q);
+        }
+        prefix.push_back(acc);
+        B->launches.back().items = acc;
+    };
+    add(L_GEN, 0, 0, [&](int q) { return (int64_t)B->T[q] * (B->T[q] + 1) / 2 * nsub * nsub; });
+    for (int k = 0; k < Tmax; ++k) {
+        for (int p = 0; p < b; p += kIB) {
+            const int64_t nrest = (b - p - kIB) / 64;
+            add(L_POTRF, k, p, [&](int q) { return (int64_t)(B->T[q] > k ? 1 : 0); });
+            if (nrest > 0) {
+                add(L_TRSM_SUB, k, p, [&](int q) { return B->T[q] > k ? nrest : (int64_t)0; });
+                add(L_SYRK_SUB, k, p, [&](int q) { return B->T[q] > k ? nrest * (nrest + 1) / 2 : (int64_t)0; });
+            }
+        }
+        add(L_TRSM, k, 0, [&](int q) { return B->T[q] > k + 1 ? (int64_t)(B->T[q] - k - 1) * (b / 64) : (int64_t)0; });
+        add(L_UPDATE, k, 0, [&](int q) {
+            const int64_t r = B->T[q] - k - 1;
+            return r > 0 ? r * (r + 1) / 2 * nsub * nsub : (int64_t)0;
+        });
+    }
+    add(L_PAD, 0, 0, [&](int q) { return ((int64_t)B->T[q] * b + 255) / 256; });
+    for (int k = 0; k < Tmax; ++k) {
+        add(L_TRSV, k, 0, [&](int q) { return (int64_t)(B->T[q] > k ? 1 : 0); });
+        add(L_GEMV, k, 0, [&](int q) { return B->T[q] > k + 1 ? (int64_t)(B->T[q] - k - 1) * (b / 64) : (int64_t)0; });
+    }
+    add(L_FINAL, 0, 0, [&](int) { return (int64_t)1; });
+}
+
+cudaError_t enqueue_all(egs_batch *B, cudaStream_t s)
+{
+    int count = 0;
+    for (const auto &L : B->launches) {
+        if (L.items <= 0) continue;
+        BatchArgs a{B->d_probs, B->d_prefix + L.prefix_off, B->nprob, B->b};
+        const unsigned g = (unsigned)L.items;
+        switch (L.kind) {
+        case L_GEN: kb_gen<<<g, 256, 0, s>>>(a); break;
+        case L_POTRF: kb_potrf_sub<<<g, 256, 0, s>>>(a, L.k, L.p); break;
+        case L_TRSM_SUB: kb_trsm_sub<<<g, 256, 0, s>>>(a, L.k, L.p); break;
+        case L_SYRK_SUB: kb_syrk_sub<<<g, 256, 0, s>>>(a, L.k, L.p); break;
+        case L_TRSM: kb_trsm_panel<<<g, 256, 0, s>>>(a, L.k); break;
+        case L_UPDATE: kb_update<<<g, 256, 0, s>>>(a, L.k); break;
+        case L_PAD: kb_pad<<<g, 256, 0, s>>>(a); break;
+        case L_TRSV: kb_trsv_diag<<<g, B->b, 0, s>>>(a, L.k); break;
+        case L_GEMV: kb_gemv_panel<<<g, 256, (size_t)B->b * sizeof(double), s>>>(a, L.k); break;
+        case L_FINAL: kb_finalize<<<g, 256, 0, s>>>(a); break;
+        }
+        ++count;
+    }
+    B->launches_per_run = count;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_precision p, egs_batch **out)
+{
+    if (!out || !n || nprob < 1) return set_error(EGS_ERR_ARG, "egs_batch_create: bad arguments");
+    *out = nullptr;
+    if (p != EGS_FP64) return set_error(EGS_ERR_UNIMPLEMENTED, "egs_batch_create: only EGS_FP64 is built");
+    if (tile == 0) {
+        int64_t nmax = 0;
+        for (int i = 0; i < nprob; ++i) nmax = std::max(nmax, n[i]);
+        tile = nmax <= 2048 ? 64 : 128;
+    }
+    if (tile < 64 || tile > 1024 || tile % 64) return set_error(EGS_ERR_ARG, "egs_batch_create: tile %d invalid", tile);
+    egs_batch *B = new egs_batch;
+    B->nprob = nprob;
+    B->b = tile;
+    size_t off = 0;
+    std::vector<size_t> tiles_off(nprob), zpad_off(nprob), part_off(nprob);
+    size_t in_doubles = 0;
+    for (int i = 0; i < nprob; ++i) {
+        if (n[i] < 1) {
+            delete B;
+            return set_error(EGS_ERR_ARG, "egs_batch_create: n[%d] = %lld", i, (long long)n[i]);
+        }
+        const int T = (int)((n[i] + tile - 1) / tile);
+        B->n.push_back(n[i]);
+        B->T.push_back(T);
+        tiles_off[i] = off;
+        off += a256((size_t)T * (T + 1) / 2 * tile * tile * sizeof(double));
+        zpad_off[i] = off;
+        off += a256((size_t)T * tile * sizeof(double));
+        part_off[i] = off;
+        off += a256((size_t)2 * T * sizeof(double));
+        B->in_off.push_back(in_doubles);
+        in_doubles += (size_t)3 * n[i];
+    }
+    const size_t probs_off = off;
+    off += a256(sizeof(BatchProblem) * nprob);
+    const size_t params_off = off;
+    off += a256(sizeof(egs_matern_params) * nprob);
+    const size_t status_off = off;
+    off += a256(sizeof(DevStatus) * nprob);
+    const size_t inputs_off = off;
+    off += a256(in_doubles * sizeof(double));
+    std::vector<int64_t> prefix;
+    plan_launches(B, prefix);
+    const size_t prefix_off = off;
+    off += a256(prefix.size() * sizeof(int64_t));
+    B->ws_bytes = off;
+    cudaError_t e = cudaMalloc((void **)&B->ws, off);
+    if (e != cudaSuccess) {
+        delete B;
+        return cuda_error(e, "egs_batch_create workspace");
+    }
+    B->d_probs = (BatchProblem *)(B->ws + probs_off);
+    B->d_params = (egs_matern_params *)(B->ws + params_off);
+    B->d_status = (DevStatus *)(B->ws + status_off);
+    B->d_inputs = (double *)(B->ws + inputs_off);
+    B->d_prefix = (int64_t *)(B->ws + prefix_off);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&B->h_probs, sizeof(BatchProblem) * nprob);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&B->h_params, sizeof(egs_matern_params) * nprob);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&B->h_status, sizeof(DevStatus) * nprob);
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        egs_batch_destroy(B);
+        return cuda_error(e, "egs_batch_create");
+    }
+    for (int i = 0; i < nprob; ++i) {
+        BatchProblem &pr = B->h_probs[i];
+        std::memset(&pr, 0, sizeof(pr));
+        double *in = B->d_inputs + B->in_off[i];
+        pr.X = in;
+        pr.Y = in + n[i];
+        pr.z = in + 2 * n[i];
+        pr.n = n[i];
+        pr.T = B->T[i];
+        pr.tiles = (double *)(B->ws + tiles_off[i]);
+        pr.zpad = (double *)(B->ws + zpad_off[i]);
+        pr.partials = (double *)(B->ws + part_off[i]);
+        pr.st = B->d_status + i;
+        pr.P = B->d_params + i;
+    }
+    e = cudaMemcpy(B->d_probs, B->h_probs, sizeof(BatchProblem) * nprob, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        egs_batch_destroy(B);
+        return cuda_error(e, "egs_batch_create");
+    }
+    *out = B;
+    return EGS_OK;
+}
+
+egs_status egs_batch_run(egs_batch *B, const double *const *locs, const double *const *z, const double *theta,
+                         double *out, egs_status *per_status, void *stream)
+{
+    if (!B || !locs || !z || !theta) return set_error(EGS_ERR_ARG, "egs_batch_run: NULL argument");
+    cudaStream_t us = (cudaStream_t)stream;
+    for (int i = 0; i < B->nprob; ++i)
+        if (egs_matern_params_init(theta + 3 * i, &B->h_params[i]) != 0)
+            return set_error(EGS_ERR_ARG, "egs_batch_run: theta of problem %d must be finite and > 0", i);
+    cudaError_t e = cudaEventRecord(B->ev_in, us);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->cs, B->ev_in, 0);
+    // inputs: copied into the plan's staging area (device or host sources)
+    for (int i = 0; i < B->nprob && e == cudaSuccess; ++i) {
+        double *in = B->d_inputs + B->in_off[i];
+        e = cudaMemcpyAsync(in, locs[i], (size_t)2 * B->n[i] * sizeof(double), cudaMemcpyDefault, B->cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(in + 2 * B->n[i], z[i], (size_t)B->n[i] * sizeof(double), cudaMemcpyDefault, B->cs);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->d_params, B->h_params, sizeof(egs_matern_params) * B->nprob, cudaMemcpyHostToDevice, B->cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_status, 0xFF, sizeof(DevStatus) * B->nprob, B->cs);
+    if (e == cudaSuccess && !B->exec) {
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(B->cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = enqueue_all(B, B->cs);
+            e = cudaStreamEndCapture(B->cs, &g);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(B->exec, B->cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->h_status, B->d_status, sizeof(DevStatus) * B->nprob, cudaMemcpyDeviceToHost, B->cs);
+    if (e == cudaSuccess) e = cudaEventRecord(B->ev_out, B->cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(us, B->ev_out, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->cs);
+    if (e != cudaSuccess) return cuda_error(e, "egs_batch_run");
+    egs_status worst = EGS_OK;
+    for (int i = 0; i < B->nprob; ++i) {
+        const bool ok = B->h_status[i].fail_index == kNoFail;
+        if (out) out[i] = B->h_status[i].result[0];
+        if (per_status) per_status[i] = ok ? EGS_OK : EGS_ERR_NOT_PD;
+        if (!ok) worst = EGS_ERR_NOT_PD;
+    }
+    if (worst != EGS_OK) set_error(worst, "egs_batch_run: at least one problem is not positive definite");
+    return worst;
+}
+
+int32_t egs_batch_launches(const egs_batch *B) { return B ? B->launches_per_run : 0; }
+
+int32_t egs_batch_tile(const egs_batch *B) { return B ? B->b : 0; }
+
+size_t egs_batch_workspace_bytes(const egs_batch *B) { return B ? B->ws_bytes : 0; }
+
+egs_status egs_batch_destroy(egs_batch *B)
+{
+    if (!B) return EGS_OK;
+    if (B->cs) cudaStreamSynchronize(B->cs);
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->ev_in) cudaEventDestroy(B->ev_in);
+    if (B->ev_out) cudaEventDestroy(B->ev_out);
+    if (B->cs) cudaStreamDestroy(B->cs);
+    if (B->ws) cudaFree(B->ws);
+    if (B->h_probs) cudaFreeHost(B->h_probs);
+    if (B->h_params) cudaFreeHost(B->h_params);
+    if (B->h_status) cudaFreeHost(B->h_status);
+    delete B;
+    return EGS_OK;
+}
+
+egs_status egs_loglik_batched(int32_t nprob, const int64_t *n, const double *const *locs, const double *const *z,
+                              const double *theta, egs_precision p, double *out, egs_status *per_status, void *stream)
+{
+    egs_batch *B = nullptr;
+    egs_status st = egs_batch_create(nprob, n, 0, p, &B);
+    if (st != EGS_OK) return st;
+    st = egs_batch_run(B, locs, z, theta, out, per_status, stream);
+    egs_batch_destroy(B);
+    return st;
+}
+
+}  // extern "C"

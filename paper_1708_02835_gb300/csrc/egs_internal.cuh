@@ -153,6 +153,31 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
                              int fmt, int refine, const MixedBuffers &mb, DevStatus *st, cudaStream_t s, KernelTimer *kt,
                              cudaEvent_t *phase_ev);
 
+// Layouts and setup of one evaluation (api.cu), shared with the serving loop.
+struct Layout {
+    size_t tiles, locs, z, zpad, partials, status, total;
+};
+struct MixedLayout {
+    size_t f64, f32, sig, panel, locs, z, vec, partials, status, err, total;
+};
+struct EvalSetup {
+    TileGeom g;
+    int band, refine;
+    bool mixed;
+    egs_precision p;
+    Layout L;
+    MixedLayout ML;
+    size_t need, locs_off, z_off;
+    egs_matern_params P;
+};
+egs_status eval_setup(int64_t n, const double *theta, egs_precision p, const egs_opts *opts, EvalSetup *es);
+// Enqueue one evaluation on s; inputs on the device, ws holds es.need bytes.
+cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double *dz, char *ws, cudaStream_t s,
+                         KernelTimer *kt, cudaEvent_t *ev);
+DevStatus *eval_status(const EvalSetup &es, char *ws);
+void fill_info(const EvalSetup &es, const DevStatus &h, egs_info *info);
+int32_t default_tile(int64_t n, egs_precision p);
+
 // Building blocks shared by the FP64 and mixed drivers.
 cudaError_t launch_potrf_diag(const Tiles &tl, int k, DevStatus *st, cudaStream_t s, KernelTimer *kt);
 cudaError_t launch_trsm_f64(const Tiles &tl, int k, int nrows, DevStatus *st, cudaStream_t s, KernelTimer *kt);

@@ -59,7 +59,9 @@ __global__ void __launch_bounds__(256) k_panel_from_f64(Tiles tl, int k, int nro
 
 // TRSM of the FP32 panel rows m = m0 + blockIdx.x: X L_kk^T = A_mk in FP32
 // (L_kk rounded to FP32), 64 rows per CTA, 32-column blocks; the result
-// overwrites A_mk and is written to the panel buffer.
+// overwrites A_mk and is written to the panel buffer.  The GEMM-style part
+// keeps 4 rows x 2 columns per thread with the operands transposed in shared
+// memory (one 16-byte and one 8-byte shared load per 8 FMAs).
 template <int FMT>
 __global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0, void *panel, const DevStatus *st)
 {
@@ -70,35 +72,47 @@ __global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0,
     const double *L = tl.t64(k, k);
     float *A = tl.t32(m, k) + (size_t)r0 * b;
     const size_t pbase = (size_t)(m - k - 1) * tl.bb() + (size_t)r0 * b;
-    __shared__ float Xs[64][17];
-    __shared__ float Ls[32][17];
+    __shared__ __align__(16) float Xt[16][64];   // [l][row]
+    __shared__ __align__(16) float Lt[16][32];   // [l][col]
     __shared__ float Ab[64][33];
     __shared__ float Ld[32][33];
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int tid = threadIdx.x;
+    const int tc = tid & 15, tr = tid >> 4;      // columns 2 tc, 2 tc + 1; rows 4 tr .. 4 tr + 3
     for (int c0 = 0; c0 < b; c0 += 32) {
-        float acc[8];
+        float acc[4][2];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] = A[(size_t)(ty * 8 + i) * b + c0 + tx];
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) acc[i][j] = A[(size_t)(4 * tr + i) * b + c0 + 2 * tc + j];
         for (int p = 0; p < c0; p += 16) {
             for (int e = tid; e < 64 * 16; e += 256) {
                 const int r = e >> 4, l = e & 15;
-                Xs[r][l] = A[(size_t)r * b + p + l];
+                Xt[l][r] = A[(size_t)r * b + p + l];
             }
             for (int e = tid; e < 32 * 16; e += 256) {
                 const int c = e >> 4, l = e & 15;
-                Ls[c][l] = (float)L[(size_t)(c0 + c) * b + p + l];
+                Lt[l][c] = (float)L[(size_t)(c0 + c) * b + p + l];
             }
             __syncthreads();
 #pragma unroll
             for (int l = 0; l < 16; ++l) {
-                const float lv = Ls[tx][l];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) acc[i] = fmaf(-Xs[ty * 8 + i][l], lv, acc[i]);
+                const float4 x = *reinterpret_cast<const float4 *>(&Xt[l][4 * tr]);
+                const float2 lv = *reinterpret_cast<const float2 *>(&Lt[l][2 * tc]);
+                acc[0][0] = fmaf(-x.x, lv.x, acc[0][0]);
+                acc[0][1] = fmaf(-x.x, lv.y, acc[0][1]);
+                acc[1][0] = fmaf(-x.y, lv.x, acc[1][0]);
+                acc[1][1] = fmaf(-x.y, lv.y, acc[1][1]);
+                acc[2][0] = fmaf(-x.z, lv.x, acc[2][0]);
+                acc[2][1] = fmaf(-x.z, lv.y, acc[2][1]);
+                acc[3][0] = fmaf(-x.w, lv.x, acc[3][0]);
+                acc[3][1] = fmaf(-x.w, lv.y, acc[3][1]);
             }
             __syncthreads();
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) Ab[ty * 8 + i][tx] = acc[i];
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) Ab[4 * tr + i][2 * tc + j] = acc[i][j];
         for (int e = tid; e < 32 * 32; e += 256) {
             const int r = e >> 5, c = e & 31;
             Ld[r][c] = (c <= r) ? (float)L[(size_t)(c0 + r) * b + c0 + c] : 0.0f;
@@ -112,10 +126,10 @@ __global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0,
             }
         }
         __syncthreads();
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float v = Ab[ty * 8 + i][tx];
-            const size_t off = (size_t)(ty * 8 + i) * b + c0 + tx;
+        for (int e = tid; e < 64 * 32; e += 256) {
+            const int r = e >> 5, c = e & 31;
+            const float v = Ab[r][c];
+            const size_t off = (size_t)r * b + c0 + c;
             A[off] = v;
             panel_store<FMT>(panel, pbase + off, v);
         }
@@ -123,19 +137,35 @@ __global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0,
     }
 }
 
-// Backward substitution on a diagonal tile: L_kk^T x = r in place, b threads.
+// Backward substitution on a diagonal tile: L_kk^T x = r in place, b threads
+// (thread i owns row i).  32-column blocks from the last: the owning warp
+// solves its 32 x 32 block with shuffles, then every thread with a smaller
+// row index subtracts the block's contribution (L read along its rows).
 __global__ void __launch_bounds__(1024) k_trsv_diag_T(Tiles tl, int k, double *__restrict__ v, const DevStatus *st)
 {
     if (mfailed(st)) return;
     __shared__ double xv[1024];
-    const int i = threadIdx.x, b = tl.b;
+    const int i = threadIdx.x, b = tl.b, lane = i & 31, w = i >> 5;
     const double *L = tl.t64(k, k);
     double r = v[(size_t)k * b + i];
-    for (int c = b - 1; c >= 0; --c) {
-        if (i == c) xv[c] = r / L[(size_t)c * b + c];
+    for (int cb = b / 32 - 1; cb >= 0; --cb) {
+        const int c0 = cb * 32;
+        if (w == cb) {
+            for (int jj = 31; jj >= 0; --jj) {
+                const double xj = __shfl_sync(0xffffffffu, r, jj) / L[(size_t)(c0 + jj) * b + c0 + jj];
+                if (lane == jj) xv[c0 + jj] = xj;
+                if (lane < jj) r = fma(-L[(size_t)(c0 + jj) * b + c0 + lane], xj, r);
+            }
+        }
         __syncthreads();
-        if (i < c) r = fma(-L[(size_t)c * b + i], xv[c], r);
+        if (i < c0) {
+            double s = 0.0;
+#pragma unroll 8
+            for (int jj = 0; jj < 32; ++jj) s = fma(L[(size_t)(c0 + jj) * b + i], xv[c0 + jj], s);
+            r -= s;
+        }
     }
+    __syncthreads();
     v[(size_t)k * b + i] = xv[i];
 }
 

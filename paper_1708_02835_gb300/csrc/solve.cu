@@ -10,7 +10,7 @@
 // row, so the update order is fixed).  The whole solve reads each stored
 // tile of L exactly once.  Reductions are fixed-order trees, so results are
 // bitwise reproducible.
-#include "egs_internal.cuh"
+#include "blocks.cuh"
 
 namespace egs {
 
@@ -25,64 +25,16 @@ __global__ void k_pad_vector(const double *__restrict__ z, int64_t n, double *__
     if (i < npad) zpad[i] = (i < n) ? z[i] : 0.0;
 }
 
-// Fixed-order tree reduction of one value per thread (any blockDim.x <= 1024).
-// Returns the total (valid in every thread after the last barrier).
-__device__ __forceinline__ double block_sum(double v, double *red)
-{
-    const int tid = threadIdx.x, nt = blockDim.x;
-    red[tid] = v;
-    __syncthreads();
-    int p2 = 1;
-    while (p2 < nt) p2 <<= 1;
-    for (int s = p2 >> 1; s > 0; s >>= 1) {
-        if (tid < s && tid + s < nt) red[tid] += red[tid + s];
-        __syncthreads();
-    }
-    return red[0];
-}
-
 // Diagonal block: y_k = L_kk^-1 r_k in place, blockDim.x = b threads.
 __global__ void __launch_bounds__(1024) k_trsv_diag_f64(Tiles tl, int k, double *__restrict__ zpad,
                                                         double *__restrict__ partials, DevStatus *st)
 {
     if (failed_s(st)) return;
-    __shared__ double yv[1024];
-    __shared__ double red[1024];
-    const int i = threadIdx.x, b = tl.b, T = tl.T;
-    const double *L = tl.t64(k, k);
-    const double *Li = L + (size_t)i * b;
-    double r = zpad[(size_t)k * b + i];
-    for (int c = 0; c < b; ++c) {
-        if (i == c) yv[c] = r / Li[c];
-        __syncthreads();
-        if (i > c) r = fma(-Li[c], yv[c], r);
-    }
-    const double y = yv[i];
-    zpad[(size_t)k * b + i] = y;
-    if (partials) {
-        const double ld = block_sum(log(Li[i]), red);
-        __syncthreads();
-        const double q = block_sum(y * y, red);
-        if (i == 0) {
-            partials[k] = ld;
-            partials[T + k] = q;
-        }
-    }
-}
-
-template <typename E>
-__device__ __forceinline__ void gemv_rows(const E *__restrict__ A, int b, int r0, const double *ys,
-                                          double *__restrict__ out)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rr = 0; rr < 8; ++rr) {
-        const int r = r0 + warp * 8 + rr;
-        const E *row = A + (size_t)r * b;
-        double s = 0.0;
-        for (int c = lane; c < b; c += 32) s = fma((double)row[c], ys[c], s);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) out[r] -= s;
+    __shared__ double ldq[2];
+    trsv_fwd_tile(tl.t64(k, k), tl.b, zpad + (size_t)k * tl.b, partials ? ldq : nullptr);
+    if (partials && threadIdx.x == 0) {
+        partials[k] = ldq[0];
+        partials[tl.T + k] = ldq[1];
     }
 }
 

@@ -55,6 +55,45 @@ struct UpdateWork {
         w.yb = (w.n - k - 1) * tl.b + w.cb * BN;
         return true;
     }
+    // 64 consecutive columns from two accumulator slices; all loads of the
+    // old values are issued before any store so they overlap in flight.
+    __device__ void store2(const WorkItem &w, int r, int c0, const float (&v0)[32], const float (&v1)[32]) const
+    {
+        const size_t row = (size_t)(w.rb * BM + r), col = (size_t)(w.cb * BN + c0);
+        if (tl.is64(w.m, w.n)) {
+            double *C = tl.t64(w.m, w.n) + row * tl.b + col;
+            double2 c[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) c[i] = *reinterpret_cast<const double2 *>(C + 2 * i);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                c[i].x -= (double)v0[2 * i];
+                c[i].y -= (double)v0[2 * i + 1];
+                c[16 + i].x -= (double)v1[2 * i];
+                c[16 + i].y -= (double)v1[2 * i + 1];
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) *reinterpret_cast<double2 *>(C + 2 * i) = c[i];
+        } else {
+            float *C = tl.t32(w.m, w.n) + row * tl.b + col;
+            float4 c[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) c[i] = *reinterpret_cast<const float4 *>(C + 4 * i);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                c[i].x -= v0[4 * i];
+                c[i].y -= v0[4 * i + 1];
+                c[i].z -= v0[4 * i + 2];
+                c[i].w -= v0[4 * i + 3];
+                c[8 + i].x -= v1[4 * i];
+                c[8 + i].y -= v1[4 * i + 1];
+                c[8 + i].z -= v1[4 * i + 2];
+                c[8 + i].w -= v1[4 * i + 3];
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) *reinterpret_cast<float4 *>(C + 4 * i) = c[i];
+        }
+    }
     __device__ void store(const WorkItem &w, int r, int c0, const float (&v)[32]) const
     {
         const size_t row = (size_t)(w.rb * BM + r), col = (size_t)(w.cb * BN + c0);
@@ -96,6 +135,11 @@ struct DenseWork {
         w.yb = w.cb * BN;
         return true;
     }
+    __device__ void store2(const WorkItem &w, int r, int c0, const float (&v0)[32], const float (&v1)[32]) const
+    {
+        store(w, r, c0, v0);
+        store(w, r, c0 + 32, v1);
+    }
     __device__ void store(const WorkItem &w, int r, int c0, const float (&v)[32]) const
     {
         float *Cp = C + (size_t)(w.rb * BM + r) * N + w.cb * BN + c0;
@@ -104,18 +148,23 @@ struct DenseWork {
     }
 };
 
+// Persistent kernel: one CTA per SM loops over the work items
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0 (one lane) streams the
+// operands of every item through the 4-stage ring; warp 1 (one lane) issues
+// the MMAs of item t into TMEM accumulator t % 2 (two 256-column buffers);
+// warps 2-9 drain accumulator t % 2 while the MMAs of item t + 1 run.
 // FMT: 2 = TF32 (K-slice 8 per MMA), 1 = BF16 (K-slice 16 per MMA).
-template <int FMT, class Work>
-__global__ void __launch_bounds__(128, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Work work, int kchunks,
-          int *err)
-{
-    WorkItem wi;
-    if (!work.decode((int64_t)blockIdx.x, wi)) return;  // uniform across the CTA
+constexpr int NUM_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr uint32_t TMEM_COLS2 = 2 * TMEM_COLS;
 
+template <int FMT, class Work>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Work work,
+          int64_t nitems, int kchunks, int *err)
+{
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t full[STAGES], empty[STAGES], accum;
+    __shared__ uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ int last_chunk[STAGES];
@@ -127,63 +176,101 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             tc::mbar_init(&empty[s], 1);
             last_chunk[s] = -1;
         }
-        tc::mbar_init(&accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&tfull[b], 1);
+            tc::mbar_init(&tempty[b], 8);
+        }
         abort_flag = 0;
         tc::fence_mbar_init();
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_base, TMEM_COLS);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, TMEM_COLS2);
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    const uint32_t tacc = tmem_base;
+    const uint32_t tbase = tmem_base;
     constexpr int KELEMS = (FMT == 2) ? 32 : 64;  // elements per 128-byte row slice
 
-    if (warp == 0 && lane == 0) {
-        tc::prefetch_tmap(&mapA);
-        tc::prefetch_tmap(&mapB);
-        for (int c = 0; c < kchunks; ++c) {
-            const int s = c % STAGES;
-            const uint32_t ph = (uint32_t)(c / STAGES) & 1u;
-            if (!tc::mbar_wait(&empty[s], ph ^ 1u, &abort_flag)) break;
-            tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-            tc::tma_load_2d(&mapA, &full[s], smem + s * STAGE_BYTES, c * KELEMS, wi.ya);
-            tc::tma_load_2d(&mapB, &full[s], smem + s * STAGE_BYTES + A_BYTES, c * KELEMS, wi.yb);
-            last_chunk[s] = c;
-        }
-    } else if (warp == 1 && lane == 0) {
-        constexpr uint32_t idesc = tc::idesc_f32acc(BM, BN, FMT);
-        for (int c = 0; c < kchunks; ++c) {
-            const int s = c % STAGES;
-            const uint32_t ph = (uint32_t)(c / STAGES) & 1u;
-            if (!tc::mbar_wait(&full[s], ph, &abort_flag)) break;
-            tc::tc_fence_after();
-            const uint32_t a0 = tc::smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t b0 = a0 + A_BYTES;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint64_t ad = tc::desc_sw128(a0 + 32 * j);
-                const uint64_t bd = tc::desc_sw128(b0 + 32 * j);
-                if (FMT == 2) tc::mma_tf32(tacc, ad, bd, idesc, (c | j) != 0);
-                else tc::mma_f16(tacc, ad, bd, idesc, (c | j) != 0);
+    if (warp == 0) {
+        if (lane == 0) {
+            tc::prefetch_tmap(&mapA);
+            tc::prefetch_tmap(&mapB);
+            int g = 0;
+            for (int64_t item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
+                WorkItem wi;
+                if (!work.decode(item, wi)) continue;
+                for (int c = 0; c < kchunks; ++c, ++g) {
+                    const int s = g % STAGES;
+                    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1u, &abort_flag)) break;
+                    tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    tc::tma_load_2d(&mapA, &full[s], smem + s * STAGE_BYTES, c * KELEMS, wi.ya);
+                    tc::tma_load_2d(&mapB, &full[s], smem + s * STAGE_BYTES + A_BYTES, c * KELEMS, wi.yb);
+                    last_chunk[s] = g;
+                }
             }
-            tc::mma_commit(&empty[s]);
         }
-        tc::mma_commit(&accum);
-    }
-    __syncwarp();
-    const bool ok = tc::mbar_wait(&accum, 0, &abort_flag);
-    tc::tc_fence_after();
-    // warp-uniform decision: the TMEM loads below are .sync.aligned
-    if (__all_sync(0xffffffffu, ok && !abort_flag)) {
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_f32acc(BM, BN, FMT);
+            int g = 0, t = 0;
+            for (int64_t item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
+                WorkItem wi;
+                if (!work.decode(item, wi)) continue;
+                const int buf = t & 1;
+                const uint32_t use = (uint32_t)(t >> 1);
+                if (!tc::mbar_wait(&tempty[buf], (use & 1u) ^ 1u, &abort_flag)) break;
+                tc::tc_fence_after();
+                const uint32_t d = tbase + (uint32_t)buf * TMEM_COLS;
+                for (int c = 0; c < kchunks; ++c, ++g) {
+                    const int s = g % STAGES;
+                    const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+                    if (!tc::mbar_wait(&full[s], ph, &abort_flag)) break;
+                    tc::tc_fence_after();
+                    const uint32_t a0 = tc::smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t b0 = a0 + A_BYTES;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint64_t ad = tc::desc_sw128(a0 + 32 * j);
+                        const uint64_t bd = tc::desc_sw128(b0 + 32 * j);
+                        if (FMT == 2) tc::mma_tf32(d, ad, bd, idesc, (c | j) != 0);
+                        else tc::mma_f16(d, ad, bd, idesc, (c | j) != 0);
+                    }
+                    tc::mma_commit(&empty[s]);
+                }
+                tc::mma_commit(&tfull[buf]);
+                ++t;
+            }
+        }
+    } else {
+        // epilogue warps 2..9: warp w reads TMEM lanes 32 (w % 4) .. + 31 and
+        // one half of the 256 columns (warps 2..5 the first, 6..9 the second)
+        const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        int t = 0;
+        for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+            WorkItem wi;
+            if (!work.decode(item, wi)) continue;
+            const int buf = t & 1;
+            const uint32_t use = (uint32_t)(t >> 1);
+            const bool ok = tc::mbar_wait(&tfull[buf], use & 1u, &abort_flag);
+            tc::tc_fence_after();
+            if (!__all_sync(0xffffffffu, ok && !abort_flag)) break;
+            const uint32_t d = tbase + (uint32_t)buf * TMEM_COLS + lane_base;
 #pragma unroll 1
-        for (int cc = 0; cc < BN / 32; ++cc) {
-            float v[32];
-            tc::tmem_ld32(tacc + lane_base + (uint32_t)(cc * 32), v);
-            work.store(wi, warp * 32 + lane, cc * 32, v);
+            for (int cc = half * (BN / 64); cc < (half + 1) * (BN / 64); cc += 2) {
+                float v0[32], v1[32];
+                tc::tmem_ld32(d + (uint32_t)(cc * 32), v0);
+                tc::tmem_ld32(d + (uint32_t)(cc * 32 + 32), v1);
+                work.store2(wi, q * 32 + lane, cc * 32, v0, v1);
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[buf]);
+            ++t;
         }
     }
-    tc::tc_fence_before();
+    __syncwarp();  // lane 0 of the producer / MMA warps rejoins its warp here
     __syncthreads();
     if (abort_flag && threadIdx.x == 0) {
         // let every TMA load that was issued land before the CTA exits
@@ -194,8 +281,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             }
         atomicExch(err, 1);
     }
+    tc::tc_fence_after();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tacc, TMEM_COLS);
+    if (warp == 0) tc::tmem_dealloc(tbase, TMEM_COLS2);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -227,13 +315,25 @@ cudaError_t make_map(CUtensorMap *m, const void *base, int fmt, uint64_t inner, 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
 template <int FMT, class Work>
-cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const Work &w, int64_t blocks, int kchunks,
+cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const Work &w, int64_t items, int kchunks,
                         int *err, cudaStream_t s)
 {
     cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<FMT, Work>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    k_tc_gemm<FMT, Work><<<(unsigned)blocks, 128, SMEM_BYTES, s>>>(ma, mb, w, kchunks, err);
+    const int64_t grid = items < num_sms() ? items : num_sms();
+    k_tc_gemm<FMT, Work><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, w, items, kchunks, err);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,115 @@
+"""Serving loop: resident fields, FIFO admission under an HBM budget,
+overlapping requests on separate streams.
+
+Each result must be identical (bitwise) whether the request ran alone or in
+a mix of concurrent requests, and identical to a direct egs_loglik_ex call
+with the same tile and band: the evaluation kernels are deterministic.
+"""
+import numpy as np
+import pytest
+
+import egs_inputs as ei
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = [1200, 2500, 700, 3100, 1800]
+TILE = 256
+
+
+@pytest.fixture(scope="module")
+def egs():
+    import paper_1708_02835_gb300 as m
+    m.load_library()
+    return m
+
+
+def _fields():
+    out = []
+    for k, n in enumerate(FIELDS):
+        locs = ei.jittered_grid(n, seed=200 + k)
+        out.append((n, np.ascontiguousarray(locs.reshape(-1)), ei.normal(300 + k, n)))
+    return out
+
+
+def _requests():
+    rng = np.random.default_rng(3)
+    reqs = []
+    for i in range(14):
+        f = int(rng.integers(len(FIELDS)))
+        th = (float(rng.uniform(0.5, 2.0)), float(rng.uniform(0.03, 0.1)), float(rng.uniform(0.4, 0.9)))
+        reqs.append((f, th, "fp64" if i % 2 == 0 else "tf32"))
+    return reqs
+
+
+def _serve(egs, fields, reqs, max_inflight, budget=64 << 30):
+    srv = egs.egs_server(budget, max_inflight=max_inflight, tile=TILE, band=2)
+    fids = [srv.add_field(l, z, n) for n, l, z in fields]
+    out = []
+    if max_inflight == 1:
+        for f, th, p in reqs:
+            out.append(srv.wait(srv.submit(fids[f], th, p))[0])
+    else:
+        tickets = [srv.submit(fids[f], th, p) for f, th, p in reqs]
+        out = [srv.wait(t)[0] for t in tickets]
+    st = srv.stats()
+    srv.close()
+    return out, st
+
+
+def test_same_alone_and_in_mix(egs):
+    from gpu_util import dev
+    fields, reqs = _fields(), _requests()
+    alone, st1 = _serve(egs, fields, reqs, 1)
+    mix, st4 = _serve(egs, fields, reqs, 4)
+    assert alone == mix
+    assert st1["inflight_peak"] == 1 and st4["inflight_peak"] > 1
+    assert st4["completed"] == len(reqs) and st4["failed"] == 0
+    assert st4["p99_ms"] >= st4["p50_ms"] > 0 and st4["evals_per_s"] > 0
+    for (f, th, p), v in zip(reqs, alone):
+        n, l, z = fields[f]
+        direct, _ = egs.egs_loglik_ex(dev(l), dev(z), th, n, p, tile=TILE, band=2)
+        assert v == direct
+
+
+def test_budget_is_never_exceeded(egs):
+    fields, reqs = _fields(), _requests()
+    need = max(egs.egs_loglik_workspace_bytes(n, TILE, p, 2) for n in FIELDS for p in ("fp64", "tf32"))
+    field_bytes = sum(3 * 8 * n for n in FIELDS)
+    budget = field_bytes + need + 1024
+    out, st = _serve(egs, fields, reqs, 4, budget=budget)
+    assert st["completed"] == len(reqs) and st["bytes_peak"] <= budget
+    alone, _ = _serve(egs, fields, reqs, 1)
+    assert out == alone
+
+
+def test_budget_for_one_serialises_equal_requests(egs):
+    fields = _fields()[:1]
+    n = FIELDS[0]
+    reqs = [(0, (1.0, 0.05 + 0.01 * i, 0.5), "fp64") for i in range(6)]
+    need = egs.egs_loglik_workspace_bytes(n, TILE, "fp64", 2)
+    out, st = _serve(egs, fields, reqs, 4, budget=3 * 8 * n + need + 1024)
+    assert st["inflight_peak"] == 1 and st["completed"] == 6
+
+
+def test_wait_timeout_then_result(egs):
+    n = 16384
+    srv = egs.egs_server(64 << 30, max_inflight=2, tile=512)
+    fid = srv.add_field(np.ascontiguousarray(ei.jittered_grid(n).reshape(-1)), ei.normal(1, n), n)
+    t = srv.submit(fid, (1.0, 0.1, 0.5), "fp64")      # about a second of FP64 work
+    with pytest.raises(egs.EgsError) as e:
+        srv.wait(t, timeout_ms=1)
+    assert e.value.status == egs.EGS_ERR_TIMEOUT
+    v, info = srv.wait(t, timeout_ms=-1)
+    assert np.isfinite(v) and info["tile"] == 512
+    srv.close()
+
+
+def test_bad_requests(egs):
+    srv = egs.egs_server(1 << 20, max_inflight=2)
+    with pytest.raises(egs.EgsError) as e:
+        srv.add_field(np.zeros(2 * 100000), np.zeros(100000), 100000)     # 2.4 MB > 1 MB budget
+    assert e.value.status == egs.EGS_ERR_OOM
+    with pytest.raises(egs.EgsError) as e:
+        srv.submit(7, (1.0, 0.1, 0.5), "fp64")
+    assert e.value.status == egs.EGS_ERR_ARG
+    srv.close()
