@@ -155,6 +155,27 @@ egs_status egs_trsv_tiles(const void *tiles, int64_t n, int32_t tile, const doub
                           double *logdet, double *quad, void *stream);
 
 /*
+ * egs_trsv_tiles_noalloc - egs_trsv_tiles for callers that cannot allocate
+ * device memory during the call (for example an application whose own
+ * memory manager has reserved the whole device, or a latency-sensitive loop
+ * that cannot afford the device-wide synchronisation cudaFree implies).  The
+ * paper has no counterpart; it is a deployment variant of the solve above.
+ * Same arguments, results and errors as egs_trsv_tiles, but the scratch (the
+ * padded solution vector, the per-tile partial sums and the status word)
+ * lives in one fixed device array inside the library, about 1.1 MB, that
+ * every GPU which loads the library keeps until the process exits; nothing is
+ * allocated or freed.  Limits: ceil(n / tile) * tile <= 131072 and
+ * ceil(n / tile) <= 2048, otherwise EGS_ERR_ARG with a message (use
+ * egs_trsv_tiles).  The first call on a device looks up the array's device
+ * address (once per device, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents: calls that overlap on the GPU (for example on two
+ * streams) race and must be serialised by the caller.  Synchronises stream.
+ */
+egs_status egs_trsv_tiles_noalloc(const void *tiles, int64_t n, int32_t tile, const double *z, double *y,
+                                  double *logdet, double *quad, void *stream);
+
+/*
  * egs_loglik - one evaluation of Eq. 1 (Algorithm 2) at theta.
  *   locs  2n doubles (x then y), device or host memory
  *   z     n doubles, device or host memory

@@ -93,6 +93,7 @@ def load_library(build_if_missing: bool = True):
         "egs_matern_tiles": (c.c_int, [vp, i64, pd, i32, c.c_int, i32, vp, vp]),
         "egs_potrf_tiles": (c.c_int, [vp, i64, i32, c.POINTER(i64), vp]),
         "egs_trsv_tiles": (c.c_int, [vp, i64, i32, vp, vp, pd, pd, vp]),
+        "egs_trsv_tiles_noalloc": (c.c_int, [vp, i64, i32, vp, vp, pd, pd, vp]),
         "egs_loglik": (c.c_int, [vp, vp, pd, i64, c.c_int, pd, c.POINTER(egs_info), vp]),
         "egs_loglik_ex": (c.c_int, [vp, vp, pd, i64, c.c_int, c.POINTER(egs_opts), pd, c.POINTER(egs_info), vp]),
         "egs_tc_gemm_test": (c.c_int, [vp, vp, i32, i32, i32, c.c_int, vp, vp]),
@@ -199,6 +200,15 @@ def egs_trsv_tiles(tiles, n: int, tile: int, z, y, stream=None) -> tuple:
     ld, q = ctypes.c_double(), ctypes.c_double()
     _check(load_library().egs_trsv_tiles(_ptr(tiles), n, tile, _ptr(z), _ptr(y), ctypes.byref(ld), ctypes.byref(q),
                                          _stream(stream)))
+    return ld.value, q.value
+
+
+def egs_trsv_tiles_noalloc(tiles, n: int, tile: int, z, y, stream=None) -> tuple:
+    """egs_trsv_tiles with its scratch in the library's fixed device array
+    (no allocation); returns (logdet, quad)."""
+    ld, q = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().egs_trsv_tiles_noalloc(_ptr(tiles), n, tile, _ptr(z), _ptr(y), ctypes.byref(ld),
+                                                 ctypes.byref(q), _stream(stream)))
     return ld.value, q.value
 
 
