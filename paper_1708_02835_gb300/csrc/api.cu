@@ -88,7 +88,7 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
     L.sig = off;
     off += align256(g.ntiles() * bb * sizeof(double));
     L.panel = off;
-    off += align256((size_t)(g.T > 1 ? g.T - 1 : 1) * bb * esz);
+    off += 2 * align256((size_t)(g.T > 1 ? g.T - 1 : 1) * bb * esz);
     L.locs = off;
     off += align256((size_t)2 * g.n * sizeof(double));
     L.z = off;
@@ -160,7 +160,9 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
         const MixedLayout &ML = es.ML;
         mb.tl = Tiles{(double *)(ws + ML.f64), (float *)(ws + ML.f32), g.b, g.T, es.band};
         mb.sig = (double *)(ws + ML.sig);
-        mb.panel = ws + ML.panel;
+        const size_t esz = (mix_fmt(es.p) == 2) ? 4 : 2;
+        mb.panel[0] = ws + ML.panel;
+        mb.panel[1] = ws + ML.panel + align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.tile_elems() * esz);
         double *v = (double *)(ws + ML.vec);
         const size_t stride = align256(npad * sizeof(double)) / sizeof(double);
         mb.zp = v;

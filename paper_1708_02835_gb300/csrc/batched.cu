@@ -89,10 +89,9 @@ __global__ void __launch_bounds__(256) kb_potrf_sub(BatchArgs a, int k, int p)
     int64_t local;
     const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
     if (failed(pr.st)) return;
-    __shared__ double pan[kIB * (kPW + 1)];
     const int b = a.b;
     double *A = dense_tiles(pr, b).t64(k, k) + (size_t)p * b + p;
-    if (!potrf_block(A, kIB, b, (int64_t)k * b + p, pr.st, pan)) return;
+    if (!potrf64_smem(A, b, (int64_t)k * b + p, pr.st)) return;
     for (int e = threadIdx.x; e < kIB * (b - p - kIB); e += 256) {
         const int r = e / (b - p - kIB), c = e % (b - p - kIB);
         A[(size_t)r * b + kIB + c] = 0.0;
@@ -106,8 +105,8 @@ __global__ void __launch_bounds__(256) kb_trsm_sub(BatchArgs a, int k, int p)
     if (failed(pr.st)) return;
     const int b = a.b;
     double *A = dense_tiles(pr, b).t64(k, k);
-    const int r0 = p + kIB + 64 * (int)local;
-    trsm_rows<64>(A + (size_t)p * b + p, b, A + (size_t)r0 * b + p, b, kIB);
+    const int r0 = p + kIB + 16 * (int)local;
+    trsm_rows<16>(A + (size_t)p * b + p, b, A + (size_t)r0 * b + p, b, kIB);
 }
 
 __global__ void __launch_bounds__(256) kb_syrk_sub(BatchArgs a, int k, int p)
@@ -120,8 +119,8 @@ __global__ void __launch_bounds__(256) kb_syrk_sub(BatchArgs a, int k, int p)
     int bi, bj;
     tri_decode(local, bi, bj);
     const int q = p + kIB;
-    const int ri = q + 64 * bi, rj = q + 64 * bj;
-    gemm_sub64(A + (size_t)ri * b + p, b, A + (size_t)rj * b + p, b, kIB, A + (size_t)ri * b + rj, b);
+    const int ri = q + 32 * bi, rj = q + 32 * bj;
+    gemm_sub32(A + (size_t)ri * b + p, b, A + (size_t)rj * b + p, b, kIB, A + (size_t)ri * b + rj, b);
 }
 
 __global__ void __launch_bounds__(256) kb_trsm_panel(BatchArgs a, int k)
@@ -273,11 +272,11 @@ void plan_launches(egs_batch *B, std::vector<int64_t> &prefix)
     add(L_GEN, 0, 0, [&](int q) { return (int64_t)B->T[q] * (B->T[q] + 1) / 2 * nsub * nsub; });
     for (int k = 0; k < Tmax; ++k) {
         for (int p = 0; p < b; p += kIB) {
-            const int64_t nrest = (b - p - kIB) / 64;
+            const int64_t nrest = (b - p - kIB) / 16, n32 = (b - p - kIB) / 32;
             add(L_POTRF, k, p, [&](int q) { return (int64_t)(B->T[q] > k ? 1 : 0); });
             if (nrest > 0) {
                 add(L_TRSM_SUB, k, p, [&](int q) { return B->T[q] > k ? nrest : (int64_t)0; });
-                add(L_SYRK_SUB, k, p, [&](int q) { return B->T[q] > k ? nrest * (nrest + 1) / 2 : (int64_t)0; });
+                add(L_SYRK_SUB, k, p, [&](int q) { return B->T[q] > k ? n32 * (n32 + 1) / 2 : (int64_t)0; });
             }
         }
         add(L_TRSM, k, 0, [&](int q) { return B->T[q] > k + 1 ? (int64_t)(B->T[q] - k - 1) * (b / 64) : (int64_t)0; });

@@ -114,6 +114,86 @@ __device__ __forceinline__ bool potrf_block(double *A, int nb, int ld, int64_t r
 }
 
 // ---------------------------------------------------------------------------
+// Cholesky of a 64 x 64 block at A (row stride ld) held in shared memory for
+// the whole factorisation (one global read and one write of the block): one
+// CTA of 256 threads, right-looking column by column.  Same failure
+// reporting as potrf_block; the strict upper triangle is zeroed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool potrf64_smem(double *A, int ld, int64_t row0, DevStatus *st)
+{
+    __shared__ double S[64][65];
+    __shared__ int fail_j;
+    const int tid = threadIdx.x;
+    if (tid == 0) fail_j = -1;
+    for (int e = tid; e < 64 * 64; e += 256) {
+        const int i = e >> 6, j = e & 63;
+        S[i][j] = (j <= i) ? A[(size_t)i * ld + j] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < 64; ++j) {
+        if (tid == 0) {
+            const double d = S[j][j];
+            if (!(d > 0.0)) fail_j = j;
+            else S[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        if (fail_j >= 0) {
+            if (tid == 0) atomicMin(&st->fail_index, (unsigned long long)(row0 + fail_j));
+            return false;
+        }
+        const double ljj = S[j][j];
+        if (tid > j && tid < 64) S[tid][j] /= ljj;
+        __syncthreads();
+        // trailing update S[i][l] -= S[i][j] S[l][j] for j < l <= i
+        const int m = 63 - j;  // trailing size
+        for (int e = tid; e < m * m; e += 256) {
+            const int i = j + 1 + e / m, l = j + 1 + e % m;
+            if (l <= i) S[i][l] -= S[i][j] * S[l][j];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < 64 * 64; e += 256) {
+        const int i = e >> 6, j = e & 63;
+        A[(size_t)i * ld + j] = (j <= i) ? S[i][j] : 0.0;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// C (32 x 32, row stride ldc) -= Am (32 x K) An (32 x K)^T; 2 x 2 outputs per
+// thread (rows ty + 16 i, columns tx + 16 j).  256 threads.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void gemm_sub32(const double *Am, int lda, const double *An, int ldb, int K, double *C,
+                                           int ldc)
+{
+    __shared__ double As[kPW][33];
+    __shared__ double Bs[kPW][33];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int p = 0; p < K; p += kPW) {
+        for (int e = tid; e < 32 * kPW; e += 256) {
+            const int r = e >> 4, l = e & 15;
+            As[l][r] = Am[(size_t)r * lda + p + l];
+            Bs[l][r] = An[(size_t)r * ldb + p + l];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < kPW; ++l) {
+            const double a0 = As[l][ty], a1 = As[l][ty + 16], b0 = Bs[l][tx], b1 = Bs[l][tx + 16];
+            acc[0][0] = fma(a0, b0, acc[0][0]);
+            acc[0][1] = fma(a0, b1, acc[0][1]);
+            acc[1][0] = fma(a1, b0, acc[1][0]);
+            acc[1][1] = fma(a1, b1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) C[(size_t)(ty + 16 * i) * ldc + tx + 16 * j] -= acc[i][j];
+}
+
+// ---------------------------------------------------------------------------
 // X L^T = A for RB rows (RB in {8, 16, 64}): X and A at Xp (row stride ldx,
 // ncols columns), L lower ncols x ncols at Lp (row stride ldl).  32-column
 // blocks: a GEMM-style update with the already-solved columns, then a
@@ -241,16 +321,21 @@ __device__ __forceinline__ void trsv_fwd_tile(const double *__restrict__ L, int 
 {
     __shared__ double yv[1024];
     __shared__ double red[1024];
+    __shared__ double D[32][33];
     const int i = threadIdx.x, lane = i & 31, w = i >> 5;
     const double *Li = L + (size_t)i * b;
     double r = v[i];
     for (int cb = 0; cb < b / 32; ++cb) {
         const int c0 = cb * 32;
+        // stage the 32 x 32 diagonal block so the warp's serial solve reads
+        // shared memory instead of global memory
+        for (int e = i; e < 32 * 32; e += b) D[e >> 5][e & 31] = L[(size_t)(c0 + (e >> 5)) * b + c0 + (e & 31)];
+        __syncthreads();
         if (w == cb) {
             for (int jj = 0; jj < 32; ++jj) {
-                const double yj = __shfl_sync(0xffffffffu, r, jj) / L[(size_t)(c0 + jj) * b + c0 + jj];
+                const double yj = __shfl_sync(0xffffffffu, r, jj) / D[jj][jj];
                 if (lane == jj) yv[c0 + jj] = yj;
-                if (lane > jj) r = fma(-Li[c0 + jj], yj, r);
+                if (lane > jj) r = fma(-D[lane][jj], yj, r);
             }
         }
         __syncthreads();

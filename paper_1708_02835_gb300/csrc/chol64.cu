@@ -29,29 +29,28 @@ namespace egs {
 __global__ void __launch_bounds__(256) k_potrf_sub(Tiles tl, int k, int p, DevStatus *st)
 {
     if (failed(st)) return;
-    __shared__ double pan[kIB * (kPW + 1)];
     const int b = tl.b;
     double *A = tl.t64(k, k) + (size_t)p * b + p;
-    if (!potrf_block(A, kIB, b, (int64_t)k * b + p, st, pan)) return;
+    if (!potrf64_smem(A, b, (int64_t)k * b + p, st)) return;
     for (int e = threadIdx.x; e < kIB * (b - p - kIB); e += 256) {
         const int r = e / (b - p - kIB), c = e % (b - p - kIB);
         A[(size_t)r * b + kIB + c] = 0.0;
     }
 }
 
-// Inside diagonal tile k: rows p + 64 + 64 * blockIdx.x solve against the
-// factored 64 x 64 sub-block at p.
+// Inside diagonal tile k: rows p + 64 + 16 * blockIdx.x solve against the
+// factored 64 x 64 sub-block at p (16 rows per CTA: more SMs on the chain).
 __global__ void __launch_bounds__(256) k_trsm_sub(Tiles tl, int k, int p, DevStatus *st)
 {
     if (failed(st)) return;
     const int b = tl.b;
     double *A = tl.t64(k, k);
-    const int r0 = p + kIB + 64 * (int)blockIdx.x;
-    trsm_rows<64>(A + (size_t)p * b + p, b, A + (size_t)r0 * b + p, b, kIB);
+    const int r0 = p + kIB + 16 * (int)blockIdx.x;
+    trsm_rows<16>(A + (size_t)p * b + p, b, A + (size_t)r0 * b + p, b, kIB);
 }
 
 // Inside diagonal tile k: rank-64 update of the trailing lower part after
-// sub-panel p, in 64 x 64 blocks (bi >= bj).
+// sub-panel p, in 32 x 32 blocks (bi >= bj).
 __global__ void __launch_bounds__(256) k_syrk_sub(Tiles tl, int k, int p, DevStatus *st)
 {
     if (failed(st)) return;
@@ -60,8 +59,8 @@ __global__ void __launch_bounds__(256) k_syrk_sub(Tiles tl, int k, int p, DevSta
     int bi, bj;
     tri_decode((int64_t)blockIdx.x, bi, bj);
     const int q = p + kIB;
-    const int ri = q + 64 * bi, rj = q + 64 * bj;
-    gemm_sub64(A + (size_t)ri * b + p, b, A + (size_t)rj * b + p, b, kIB, A + (size_t)ri * b + rj, b);
+    const int ri = q + 32 * bi, rj = q + 32 * bj;
+    gemm_sub32(A + (size_t)ri * b + p, b, A + (size_t)rj * b + p, b, kIB, A + (size_t)ri * b + rj, b);
 }
 
 // TRSM on the panel below tile k: rows m = k+1+blockIdx.x, RB rows per CTA.
@@ -97,10 +96,11 @@ cudaError_t launch_potrf_diag(const Tiles &tl, int k, DevStatus *st, cudaStream_
     const int b = tl.b;
     for (int p = 0; p < b; p += kIB) {
         EGS_LAUNCH(kt, KC_POTRF, s, k_potrf_sub<<<1, 256, 0, s>>>(tl, k, p, st));
-        const int nrest = (b - p - kIB) / 64;
+        const int nrest = (b - p - kIB) / 16;   // 16-row TRSM blocks
+        const int n32 = (b - p - kIB) / 32;     // 32 x 32 SYRK blocks per side
         if (nrest > 0) {
             EGS_LAUNCH(kt, KC_POTRF, s, k_trsm_sub<<<(unsigned)nrest, 256, 0, s>>>(tl, k, p, st));
-            EGS_LAUNCH(kt, KC_POTRF, s, k_syrk_sub<<<(unsigned)(nrest * (nrest + 1) / 2), 256, 0, s>>>(tl, k, p, st));
+            EGS_LAUNCH(kt, KC_POTRF, s, k_syrk_sub<<<(unsigned)(n32 * (n32 + 1) / 2), 256, 0, s>>>(tl, k, p, st));
         }
     }
     return cudaGetLastError();
@@ -123,11 +123,34 @@ cudaError_t launch_trsm_f64(const Tiles &tl, int k, int nrows, DevStatus *st, cu
     return cudaGetLastError();
 }
 
+// The same update in 32 x 32 sub-blocks, for launches too small to fill the
+// GPU with 64 x 64 blocks.
+__global__ void __launch_bounds__(256) k_update_f64_32(Tiles tl, int k, DevStatus *st)
+{
+    if (failed(st)) return;
+    const int b = tl.b;
+    int mm, nn;
+    tri_decode((int64_t)blockIdx.x, mm, nn);
+    const int m = k + 1 + mm, nc = k + 1 + nn;
+    const int nsub = b >> 5;
+    const int sr = (int)blockIdx.y / nsub, sc = (int)blockIdx.y % nsub;
+    if (m == nc && sc > sr) return;
+    gemm_sub32(tl.t64(m, k) + (size_t)sr * 32 * b, b, tl.t64(nc, k) + (size_t)sc * 32 * b, b, b,
+               tl.t64(m, nc) + (size_t)sr * 32 * b + sc * 32, b);
+}
+
 cudaError_t launch_update_f64(const Tiles &tl, int k, int64_t ntri, DevStatus *st, cudaStream_t s, KernelTimer *kt)
 {
     if (ntri <= 0) return cudaSuccess;
     const int nsub = tl.b / 64;
-    EGS_LAUNCH(kt, KC_UPDATE, s, k_update_f64<<<dim3((unsigned)ntri, (unsigned)(nsub * nsub)), 256, 0, s>>>(tl, k, st));
+    if (ntri * nsub * (nsub + 1) / 2 < 304) {
+        const int n32 = tl.b / 32;
+        EGS_LAUNCH(kt, KC_UPDATE, s,
+                   k_update_f64_32<<<dim3((unsigned)ntri, (unsigned)(n32 * n32)), 256, 0, s>>>(tl, k, st));
+    } else {
+        EGS_LAUNCH(kt, KC_UPDATE, s,
+                   k_update_f64<<<dim3((unsigned)ntri, (unsigned)(nsub * nsub)), 256, 0, s>>>(tl, k, st));
+    }
     return cudaGetLastError();
 }
 

@@ -141,7 +141,7 @@ cudaError_t launch_matern_tiles(const double *X, const double *Y, int64_t n, con
 struct MixedBuffers {
     Tiles tl;
     double *sig;      // dense FP64 lower tiles of Sigma (for the refinement residual)
-    void *panel;      // (T-1) * b * b operands (FP32 for TF32, BF16)
+    void *panel[2];   // two buffers of (T-1) * b * b operands (FP32 for TF32, BF16), step k uses k % 2
     double *zp, *y, *x, *d, *res, *rows, *cols;  // T*b vectors
     double *partials; // 2T
     int *err;
@@ -194,7 +194,8 @@ cudaError_t launch_pad_vector(const double *z, int64_t n, double *zpad, int64_t 
 // Tensor maps over the panel operand buffer ((T-1)*b rows of b elements;
 // fmt 2 = FP32/TF32, 1 = BF16) and the tcgen05 trailing update of step k.
 cudaError_t make_panel_maps(const void *panel, int fmt, int b, int T, CUtensorMap *mapA, CUtensorMap *mapB);
+// part 0: all trailing tiles of step k; 1: column k + 1; 2: columns k + 2 onwards.
 cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, int fmt, const Tiles &tl, int k,
-                             int *err, cudaStream_t s, KernelTimer *kt);
+                             int *err, cudaStream_t s, KernelTimer *kt, int part = 0);
 
 }  // namespace egs

@@ -145,16 +145,19 @@ __global__ void __launch_bounds__(1024) k_trsv_diag_T(Tiles tl, int k, double *_
 {
     if (mfailed(st)) return;
     __shared__ double xv[1024];
+    __shared__ double D[32][33];
     const int i = threadIdx.x, b = tl.b, lane = i & 31, w = i >> 5;
     const double *L = tl.t64(k, k);
     double r = v[(size_t)k * b + i];
     for (int cb = b / 32 - 1; cb >= 0; --cb) {
         const int c0 = cb * 32;
+        for (int e = i; e < 32 * 32; e += b) D[e >> 5][e & 31] = L[(size_t)(c0 + (e >> 5)) * b + c0 + (e & 31)];
+        __syncthreads();
         if (w == cb) {
             for (int jj = 31; jj >= 0; --jj) {
-                const double xj = __shfl_sync(0xffffffffu, r, jj) / L[(size_t)(c0 + jj) * b + c0 + jj];
+                const double xj = __shfl_sync(0xffffffffu, r, jj) / D[jj][jj];
                 if (lane == jj) xv[c0 + jj] = xj;
-                if (lane < jj) r = fma(-L[(size_t)(c0 + jj) * b + c0 + lane], xj, r);
+                if (lane < jj) r = fma(-D[jj][lane], xj, r);
             }
         }
         __syncthreads();
@@ -308,37 +311,67 @@ cudaError_t backward_solve(const Tiles &tl, double *v, const DevStatus *st, cuda
     return cudaGetLastError();
 }
 
+// The factorisation with one step of lookahead.  The FP64 chain of step k
+// (POTRF and the band TRSM) runs on a side stream; the main stream then runs
+// the FP32 TRSM of the off-band panel on the whole GPU, the FP64 band x band
+// update and the tensor-core update of column k + 1, signals the side stream
+// (whose chain for step k + 1 needs only that column), and updates the rest
+// of the trailing matrix (leaving a few SMs free) while the next chain runs.
+// Panels alternate between two buffers.
 template <int FMT>
-cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap &ma, const CUtensorMap &mbm, DevStatus *st,
+cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CUtensorMap *mbm, DevStatus *st,
                          cudaStream_t s, KernelTimer *kt)
 {
     const Tiles &tl = mb.tl;
     const int T = tl.T, b = tl.b;
-    for (int k = 0; k < T; ++k) {
-        cudaError_t e = launch_potrf_diag(tl, k, st, s, kt);
-        if (e != cudaSuccess) return e;
-        if (k + 1 == T) break;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_panel = nullptr, ev_col = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_col, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);  // the side stream starts after prior work on s
+    KernelTimer *kts = kt;  // side-stream kernels are timed with events on the side stream
+    for (int k = 0; k < T && e == cudaSuccess; ++k) {
         const int nb = (tl.band - 1 < T - k - 1) ? tl.band - 1 : T - k - 1;  // FP64 rows below k
         const int nf = T - k - 1 - nb;                                       // FP32 rows
-        e = launch_trsm_f64(tl, k, nb, st, s, kt);
-        if (e != cudaSuccess) return e;
-        // updates whose two operands are FP64 band tiles stay in FP64 (they
-        // carry the nearest-neighbour entries that set the diagonal pivots)
-        e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, s, kt);
-        if (e != cudaSuccess) return e;
-        if (nb > 0) {
-            const size_t total = (size_t)nb * tl.bb();
-            const unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-            EGS_LAUNCH(kt, KC_TRSM, s, k_panel_from_f64<FMT><<<blocks, 256, 0, s>>>(tl, k, nb, mb.panel, st));
+        void *panel = mb.panel[k & 1];
+        // ---- chain of step k on the side stream: POTRF and the FP64 band TRSM
+        e = cudaStreamWaitEvent(side, ev_col, 0);
+        if (e == cudaSuccess) e = launch_potrf_diag(tl, k, st, side, kts);
+        if (e == cudaSuccess && k + 1 < T) {
+            e = launch_trsm_f64(tl, k, nb, st, side, kts);
+            if (e == cudaSuccess && nb > 0) {
+                const size_t total = (size_t)nb * tl.bb();
+                const unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+                EGS_LAUNCH(kts, KC_TRSM, side, k_panel_from_f64<FMT><<<blocks, 256, 0, side>>>(tl, k, nb, panel, st));
+            }
+            if (e == cudaSuccess) e = cudaGetLastError();
         }
-        if (nf > 0)
+        if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
+        if (k + 1 == T || e != cudaSuccess) break;
+        // ---- step k on the main stream: the FP32 TRSM (whole GPU), the FP64
+        // band x band update, column k + 1, signal, then the rest
+        e = cudaStreamWaitEvent(s, ev_panel, 0);
+        if (e == cudaSuccess && nf > 0)
             EGS_LAUNCH(kt, KC_TRSM, s,
                        k_trsm_panel_f32<FMT><<<dim3((unsigned)nf, (unsigned)(b / 64)), 256, 0, s>>>(tl, k, k + 1 + nb,
-                                                                                                    mb.panel, st));
-        e = launch_update_tc(ma, mbm, FMT, tl, k, mb.err, s, kt);
-        if (e != cudaSuccess) return e;
+                                                                                                panel, st));
+        // updates whose two operands are FP64 band tiles stay in FP64 (they
+        // carry the nearest-neighbour entries that set the diagonal pivots)
+        if (e == cudaSuccess) e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, s, kt);
+        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], FMT, tl, k, mb.err, s, kt, 1);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);
+        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], FMT, tl, k, mb.err, s, kt, 2);
     }
-    return cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_panel, 0);  // join the side stream
+    // destroying a stream or event with work still pending is legal: the
+    // resources are released once that work completes, and s already waits
+    // for it through ev_panel
+    if (side) cudaStreamDestroy(side);
+    if (ev_panel) cudaEventDestroy(ev_panel);
+    if (ev_col) cudaEventDestroy(ev_col);
+    return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 }  // namespace
@@ -355,8 +388,9 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     cudaError_t e = launch_matern_tiles(X, Y, n, tl, P, mb.sig, s, kt);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
-    CUtensorMap ma, mbm;
-    e = make_panel_maps(mb.panel, fmt, b, T, &ma, &mbm);
+    CUtensorMap ma[2], mbm[2];
+    e = make_panel_maps(mb.panel[0], fmt, b, T, &ma[0], &mbm[0]);
+    if (e == cudaSuccess) e = make_panel_maps(mb.panel[1], fmt, b, T, &ma[1], &mbm[1]);
     if (e != cudaSuccess) return e;
     e = (fmt == 2) ? factor_mixed<2>(mb, ma, mbm, st, s, kt) : factor_mixed<1>(mb, ma, mbm, st, s, kt);
     if (e != cudaSuccess) return e;

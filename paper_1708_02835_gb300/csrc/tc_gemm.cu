@@ -22,6 +22,7 @@ namespace egs {
 namespace {
 
 constexpr int BM = 128, BN = 256, STAGES = 4;
+constexpr int kReserveSms = 24;  // SMs the bulk update leaves to the lookahead chain
 constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 256;
@@ -32,21 +33,31 @@ struct WorkItem {
     int ya, yb;  // TMA row coordinates of the A and B boxes
 };
 
-// Trailing update of step k over the lower-tile storage.
+// Trailing update of step k over the lower-tile storage: the output tiles
+// (m, n) with m >= n >= col0 (one_col: only n = col0).  Panel tile m of
+// step k is operand row block m - k - 1.
 struct UpdateWork {
     Tiles tl;
     int k;
+    int col0;
+    int one_col;
     __device__ bool decode(int64_t bid, WorkItem &w) const
     {
         const int nrb = tl.b / BM, ncb = tl.b / BN, per = nrb * ncb;
         const int64_t t = bid / per;
         const int blk = (int)(bid % per);
-        int ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while ((int64_t)ii * (ii + 1) / 2 > t) --ii;
-        while ((int64_t)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
-        const int jj = (int)(t - (int64_t)ii * (ii + 1) / 2);
-        w.m = k + 1 + ii;
-        w.n = k + 1 + jj;
+        int ii, jj;
+        if (one_col) {
+            ii = (int)t;
+            jj = 0;
+        } else {
+            ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+            while ((int64_t)ii * (ii + 1) / 2 > t) --ii;
+            while ((int64_t)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
+            jj = (int)(t - (int64_t)ii * (ii + 1) / 2);
+        }
+        w.m = col0 + ii;
+        w.n = col0 + jj;
         w.rb = blk / ncb;
         w.cb = blk % ncb;
         if (w.m - k < tl.band && w.n - k < tl.band) return false;         // FP64 band x band: done in FP64
@@ -326,13 +337,16 @@ int num_sms()
     return sms;
 }
 
+// reserve > 0 leaves that many SMs free for kernels on other streams (the
+// factorisation's critical chain runs beside the update).
 template <int FMT, class Work>
 cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const Work &w, int64_t items, int kchunks,
-                        int *err, cudaStream_t s)
+                        int *err, cudaStream_t s, int reserve = 0)
 {
     cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<FMT, Work>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    const int64_t grid = items < num_sms() ? items : num_sms();
+    const int64_t ctas = num_sms() - reserve > 1 ? num_sms() - reserve : 1;
+    const int64_t grid = items < ctas ? items : ctas;
     k_tc_gemm<FMT, Work><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, w, items, kchunks, err);
     return cudaGetLastError();
 }
@@ -350,17 +364,28 @@ cudaError_t make_panel_maps(const void *panel, int fmt, int b, int T, CUtensorMa
 }
 
 cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, int fmt, const Tiles &tl, int k,
-                             int *err, cudaStream_t s, KernelTimer *kt)
+                             int *err, cudaStream_t s, KernelTimer *kt, int part)
 {
-    const int64_t ntiles = (int64_t)(tl.T - k - 1) * (tl.T - k) / 2;
+    // part 0: every trailing tile; 1: column k + 1 only; 2: columns k + 2 .. T - 1
+    const int64_t r = tl.T - k - 1;
+    int64_t ntiles = 0;
+    UpdateWork w{tl, k, k + 1, 0};
+    if (part == 0) ntiles = r * (r + 1) / 2;
+    else if (part == 1) {
+        ntiles = r;
+        w.one_col = 1;
+    } else {
+        ntiles = (r - 1) * r / 2;
+        w.col0 = k + 2;
+    }
     if (ntiles <= 0) return cudaSuccess;
     const int64_t blocks = ntiles * (tl.b / BM) * (tl.b / BN);
-    UpdateWork w{tl, k};
     const int kchunks = tl.b / (fmt == 2 ? 32 : 64);
     cudaError_t e;
     if (kt) kt->begin(KC_UPDATE, s);
-    if (fmt == 2) e = launch_gemm<2>(mapA, mapB, w, blocks, kchunks, err, s);
-    else e = launch_gemm<1>(mapA, mapB, w, blocks, kchunks, err, s);
+    const int reserve = (part == 2) ? kReserveSms : 0;
+    if (fmt == 2) e = launch_gemm<2>(mapA, mapB, w, blocks, kchunks, err, s, reserve);
+    else e = launch_gemm<1>(mapA, mapB, w, blocks, kchunks, err, s, reserve);
     if (kt) kt->end(KC_UPDATE, s);
     return e;
 }
