@@ -47,6 +47,12 @@ def parse():
     ap.add_argument("--theta", default="1.0,0.1,0.5")
     ap.add_argument("--e2e-steps", type=int, default=-1, help="steps of the end-to-end leg (default: = steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="config3",
+                    choices=["config3", "config2-mle", "config4-batched", "config5-serve"],
+                    help="config3 (default): one n=102,400 evaluation per step; the others are the "
+                         "MLE, batched and serving workloads")
+    ap.add_argument("--evals", type=int, default=50, help="config2-mle: likelihood evaluations")
+    ap.add_argument("--requests", type=int, default=48, help="config5-serve: requests per arrival rate")
     ap.add_argument("--cpu-sample-n", type=int, default=8192)
     return ap.parse_args()
 
@@ -188,6 +194,153 @@ def run_reference(a, rank: int):
     print(json.dumps(line), flush=True)
 
 
+def _to_dev(a):
+    import numpy as np
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def run_mle(a, egs):
+    """Config 2: n = 25,600 (160 x 160), theta = (1, 0.2, 1.3), Z simulated on the
+    GPU by Algorithm 1; one MLE run of --evals derivative-free evaluations."""
+    import torch
+    import egs_inputs as ei
+    from paper_1708_02835_gb300 import mle
+    p = ei.CONFIG2
+    n = p.n if a.n == 102400 else a.n
+    theta = p.theta
+    locs = ei.jittered_grid(n, seed=p.seed)
+    dl, de = _to_dev(locs.reshape(-1)), _to_dev(ei.normal(p.seed, n))
+    dz = torch.empty(n, dtype=torch.float64, device="cuda")
+    egs.egs_simulate(dl, de, theta, n, dz)
+    start = (0.5, 0.1, 1.0)
+    out = {}
+    for prec in (["fp64", a.precision] if a.precision != "fp64" else ["fp64"]):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = mle.fit(dl, dz, n, prec, start=start, max_evals=a.evals, tile=0 if prec == "fp64" else 512)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[prec] = {"theta_hat": list(r.theta), "loglik": r.loglik, "evals": r.evals, "seconds": dt,
+                     "evals_per_s": r.evals / dt}
+    line = {"metric": "MLE log-likelihood evaluations/s (config 2)", "value": out["fp64"]["evals_per_s"],
+            "unit": "evals/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "n=%d (160x160 jittered grid), theta=(1,0.2,1.3), Z by Algorithm 1 on the GPU, "
+                                   "bounded Nelder-Mead from %s over [0.01,5]^3" % (n, start), "n": n},
+            "runs": out, "theta_true": list(theta)}
+    if len(out) > 1:
+        f, m = out["fp64"]["theta_hat"], out[a.precision]["theta_hat"]
+        line["theta_hat_max_rel_diff"] = max(abs(x - y) / abs(x) for x, y in zip(f, m))
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(a, egs):
+    """Config 4: 512 independent problems, n ~ U{256..4096} on random sub-squares,
+    own theta each (FP64); tile picked by measuring 64 / 128 / 256."""
+    import numpy as np
+    import torch
+    import egs_inputs as ei
+    probs = ei.batched_problems(512)
+    ns = [p.n for p in probs]
+    dl = [_to_dev(p.locations().reshape(-1)) for p in probs]
+    dz = [_to_dev(p.e()) for p in probs]
+    th = np.array([p.theta for p in probs])
+    tune = {}
+    for tile in (64, 128, 256):
+        B = egs.egs_batch(ns, tile=tile)
+        B.run(dl, dz, th)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.run(dl, dz, th)
+        tune[tile] = time.perf_counter() - t0
+        B.close()
+    best = min(tune, key=tune.get)
+    B = egs.egs_batch(ns, tile=best)
+    for _ in range(a.warmup):
+        out, stat = B.run(dl, dz, th)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        out, stat = B.run(dl, dz, th, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    flops = sum(n ** 3 / 3.0 for n in ns)
+    line = {"metric": "batched log-likelihood problems/s (config 4)", "value": len(ns) / (ms / 1e3),
+            "unit": "problems/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic (z ~ N(0, I))",
+            "config": {"workload": "512 problems, n ~ U{256..4096}, jittered grids on random sub-squares, own theta",
+                       "tile": best, "graph_kernels": B.launches},
+            "autotune_seconds": tune, "potrf_tflops_equiv": flops / (ms / 1e3) / 1e12,
+            "not_pd": int(np.sum(stat != 0))}
+    B.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(a, egs):
+    """Config 5: 64 resident fields, n log-uniform in [1000, 40000], nu ~ U(0.3, 2);
+    Poisson arrivals of theta updates at 0.5 / 0.8 / 0.95 of measured capacity,
+    half FP64 and half TF32; 150 GB HBM budget."""
+    import numpy as np
+    import egs_inputs as ei
+    fields = ei.serving_fields(64)
+    rng = np.random.default_rng(0)
+    srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=2)
+    fids = [srv.add_field(np.ascontiguousarray(f.locations().reshape(-1)), f.e(), f.n) for f in fields]
+
+    def request(i):
+        f = int(rng.integers(len(fields)))
+        th = tuple(float(v) * float(np.exp(rng.normal(0, 0.1))) for v in fields[f].theta)
+        return fids[f], th, ("fp64" if i % 2 == 0 else "tf32")
+
+    # capacity: a closed burst of requests
+    burst = [request(i) for i in range(16)]
+    t0 = time.perf_counter()
+    tickets = [srv.submit(*r) for r in burst]
+    for t in tickets:
+        try:
+            srv.wait(t)
+        except egs.EgsError:
+            pass
+    cap = len(burst) / (time.perf_counter() - t0)
+    srv.close()
+    results = {}
+    for rho in (0.5, 0.8, 0.95):
+        srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=2)
+        fids = [srv.add_field(np.ascontiguousarray(f.locations().reshape(-1)), f.e(), f.n) for f in fields]
+        rate = rho * cap
+        gaps = rng.exponential(1.0 / rate, a.requests)
+        tickets = []
+        t_start = time.perf_counter()
+        t_next = t_start
+        for i in range(a.requests):
+            t_next += gaps[i]
+            delay = t_next - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(*request(i)))
+        for t in tickets:
+            try:
+                srv.wait(t)
+            except egs.EgsError:
+                pass
+        st = srv.stats()
+        results[str(rho)] = {"rate_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                             "mean_ms": st["mean_ms"], "evals_per_s": st["evals_per_s"],
+                             "completed": st["completed"], "failed_not_pd": st["failed"],
+                             "inflight_peak": st["inflight_peak"], "bytes_peak": st["bytes_peak"]}
+        srv.close()
+    line = {"metric": "serve p50/p99 ms and evals/s (config 5)", "value": results["0.8"]["p50_ms"],
+            "unit": "ms (p50 at 0.8 of capacity)", "n_gpus": 1, "higher_is_better": False, "dtype": "f64/f64+tf32",
+            "data": "synthetic (z ~ N(0, I))",
+            "config": {"workload": "64 fields, n log-uniform [1000, 40000], nu ~ U(0.3, 2), Poisson arrivals, "
+                                   "50/50 FP64 and TF32, 150 GB budget, 8 slots", "capacity_per_s": cap},
+            "rates": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -195,6 +348,13 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         run_reference(a, rank)
+        return
+    if a.workload != "config3":
+        import torch
+        import paper_1708_02835_gb300 as egs
+        torch.cuda.set_device(local)
+        egs.load_library()
+        {"config2-mle": run_mle, "config4-batched": run_batched, "config5-serve": run_serve}[a.workload](a, egs)
         return
 
     import numpy as np

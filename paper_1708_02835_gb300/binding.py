@@ -94,6 +94,7 @@ def load_library(build_if_missing: bool = True):
         "egs_potrf_tiles": (c.c_int, [vp, i64, i32, c.POINTER(i64), vp]),
         "egs_trsv_tiles": (c.c_int, [vp, i64, i32, vp, vp, pd, pd, vp]),
         "egs_trsv_tiles_noalloc": (c.c_int, [vp, i64, i32, vp, vp, pd, pd, vp]),
+        "egs_simulate": (c.c_int, [vp, vp, pd, i64, i32, vp, vp]),
         "egs_loglik": (c.c_int, [vp, vp, pd, i64, c.c_int, pd, c.POINTER(egs_info), vp]),
         "egs_loglik_ex": (c.c_int, [vp, vp, pd, i64, c.c_int, c.POINTER(egs_opts), pd, c.POINTER(egs_info), vp]),
         "egs_tc_gemm_test": (c.c_int, [vp, vp, i32, i32, i32, c.c_int, vp, vp]),
@@ -225,6 +226,12 @@ def egs_loglik_ex(locs, z, theta, n: int, precision="fp64", tile: int = 0, band:
                                       ctypes.byref(out), ctypes.byref(info), _stream(stream))
     _check(st)
     return out.value, info.as_dict()
+
+
+def egs_simulate(locs, e, theta, n: int, z, tile: int = 0, stream=None):
+    """Algorithm 1 on the GPU: z = L e with Sigma(theta) = L L^T (FP64)."""
+    tp, _keep = _theta(theta)
+    _check(load_library().egs_simulate(_ptr(locs), _ptr(e), tp, n, tile, _ptr(z), _stream(stream)))
 
 
 def egs_loglik(locs, z, theta, n: int, precision="fp64", stream=None) -> float:

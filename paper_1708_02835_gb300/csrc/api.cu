@@ -392,6 +392,56 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
     return EGS_OK;
 }
 
+egs_status egs_simulate(const double *locs, const double *e, const double theta[3], int64_t n, int32_t tile, double *z,
+                        void *stream)
+{
+    g_err[0] = 0;
+    if (!locs || !e || !z) return set_error(EGS_ERR_ARG, "NULL pointer");
+    if (!is_device_ptr(z)) return set_error(EGS_ERR_ARG, "egs_simulate: z must be device memory");
+    EvalSetup es;
+    egs_opts o{};
+    o.tile = tile;
+    egs_status sc = eval_setup(n, theta, EGS_FP64, &o, &es);
+    if (sc != EGS_OK) return sc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const TileGeom &g = es.g;
+    char *ws = nullptr;
+    cudaError_t err = cudaMallocAsync((void **)&ws, es.need, s);
+    if (err != cudaSuccess) return cuda_error(err, "egs_simulate workspace");
+    double *tiles = (double *)(ws + es.L.tiles);
+    double *epad = (double *)(ws + es.L.zpad);
+    DevStatus *st = eval_status(es, ws);
+    const double *dlocs = locs, *de = e;
+    if (!is_device_ptr(locs)) {
+        dlocs = (const double *)(ws + es.L.locs);
+        err = cudaMemcpyAsync((void *)dlocs, locs, (size_t)2 * n * sizeof(double), cudaMemcpyHostToDevice, s);
+    }
+    if (err == cudaSuccess && !is_device_ptr(e)) {
+        de = (const double *)(ws + es.L.z);
+        err = cudaMemcpyAsync((void *)de, e, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s);
+    }
+    double *zfull = nullptr;
+    if (err == cudaSuccess) err = cudaMallocAsync((void **)&zfull, (size_t)g.T * g.b * sizeof(double), s);
+    if (err == cudaSuccess) {
+        status_init(st, s);
+        err = launch_matern_tiles_f64(dlocs, dlocs + n, g, es.P, tiles, s);
+    }
+    if (err == cudaSuccess) err = launch_potrf_tiles_f64(tiles, g, st, s);
+    if (err == cudaSuccess) err = launch_pad_vector(de, n, epad, (int64_t)g.T * g.b, s);
+    if (err == cudaSuccess) err = launch_trmv_lower(tiles, g, epad, zfull, st, s);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(z, zfull, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    DevStatus h;
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (zfull) cudaFreeAsync(zfull, s);
+    cudaFreeAsync(ws, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return cuda_error(err, "egs_simulate");
+    if (h.fail_index != kNoFail)
+        return set_error(EGS_ERR_NOT_PD, "egs_simulate: not positive definite at row %lld",
+                         (long long)h.fail_index);
+    return EGS_OK;
+}
+
 egs_status egs_loglik(const double *locs, const double *z, const double theta[3], int64_t n, egs_precision p,
                       double *out_loglik, egs_info *info, void *stream)
 {

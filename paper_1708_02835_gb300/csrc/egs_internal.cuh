@@ -187,6 +187,10 @@ cudaError_t launch_forward_solve(const Tiles &tl, double *zpad, double *partials
                                  KernelTimer *kt);
 cudaError_t launch_finalize(const double *partials, int T, int64_t n, DevStatus *st, cudaStream_t s, KernelTimer *kt);
 
+// Z = L e over FP64 lower tiles (diagonal tiles with a zero upper triangle).
+cudaError_t launch_trmv_lower(const double *tiles, const TileGeom &g, const double *epad, double *out,
+                              const DevStatus *st, cudaStream_t s);
+
 // Copy z (n doubles) into zpad (T*b doubles), zero padding.
 cudaError_t launch_pad_vector(const double *z, int64_t n, double *zpad, int64_t npad, cudaStream_t s,
                               KernelTimer *kt = nullptr);
@@ -194,8 +198,10 @@ cudaError_t launch_pad_vector(const double *z, int64_t n, double *zpad, int64_t 
 // Tensor maps over the panel operand buffer ((T-1)*b rows of b elements;
 // fmt 2 = FP32/TF32, 1 = BF16) and the tcgen05 trailing update of step k.
 cudaError_t make_panel_maps(const void *panel, int fmt, int b, int T, CUtensorMap *mapA, CUtensorMap *mapB);
+// Map for the epilogue's TMA reduce into the off-band FP32 tiles.
+cudaError_t make_offband_map(const float *f32, int b, size_t ntiles, CUtensorMap *mapC);
 // part 0: all trailing tiles of step k; 1: column k + 1; 2: columns k + 2 onwards.
-cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, int fmt, const Tiles &tl, int k,
-                             int *err, cudaStream_t s, KernelTimer *kt, int part = 0);
+cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, const CUtensorMap &mapC, int fmt,
+                             const Tiles &tl, int k, int *err, cudaStream_t s, KernelTimer *kt, int part = 0);
 
 }  // namespace egs

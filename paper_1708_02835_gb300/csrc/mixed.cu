@@ -319,8 +319,8 @@ cudaError_t backward_solve(const Tiles &tl, double *v, const DevStatus *st, cuda
 // of the trailing matrix (leaving a few SMs free) while the next chain runs.
 // Panels alternate between two buffers.
 template <int FMT>
-cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CUtensorMap *mbm, DevStatus *st,
-                         cudaStream_t s, KernelTimer *kt)
+cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CUtensorMap *mbm,
+                         const CUtensorMap &mc, DevStatus *st, cudaStream_t s, KernelTimer *kt)
 {
     const Tiles &tl = mb.tl;
     const int T = tl.T, b = tl.b;
@@ -359,9 +359,9 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         // updates whose two operands are FP64 band tiles stay in FP64 (they
         // carry the nearest-neighbour entries that set the diagonal pivots)
         if (e == cudaSuccess) e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, s, kt);
-        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], FMT, tl, k, mb.err, s, kt, 1);
+        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, FMT, tl, k, mb.err, s, kt, 1);
         if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);
-        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], FMT, tl, k, mb.err, s, kt, 2);
+        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, FMT, tl, k, mb.err, s, kt, 2);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_panel, 0);  // join the side stream
@@ -388,11 +388,12 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     cudaError_t e = launch_matern_tiles(X, Y, n, tl, P, mb.sig, s, kt);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
-    CUtensorMap ma[2], mbm[2];
+    CUtensorMap ma[2], mbm[2], mc;
     e = make_panel_maps(mb.panel[0], fmt, b, T, &ma[0], &mbm[0]);
     if (e == cudaSuccess) e = make_panel_maps(mb.panel[1], fmt, b, T, &ma[1], &mbm[1]);
+    if (e == cudaSuccess) e = make_offband_map(tl.f32, b, Tiles::f32_tiles(T, tl.band), &mc);
     if (e != cudaSuccess) return e;
-    e = (fmt == 2) ? factor_mixed<2>(mb, ma, mbm, st, s, kt) : factor_mixed<1>(mb, ma, mbm, st, s, kt);
+    e = (fmt == 2) ? factor_mixed<2>(mb, ma, mbm, mc, st, s, kt) : factor_mixed<1>(mb, ma, mbm, mc, st, s, kt);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);
     // y = L^-1 z (log-det and y.y partials), x = L^-T y

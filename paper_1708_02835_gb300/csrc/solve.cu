@@ -79,6 +79,35 @@ __global__ void k_finalize(const double *__restrict__ partials, int T, int64_t n
     }
 }
 
+// Z = L e over the lower tiles of L (Algorithm 1, dtrmm): out[i*b + r] =
+// sum_{j <= i} L_ij[r][:] . e_j, one warp per row, fixed shuffle tree.
+// Diagonal tiles hold L with a zero strict upper triangle.  grid = (T, b/8).
+__global__ void __launch_bounds__(256) k_trmv_lower(const double *__restrict__ tiles, int b, int T,
+                                                    const double *__restrict__ e, double *__restrict__ out,
+                                                    const DevStatus *st)
+{
+    if (failed_s(st)) return;
+    const int i = (int)blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = (int)blockIdx.y * 8 + warp;
+    const size_t bb = (size_t)b * b;
+    double s = 0.0;
+    for (int j = 0; j <= i; ++j) {
+        const double *row = tiles + (size_t)tile_linear(i, j) * bb + (size_t)r * b;
+        const double *ej = e + (size_t)j * b;
+        for (int c = lane; c < b; c += 32) s = fma(row[c], ej[c], s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) out[(size_t)i * b + r] = s;
+}
+
+cudaError_t launch_trmv_lower(const double *tiles, const TileGeom &g, const double *epad, double *out,
+                              const DevStatus *st, cudaStream_t s)
+{
+    k_trmv_lower<<<dim3((unsigned)g.T, (unsigned)(g.b / 8)), 256, 0, s>>>(tiles, g.b, g.T, epad, out, st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pad_vector(const double *z, int64_t n, double *zpad, int64_t npad, cudaStream_t s, KernelTimer *kt)
 {
     const unsigned blocks = (unsigned)((npad + 255) / 256);

@@ -21,10 +21,12 @@ namespace egs {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, STAGES = 4;
+constexpr int BM = 128, BN = 256, STAGES = 3;
 constexpr int kReserveSms = 24;  // SMs the bulk update leaves to the lookahead chain
 constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr int EPI_WARPS = 8;
+constexpr int STAGE_C = 32 * 32 * 4;  // one 32 x 32 FP32 box staged for the TMA reduce
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_WARPS * 2 * STAGE_C + 1024;
 constexpr uint32_t TMEM_COLS = 256;
 
 struct WorkItem {
@@ -105,6 +107,17 @@ struct UpdateWork {
             for (int i = 0; i < 16; ++i) *reinterpret_cast<float4 *>(C + 4 * i) = c[i];
         }
     }
+    // FP32 output tiles take the TMA reduce path: row of the 2-D view of the
+    // off-band tile array where output row r of this item lives.
+    static constexpr bool kReduce = true;
+    __device__ bool reduce_here(const WorkItem &w) const { return !tl.is64(w.m, w.n); }
+    __device__ int reduce_row(const WorkItem &w, int r) const
+    {
+        const int64_t q = w.m - tl.band;
+        const int64_t idx = q * (q + 1) / 2 + w.n;
+        return (int)(idx * tl.b + w.rb * BM + r);
+    }
+    __device__ int reduce_col(const WorkItem &w, int c0) const { return w.cb * BN + c0; }
     __device__ void store(const WorkItem &w, int r, int c0, const float (&v)[32]) const
     {
         const size_t row = (size_t)(w.rb * BM + r), col = (size_t)(w.cb * BN + c0);
@@ -137,6 +150,10 @@ struct DenseWork {
     float *C;
     int N;  // columns of C
     int nrb, ncb;
+    static constexpr bool kReduce = false;
+    __device__ bool reduce_here(const WorkItem &) const { return false; }
+    __device__ int reduce_row(const WorkItem &, int) const { return 0; }
+    __device__ int reduce_col(const WorkItem &, int) const { return 0; }
     __device__ bool decode(int64_t bid, WorkItem &w) const
     {
         w.rb = (int)(bid / ncb);
@@ -170,8 +187,8 @@ constexpr uint32_t TMEM_COLS2 = 2 * TMEM_COLS;
 
 template <int FMT, class Work>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Work work,
-          int64_t nitems, int kchunks, int *err)
+k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+          const __grid_constant__ CUtensorMap mapC, Work work, int64_t nitems, int kchunks, int *err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -254,11 +271,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         }
     } else {
         // epilogue warps 2..9: warp w reads TMEM lanes 32 (w % 4) .. + 31 and
-        // one half of the 256 columns (warps 2..5 the first, 6..9 the second)
+        // one half of the 256 columns (warps 2..5 the first, 6..9 the second).
+        // FP32 outputs: -acc is staged in shared memory (128-byte swizzle) and
+        // added to C by a TMA reduce, so the SM never waits on reading C;
+        // FP64 outputs are read-modify-written from registers.
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        int t = 0;
+        uint8_t *stage = smem + STAGES * STAGE_BYTES + (warp - 2) * 2 * STAGE_C;
+        int t = 0, issued = 0;
         for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
             WorkItem wi;
             if (!work.decode(item, wi)) continue;
@@ -268,18 +289,44 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             tc::tc_fence_after();
             if (!__all_sync(0xffffffffu, ok && !abort_flag)) break;
             const uint32_t d = tbase + (uint32_t)buf * TMEM_COLS + lane_base;
+            if (Work::kReduce && work.reduce_here(wi)) {
+                const int y = work.reduce_row(wi, q * 32);
 #pragma unroll 1
-            for (int cc = half * (BN / 64); cc < (half + 1) * (BN / 64); cc += 2) {
-                float v0[32], v1[32];
-                tc::tmem_ld32(d + (uint32_t)(cc * 32), v0);
-                tc::tmem_ld32(d + (uint32_t)(cc * 32 + 32), v1);
-                work.store2(wi, q * 32 + lane, cc * 32, v0, v1);
+                for (int cc = half * (BN / 64); cc < (half + 1) * (BN / 64); ++cc) {
+                    float v[32];
+                    tc::tmem_ld32(d + (uint32_t)(cc * 32), v);
+                    uint8_t *sb = stage + (issued & 1) * STAGE_C;
+                    if (issued >= 2 && lane == 0) tc::bulk_wait_read<1>();  // the box two back has been read
+                    __syncwarp();
+                    // row `lane`, 16-byte chunk j at chunk position j ^ (lane & 7)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        *reinterpret_cast<float4 *>(sb + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+                            make_float4(-v[4 * j], -v[4 * j + 1], -v[4 * j + 2], -v[4 * j + 3]);
+                    tc::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tc::tma_reduce_add_2d(&mapC, sb, work.reduce_col(wi, cc * 32), y);
+                        tc::bulk_commit();
+                    }
+                    ++issued;
+                }
+            } else {
+#pragma unroll 1
+                for (int cc = half * (BN / 64); cc < (half + 1) * (BN / 64); cc += 2) {
+                    float v0[32], v1[32];
+                    tc::tmem_ld32(d + (uint32_t)(cc * 32), v0);
+                    tc::tmem_ld32(d + (uint32_t)(cc * 32 + 32), v1);
+                    work.store2(wi, q * 32 + lane, cc * 32, v0, v1);
+                }
             }
             tc::tc_fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&tempty[buf]);
             ++t;
         }
+        if (lane == 0) tc::bulk_wait_all();  // every reduce issued by this warp has landed
+        __syncwarp();
     }
     __syncwarp();  // lane 0 of the producer / MMA warps rejoins its warp here
     __syncthreads();
@@ -340,18 +387,35 @@ int num_sms()
 // reserve > 0 leaves that many SMs free for kernels on other streams (the
 // factorisation's critical chain runs beside the update).
 template <int FMT, class Work>
-cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const Work &w, int64_t items, int kchunks,
-                        int *err, cudaStream_t s, int reserve = 0)
+cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Work &w,
+                        int64_t items, int kchunks, int *err, cudaStream_t s, int reserve = 0)
 {
     cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<FMT, Work>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int64_t ctas = num_sms() - reserve > 1 ? num_sms() - reserve : 1;
     const int64_t grid = items < ctas ? items : ctas;
-    k_tc_gemm<FMT, Work><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, w, items, kchunks, err);
+    k_tc_gemm<FMT, Work><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, mc, w, items, kchunks, err);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+// Map over the off-band FP32 tile array viewed as rows x b floats, box
+// 32 x 32 with the 128-byte swizzle: the target of the epilogue's TMA reduce.
+cudaError_t make_offband_map(const float *f32, int b, size_t ntiles, CUtensorMap *mapC)
+{
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const uint64_t rows = (uint64_t)(ntiles > 0 ? ntiles : 1) * (uint64_t)b;
+    cuuint64_t dims[2] = {(cuuint64_t)b, rows};
+    cuuint64_t strides[1] = {(cuuint64_t)b * 4};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(mapC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(f32), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 // Panel maps for the trailing update: the panel buffer holds rows
 // (T - 1) * b of K = b operand elements.
@@ -363,8 +427,8 @@ cudaError_t make_panel_maps(const void *panel, int fmt, int b, int T, CUtensorMa
     return e;
 }
 
-cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, int fmt, const Tiles &tl, int k,
-                             int *err, cudaStream_t s, KernelTimer *kt, int part)
+cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, const CUtensorMap &mapC, int fmt,
+                             const Tiles &tl, int k, int *err, cudaStream_t s, KernelTimer *kt, int part)
 {
     // part 0: every trailing tile; 1: column k + 1 only; 2: columns k + 2 .. T - 1
     const int64_t r = tl.T - k - 1;
@@ -384,8 +448,8 @@ cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, i
     cudaError_t e;
     if (kt) kt->begin(KC_UPDATE, s);
     const int reserve = (part == 2) ? kReserveSms : 0;
-    if (fmt == 2) e = launch_gemm<2>(mapA, mapB, w, blocks, kchunks, err, s, reserve);
-    else e = launch_gemm<1>(mapA, mapB, w, blocks, kchunks, err, s, reserve);
+    if (fmt == 2) e = launch_gemm<2>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
+    else e = launch_gemm<1>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
     if (kt) kt->end(KC_UPDATE, s);
     return e;
 }
@@ -413,8 +477,8 @@ extern "C" egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, 
     cudaMemsetAsync(err, 0, sizeof(int), s);
     DenseWork w{C, N, M / BM, N / BN};
     const int kchunks = K / (fmt == 2 ? 32 : 64);
-    if (fmt == 2) e = launch_gemm<2>(ma, mb, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s);
-    else e = launch_gemm<1>(ma, mb, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s);
+    if (fmt == 2) e = launch_gemm<2>(ma, mb, ma, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s);
+    else e = launch_gemm<1>(ma, mb, ma, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(err, s);

@@ -202,3 +202,18 @@ def test_bad_sizes(egs):
         egs.egs_loglik(locs_dev(locs), dev(np.ones(100)), (1, 0.1, 0.5), 0)
     with pytest.raises(egs.EgsError):
         egs.egs_loglik_ex(locs_dev(locs), dev(np.ones(100)), (1, 0.1, 0.5), 100, "fp64", tile=100)
+
+
+@pytest.mark.parametrize("n,tile", [(900, 128), (1600, 320)])
+def test_simulate_matches_oracle(egs, n, tile):
+    """Algorithm 1 on the GPU: z = L e against the oracle's L e."""
+    from gpu_util import locs_dev, dev
+    import torch
+    theta = (1.0, 0.1, 0.5)
+    p = ei.Problem(n=n, theta=theta, seed=8)
+    locs, e = p.locations(), p.e()
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    egs.egs_simulate(locs_dev(locs), dev(e), theta, n, z, tile=tile)
+    want = oracle.simulate_z(locs, theta, e)
+    got = z.cpu().numpy()
+    assert np.allclose(got, want, rtol=1e-11, atol=1e-12 * np.abs(want).max())
