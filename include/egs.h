@@ -176,6 +176,18 @@ egs_status egs_trsv_tiles_noalloc(const void *tiles, int64_t n, int32_t tile, co
                                   double *logdet, double *quad, void *stream);
 
 /*
+ * egs_simulate - synthetic measurements, Algorithm 1 (Section 5.3): generate
+ * Sigma(theta) at the locations, factor Sigma = L L^T in FP64 (dpotrf) and
+ * form Z = L e (dtrmm) for a caller-supplied e (normally e ~ N(0, I)).
+ *   locs  2n doubles (x then y), device or host;  e  n doubles, device or host
+ *   z     device, n doubles, written.  tile 0 = default.
+ * EGS_ERR_NOT_PD if Sigma(theta) is not positive definite in FP64.
+ * Synchronises stream.
+ */
+egs_status egs_simulate(const double *locs, const double *e, const double theta[3], int64_t n, int32_t tile, double *z,
+                        void *stream);
+
+/*
  * egs_loglik - one evaluation of Eq. 1 (Algorithm 2) at theta.
  *   locs  2n doubles (x then y), device or host memory
  *   z     n doubles, device or host memory

@@ -379,4 +379,23 @@ __device__ __forceinline__ void gemv_rows(const E *__restrict__ A, int b, int r0
     }
 }
 
+// FP32 variant for the off-band tiles of the mixed-precision solves: the
+// products and the row sum run in FP32 (the tile itself is only FP32
+// accurate, and the quadratic form is recovered by the FP64 refinement); the
+// FP32 row sum is subtracted from the FP64 residual.  ys32: y in FP32.
+__device__ __forceinline__ void gemv_rows_f32(const float *__restrict__ A, int b, int r0, const float *ys32,
+                                              double *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rr = 0; rr < 8; ++rr) {
+        const int r = r0 + warp * 8 + rr;
+        const float *row = A + (size_t)r * b;
+        float s = 0.0f;
+        for (int c = lane; c < b; c += 32) s = fmaf(row[c], ys32[c], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) out[r] -= (double)s;
+    }
+}
+
 }  // namespace egs

@@ -172,12 +172,22 @@ __global__ void __launch_bounds__(1024) k_trsv_diag_T(Tiles tl, int k, double *_
     v[(size_t)k * b + i] = xv[i];
 }
 
-template <typename E>
-__device__ __forceinline__ double col_dot(const E *__restrict__ A, int b, int c, int g, const double *xs)
+__device__ __forceinline__ double col_dot(const double *__restrict__ A, int b, int c, int g, const double *xs,
+                                          const float *)
 {
     double s = 0.0;
-    for (int r = g; r < b; r += 4) s = fma((double)A[(size_t)r * b + c], xs[r], s);
+    for (int r = g; r < b; r += 4) s = fma(A[(size_t)r * b + c], xs[r], s);
     return s;
+}
+
+// Off-band (FP32) tiles: products and the partial sum in FP32 (the tile is
+// only FP32 accurate; the refinement recovers the quadratic form in FP64).
+__device__ __forceinline__ double col_dot(const float *__restrict__ A, int b, int c, int g, const double *,
+                                          const float *xs32)
+{
+    float s = 0.0f;
+    for (int r = g; r < b; r += 4) s = fmaf(A[(size_t)r * b + c], xs32[r], s);
+    return (double)s;
 }
 
 // r_j -= L_kj^T x_k for j < k.  grid = (k, b/64); 64 columns x 4 row groups,
@@ -186,12 +196,17 @@ __global__ void __launch_bounds__(256) k_gemv_T(Tiles tl, int k, double *__restr
 {
     if (mfailed(st)) return;
     __shared__ double xs[1024];
+    __shared__ float xs32[1024];
     __shared__ double red[4][64];
     const int b = tl.b, j = (int)blockIdx.x, c0 = (int)blockIdx.y * 64;
     const int tx = threadIdx.x & 63, g = threadIdx.x >> 6;
-    for (int c = threadIdx.x; c < b; c += 256) xs[c] = v[(size_t)k * b + c];
+    for (int c = threadIdx.x; c < b; c += 256) {
+        xs[c] = v[(size_t)k * b + c];
+        xs32[c] = (float)xs[c];
+    }
     __syncthreads();
-    const double s = tl.is64(k, j) ? col_dot(tl.t64(k, j), b, c0 + tx, g, xs) : col_dot(tl.t32(k, j), b, c0 + tx, g, xs);
+    const double s = tl.is64(k, j) ? col_dot(tl.t64(k, j), b, c0 + tx, g, xs, xs32)
+                                   : col_dot(tl.t32(k, j), b, c0 + tx, g, xs, xs32);
     red[g][tx] = s;
     __syncthreads();
     if (g == 0) v[(size_t)j * b + c0 + tx] -= ((red[0][tx] + red[1][tx]) + red[2][tx]) + red[3][tx];

@@ -48,10 +48,16 @@ __global__ void __launch_bounds__(256) k_gemv_panel(Tiles tl, int k, double *__r
     const int b = tl.b;
     const int m = k + 1 + (int)blockIdx.x;
     const int r0 = (int)blockIdx.y * 64;
-    for (int c = threadIdx.x; c < b; c += 256) ys[c] = zpad[(size_t)k * b + c];
+    const bool f64 = tl.is64(m, k);
+    float *ys32 = reinterpret_cast<float *>(ys + b);
+    for (int c = threadIdx.x; c < b; c += 256) {
+        const double v = zpad[(size_t)k * b + c];
+        ys[c] = v;
+        ys32[c] = (float)v;
+    }
     __syncthreads();
-    if (tl.is64(m, k)) gemv_rows(tl.t64(m, k), b, r0, ys, zpad + (size_t)m * b);
-    else gemv_rows(tl.t32(m, k), b, r0, ys, zpad + (size_t)m * b);
+    if (f64) gemv_rows(tl.t64(m, k), b, r0, ys, zpad + (size_t)m * b);
+    else gemv_rows_f32(tl.t32(m, k), b, r0, ys32, zpad + (size_t)m * b);
 }
 
 // l = -1/2 quad - 1/2 logdet - n/2 log(2 pi) from the per-tile partials.
@@ -123,8 +129,8 @@ cudaError_t launch_forward_solve(const Tiles &tl, double *zpad, double *partials
         EGS_LAUNCH(kt, KC_TRSV, s, k_trsv_diag_f64<<<1, b, 0, s>>>(tl, k, zpad, partials, st));
         if (k + 1 < T)
             EGS_LAUNCH(kt, KC_TRSV, s,
-                       k_gemv_panel<<<dim3((unsigned)(T - k - 1), (unsigned)(b / 64)), 256, (size_t)b * sizeof(double),
-                                      s>>>(tl, k, zpad, st));
+                       k_gemv_panel<<<dim3((unsigned)(T - k - 1), (unsigned)(b / 64)), 256,
+                                      (size_t)b * (sizeof(double) + sizeof(float)), s>>>(tl, k, zpad, st));
     }
     return cudaGetLastError();
 }
