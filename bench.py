@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="egs", choices=["egs", "reference"])
-    ap.add_argument("--precision", default="tf32", choices=["fp64", "tf32", "bf16"])
+    ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--n", type=int, default=102400, help="development override; the workload is n=102400")
     ap.add_argument("--tile", type=int, default=512)
     ap.add_argument("--band", type=int, default=2)
@@ -84,6 +84,20 @@ def band_band_flops(n: int, b: int, band: int) -> float:
     return tot
 
 
+def band_out_flops(n: int, b: int, band: int) -> float:
+    """Updates whose output is a band tile (m - n < band) but whose operands
+    are not both band tiles: FP64 in the FP32 (split-TF32) mode."""
+    T = -(-n // b)
+    tot = 0.0
+    for k in range(T - 1):
+        for c in range(k + 1, T):
+            for d in range(band):
+                m = c + d
+                if m < T and m - k >= band:
+                    tot += b ** 3 if d == 0 else 2 * b ** 3
+    return tot
+
+
 def tensor_peak(precision: str) -> dict:
     """Dense tensor peak for the operand type, from the measured bf16 figure."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -95,7 +109,7 @@ def tensor_peak(precision: str) -> dict:
     except Exception:
         bf16 = 1900.0
         src = "fallback bf16 1.9 PFLOP/s"
-    if precision == "tf32":
+    if precision in ("tf32", "fp32"):
         return {"tflops": bf16 * 0.5, "source": src + " x 1/2 (nominal tf32:bf16 dense ratio 1.1:2.25)"}
     return {"tflops": bf16, "source": src}
 
@@ -434,6 +448,7 @@ def main():
         upd_ms = statistics.mean(i["ms_update"] for i in infos)
         launches_update = fc["T"] - 1
         classes = {"update": statistics.mean(i["ms_update"] for i in infos),
+                   "update_f64": statistics.mean(i["ms_update_f64"] for i in infos),
                    "potrf": statistics.mean(i["ms_potrf"] for i in infos),
                    "trsm": statistics.mean(i["ms_trsm"] for i in infos),
                    "trsv": statistics.mean(i["ms_trsv"] for i in infos),
@@ -446,15 +461,32 @@ def main():
                     "launches_per_step": launches_update,
                     "flops_per_launch": fc["update"] / launches_update, "ms_per_launch": upd_ms / launches_update}
         else:
-            # tensor-core trailing update: every update except the FP64 band x band tiles
-            tc_flops = fc["update"] - band_band_flops(n, tile, a.band)
-            achieved = tc_flops / (upd_ms / 1e3) / 1e12
+            # tensor-core trailing update: every update except the FP64 band x
+            # band tiles (FP32 mode: except every band output, and each
+            # update is three TF32 products hi hi' + lo hi' + hi lo')
+            f64_flops = band_band_flops(n, tile, a.band)
+            tc_flops = fc["update"] - f64_flops
+            products = 1
+            if a.precision == "fp32":
+                bo = band_out_flops(n, tile, a.band)
+                tc_flops -= bo
+                f64_flops += bo
+                products = 3
+            achieved = products * tc_flops / (upd_ms / 1e3) / 1e12
             peak = tensor_peak(a.precision)
             roof = {"bound": "tensor", "kernel": "k_tc_gemm (tcgen05 trailing update, %s)" % a.precision,
                     "achieved": achieved, "peak": peak["tflops"], "unit": "TFLOP/s", "frac": achieved / peak["tflops"],
-                    "traffic": None, "peak_source": peak["source"], "launches_per_step": launches_update,
-                    "flops_per_launch": tc_flops / launches_update, "ms_per_launch": upd_ms / launches_update,
-                    "note": "ms_update also includes the small FP64 band x band update launches"}
+                    "traffic": None, "peak_source": peak["source"], "launches_per_step": 2 * launches_update,
+                    "flops_per_launch": products * tc_flops / (2 * launches_update),
+                    "ms_per_launch": upd_ms / (2 * launches_update),
+                    "note": "executed TF32/BF16 MMA flops (%d product(s) per update) over the tcgen05 launches' "
+                            "event time (two launches per step: column k+1, then the rest)" % products}
+            upd64 = statistics.mean(i["ms_update_f64"] for i in infos)
+            if upd64 > 0:
+                a64 = f64_flops / (upd64 / 1e3) / 1e12
+                roof["fp64_updates"] = {"kernel": "k_update_f64 / k_update_band_out", "achieved": a64,
+                                        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": a64 / FP64_PEAK_TFLOPS,
+                                        "flops_per_step": f64_flops, "ms_per_step": upd64}
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f64+" + a.precision,

@@ -66,7 +66,9 @@ typedef enum {
 
 typedef enum {
     EGS_FP64 = 0,     /* everything in double */
-    EGS_MIX_FP32 = 1, /* FP64 band; off-band tiles FP32, updates in FP32 */
+    EGS_MIX_FP32 = 1, /* FP64 band; off-band tiles FP32; updates of band tiles in
+                         FP64, of off-band tiles on tcgen05 as split TF32
+                         (hi hi' + lo hi' + hi lo', FP32-accurate products) */
     EGS_MIX_TF32 = 2, /* FP64 band; off-band tiles FP32, updates on tcgen05 TF32 */
     EGS_MIX_BF16 = 3  /* FP64 band; off-band operands BF16, FP32 accumulation */
 } egs_precision;
@@ -94,6 +96,9 @@ typedef struct {
     double ms_trsm;       /* timing = 2: panel TRSM kernels */
     double ms_update;     /* timing = 2: SYRK/GEMM trailing-update kernels */
     double ms_trsv;       /* timing = 2: solve kernels */
+    double ms_update_f64; /* timing = 2, mixed precision: the FP64 update launches
+                             (band x band, and in EGS_MIX_FP32 every band output);
+                             ms_update then counts only the tensor-core update */
 } egs_info;
 
 /* Optional knobs for egs_loglik_ex.  Zero-initialise for defaults. */

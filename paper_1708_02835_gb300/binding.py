@@ -38,7 +38,8 @@ class egs_info(ctypes.Structure):
                 ("band", ctypes.c_int32), ("launches", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
                 ("quad_unrefined", ctypes.c_double), ("ms_generate", ctypes.c_double), ("ms_factor", ctypes.c_double),
                 ("ms_solve", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_potrf", ctypes.c_double),
-                ("ms_trsm", ctypes.c_double), ("ms_update", ctypes.c_double), ("ms_trsv", ctypes.c_double)]
+                ("ms_trsm", ctypes.c_double), ("ms_update", ctypes.c_double), ("ms_trsv", ctypes.c_double),
+                ("ms_update_f64", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

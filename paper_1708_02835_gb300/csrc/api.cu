@@ -72,14 +72,13 @@ static Layout make_layout(const TileGeom &g)
 }
 
 
-static int mix_fmt(egs_precision p) { return p == EGS_MIX_TF32 ? 2 : 1; }
+static int mix_fmt(egs_precision p) { return p == EGS_MIX_FP32 ? 3 : (p == EGS_MIX_TF32 ? 2 : 1); }
 
 static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision p)
 {
     MixedLayout L;
     const size_t bb = g.tile_elems();
     const size_t npad = (size_t)g.T * g.b;
-    const size_t esz = (mix_fmt(p) == 2) ? 4 : 2;
     size_t off = 0;
     L.f64 = off;
     off += align256(Tiles::f64_tiles(g.T, band) * bb * sizeof(double));
@@ -88,7 +87,7 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
     L.sig = off;
     off += align256(g.ntiles() * bb * sizeof(double));
     L.panel = off;
-    off += 2 * align256((size_t)(g.T > 1 ? g.T - 1 : 1) * bb * esz);
+    off += 2 * align256(panel_buffer_bytes(g.b, g.T, mix_fmt(p)));
     L.locs = off;
     off += align256((size_t)2 * g.n * sizeof(double));
     L.z = off;
@@ -105,7 +104,7 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
     return L;
 }
 
-static bool mixed_p(egs_precision p) { return p == EGS_MIX_TF32 || p == EGS_MIX_BF16; }
+static bool mixed_p(egs_precision p) { return p == EGS_MIX_FP32 || p == EGS_MIX_TF32 || p == EGS_MIX_BF16; }
 
 static void status_init(DevStatus *st, cudaStream_t s)
 {
@@ -160,9 +159,8 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
         const MixedLayout &ML = es.ML;
         mb.tl = Tiles{(double *)(ws + ML.f64), (float *)(ws + ML.f32), g.b, g.T, es.band};
         mb.sig = (double *)(ws + ML.sig);
-        const size_t esz = (mix_fmt(es.p) == 2) ? 4 : 2;
         mb.panel[0] = ws + ML.panel;
-        mb.panel[1] = ws + ML.panel + align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.tile_elems() * esz);
+        mb.panel[1] = ws + ML.panel + align256(panel_buffer_bytes(g.b, g.T, mix_fmt(es.p)));
         double *v = (double *)(ws + ML.vec);
         const size_t stride = align256(npad * sizeof(double)) / sizeof(double);
         mb.zp = v;
@@ -384,6 +382,7 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
         info->ms_trsm = kt.ms(KC_TRSM);
         info->ms_update = kt.ms(KC_UPDATE);
         info->ms_trsv = kt.ms(KC_TRSV);
+        info->ms_update_f64 = kt.ms(KC_UPDATE64);
     }
     const int64_t fi = (h.fail_index == kNoFail) ? -1 : (int64_t)h.fail_index;
     if (fi >= 0) return set_error(EGS_ERR_NOT_PD, "not positive definite at row %lld (tile %lld)", (long long)fi,

@@ -161,10 +161,11 @@ __device__ __forceinline__ bool potrf64_smem(double *A, int ld, int64_t row0, De
 
 // ---------------------------------------------------------------------------
 // C (32 x 32, row stride ldc) -= Am (32 x K) An (32 x K)^T; 2 x 2 outputs per
-// thread (rows ty + 16 i, columns tx + 16 j).  256 threads.
+// thread (rows ty + 16 i, columns tx + 16 j).  FP64 or FP32 operands, FP64
+// arithmetic.  256 threads.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void gemm_sub32(const double *Am, int lda, const double *An, int ldb, int K, double *C,
-                                           int ldc)
+template <typename EA, typename EB>
+__device__ __forceinline__ void gemm_sub32(const EA *Am, int lda, const EB *An, int ldb, int K, double *C, int ldc)
 {
     __shared__ double As[kPW][33];
     __shared__ double Bs[kPW][33];
@@ -173,8 +174,8 @@ __device__ __forceinline__ void gemm_sub32(const double *Am, int lda, const doub
     for (int p = 0; p < K; p += kPW) {
         for (int e = tid; e < 32 * kPW; e += 256) {
             const int r = e >> 4, l = e & 15;
-            As[l][r] = Am[(size_t)r * lda + p + l];
-            Bs[l][r] = An[(size_t)r * ldb + p + l];
+            As[l][r] = (double)Am[(size_t)r * lda + p + l];
+            Bs[l][r] = (double)An[(size_t)r * ldb + p + l];
         }
         __syncthreads();
 #pragma unroll
@@ -254,10 +255,12 @@ __device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, double *Xp,
 
 // ---------------------------------------------------------------------------
 // C (64 x 64, row stride ldc) -= Am (64 x K) An (64 x K)^T with row strides
-// lda, ldb.  4 x 4 outputs per thread (rows ty + 16 i, columns tx + 16 j, so a
+// lda, ldb; the operands may be FP64 or FP32 (widened to FP64 on staging, so
+// the products and sums are FP64 either way).  4 x 4 outputs per thread (rows ty + 16 i, columns tx + 16 j, so a
 // half-warp touches 128 contiguous bytes).  256 threads.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void gemm_sub64(const double *Am, int lda, const double *An, int ldb, int K, double *C, int ldc)
+template <typename EA, typename EB>
+__device__ __forceinline__ void gemm_sub64(const EA *Am, int lda, const EB *An, int ldb, int K, double *C, int ldc)
 {
     __shared__ double As[kPW][65];
     __shared__ double Bs[kPW][65];
@@ -270,8 +273,8 @@ __device__ __forceinline__ void gemm_sub64(const double *Am, int lda, const doub
     for (int p = 0; p < K; p += kPW) {
         for (int e = tid; e < 64 * kPW; e += 256) {
             const int r = e >> 4, l = e & 15;
-            As[l][r] = Am[(size_t)r * lda + p + l];
-            Bs[l][r] = An[(size_t)r * ldb + p + l];
+            As[l][r] = (double)Am[(size_t)r * lda + p + l];
+            Bs[l][r] = (double)An[(size_t)r * ldb + p + l];
         }
         __syncthreads();
 #pragma unroll

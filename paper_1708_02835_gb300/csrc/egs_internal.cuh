@@ -64,7 +64,8 @@ struct TileGeom {
 };
 
 // Kernel classes for per-class device timing.
-enum KernelClass { KC_GEN = 0, KC_POTRF, KC_TRSM, KC_UPDATE, KC_TRSV, KC_OTHER, KC_COUNT };
+// KC_UPDATE64: the FP64 update launches of the mixed-precision factorisation.
+enum KernelClass { KC_GEN = 0, KC_POTRF, KC_TRSM, KC_UPDATE, KC_TRSV, KC_OTHER, KC_UPDATE64, KC_COUNT };
 
 // Counts launches and, when enabled, brackets each launch with a CUDA event
 // pair on the launching stream so the summed duration of each kernel class
@@ -141,13 +142,13 @@ cudaError_t launch_matern_tiles(const double *X, const double *Y, int64_t n, con
 struct MixedBuffers {
     Tiles tl;
     double *sig;      // dense FP64 lower tiles of Sigma (for the refinement residual)
-    void *panel[2];   // two buffers of (T-1) * b * b operands (FP32 for TF32, BF16), step k uses k % 2
+    void *panel[2];   // two operand buffers of panel_buffer_bytes each, step k uses k % 2
     double *zp, *y, *x, *d, *res, *rows, *cols;  // T*b vectors
     double *partials; // 2T
     int *err;
 };
 
-// One mixed-precision evaluation (fmt 2 = TF32, 1 = BF16 operands); the
+// One mixed-precision evaluation (fmt 3 = split TF32, 2 = TF32, 1 = BF16); the
 // result lands in st->result (loglik, logdet, quad refined, quad unrefined).
 cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, int64_t n, const egs_matern_params &P,
                              int fmt, int refine, const MixedBuffers &mb, DevStatus *st, cudaStream_t s, KernelTimer *kt,
@@ -182,7 +183,12 @@ int32_t default_tile(int64_t n, egs_precision p);
 cudaError_t launch_potrf_diag(const Tiles &tl, int k, DevStatus *st, cudaStream_t s, KernelTimer *kt);
 cudaError_t launch_trsm_f64(const Tiles &tl, int k, int nrows, DevStatus *st, cudaStream_t s, KernelTimer *kt);
 // FP64 update of the first ntri tiles of step k's trailing triangle (row order).
-cudaError_t launch_update_f64(const Tiles &tl, int k, int64_t ntri, DevStatus *st, cudaStream_t s, KernelTimer *kt);
+cudaError_t launch_update_f64(const Tiles &tl, int k, int64_t ntri, DevStatus *st, cudaStream_t s, KernelTimer *kt,
+                              int cls = KC_UPDATE);
+// FP64 update of the band tiles of columns col0 .. col0 + ncols - 1 whose
+// panel operands are not both FP64 band tiles (mixed storage, FP32 mode).
+cudaError_t launch_update_band_out(const Tiles &tl, int k, int col0, int ncols, DevStatus *st, cudaStream_t s,
+                                   KernelTimer *kt, int cls = KC_UPDATE64);
 cudaError_t launch_forward_solve(const Tiles &tl, double *zpad, double *partials, DevStatus *st, cudaStream_t s,
                                  KernelTimer *kt);
 cudaError_t launch_finalize(const double *partials, int T, int64_t n, DevStatus *st, cudaStream_t s, KernelTimer *kt);
@@ -195,12 +201,20 @@ cudaError_t launch_trmv_lower(const double *tiles, const TileGeom &g, const doub
 cudaError_t launch_pad_vector(const double *z, int64_t n, double *zpad, int64_t npad, cudaStream_t s,
                               KernelTimer *kt = nullptr);
 
-// Tensor maps over the panel operand buffer ((T-1)*b rows of b elements;
-// fmt 2 = FP32/TF32, 1 = BF16) and the tcgen05 trailing update of step k.
+// Operand formats of the tensor-core update: 1 = BF16, 2 = TF32 (FP32
+// storage), 3 = split TF32 (the A-role copy of each panel row holds
+// [hi | lo | hi], the B-role copy [hi | hi | lo], hi = tf32(x),
+// lo = tf32(x - hi), so one TF32 GEMM over K = 3b gives
+// hi hi^T + lo hi^T + hi lo^T, an FP32-accurate product).
+// Bytes of one panel buffer ((T-1) * b rows) in format fmt.
+size_t panel_buffer_bytes(int b, int T, int fmt);
+// Tensor maps over one panel buffer and the tcgen05 trailing update of step k.
 cudaError_t make_panel_maps(const void *panel, int fmt, int b, int T, CUtensorMap *mapA, CUtensorMap *mapB);
 // Map for the epilogue's TMA reduce into the off-band FP32 tiles.
 cudaError_t make_offband_map(const float *f32, int b, size_t ntiles, CUtensorMap *mapC);
 // part 0: all trailing tiles of step k; 1: column k + 1; 2: columns k + 2 onwards.
+// fmt 3 updates only the off-band outputs (m - n >= band); the band outputs
+// are left to the FP64 kernels.
 cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, const CUtensorMap &mapC, int fmt,
                              const Tiles &tl, int k, int *err, cudaStream_t s, KernelTimer *kt, int part = 0);
 

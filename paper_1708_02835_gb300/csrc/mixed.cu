@@ -5,12 +5,17 @@
 //   POTRF  L_kk in FP64;
 //   TRSM   band rows (m - k < band) in FP64, the other rows in FP32 with
 //          L_kk rounded to FP32; every solved tile is also written to the
-//          panel buffer in the tensor-core operand format (TF32-rounded FP32
-//          or BF16);
+//          panel buffer in the tensor-core operand format (TF32-rounded FP32,
+//          split TF32 hi/lo pairs, or BF16);
 //   UPDATE C_mn -= P_m P_n^T: when both P_m and P_n are FP64 band tiles the
-//          update runs in FP64 (DFMA) on the unrounded values; every other
-//          update runs on tcgen05 with FP32 accumulation (tc_gemm.cu) and is
-//          subtracted in FP64 from band tiles and in FP32 from the others.
+//          update runs in FP64 (DFMA) on the unrounded values.  TF32 / BF16:
+//          every other update runs on tcgen05 with FP32 accumulation
+//          (tc_gemm.cu) and is subtracted in FP64 from band tiles and in FP32
+//          from the others.  FP32 mode (split TF32): each update takes the
+//          precision of its output tile, as in a mixed-precision tile
+//          Cholesky that keeps the band in double -- band outputs in FP64 on
+//          the stored FP32 / FP64 values, off-band outputs on tcgen05 as
+//          hi hi^T + lo hi^T + hi lo^T (FP32-accurate products).
 // The log-determinant 2 sum log L_ii is reduced in FP64 from the FP64
 // diagonal tiles.  The quadratic form Z^T Sigma^-1 Z is won back in FP64 by
 // iterative refinement: x0 = L^-T L^-1 Z, r = Z - Sigma x0 with Sigma the FP64
@@ -35,11 +40,29 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(r);
 }
 
+// Element (row, col) of the panel operand buffer; row counts over all panel
+// tiles ((T-1) b rows), col < b.  FMT 3 (split TF32) writes hi = tf32(v) and
+// lo = tf32(v - hi) (v - hi is exact in FP32) as [hi | lo | hi] into the
+// A-role array and [hi | hi | lo] into the B-role array that follows it.
 template <int FMT>
-__device__ __forceinline__ void panel_store(void *panel, size_t idx, float v)
+__device__ __forceinline__ void panel_store(void *panel, const Tiles &tl, size_t row, int col, float v)
 {
-    if (FMT == 2) reinterpret_cast<float *>(panel)[idx] = to_tf32(v);
-    else reinterpret_cast<__nv_bfloat16 *>(panel)[idx] = __float2bfloat16_rn(v);
+    if (FMT == 3) {
+        const size_t ld = 3 * (size_t)tl.b;
+        float *pa = reinterpret_cast<float *>(panel) + row * ld + col;
+        float *pb = pa + (size_t)(tl.T - 1) * tl.b * ld;
+        const float hi = to_tf32(v), lo = to_tf32(v - hi);
+        pa[0] = hi;
+        pa[tl.b] = lo;
+        pa[2 * tl.b] = hi;
+        pb[0] = hi;
+        pb[tl.b] = hi;
+        pb[2 * tl.b] = lo;
+    } else if (FMT == 2) {
+        reinterpret_cast<float *>(panel)[row * tl.b + col] = to_tf32(v);
+    } else {
+        reinterpret_cast<__nv_bfloat16 *>(panel)[row * tl.b + col] = __float2bfloat16_rn(v);
+    }
 }
 
 // FP64 band panel tiles (m = k+1..k+nrows) -> operand format.
@@ -53,7 +76,8 @@ __global__ void __launch_bounds__(256) k_panel_from_f64(Tiles tl, int k, int nro
         const int t = (int)(e / bb);
         const size_t off = e % bb;
         const int m = k + 1 + t;
-        panel_store<FMT>(panel, (size_t)(m - k - 1) * bb + off, (float)tl.t64(m, k)[off]);
+        panel_store<FMT>(panel, tl, (size_t)(m - k - 1) * tl.b + off / tl.b, (int)(off % tl.b),
+                         (float)tl.t64(m, k)[off]);
     }
 }
 
@@ -71,7 +95,7 @@ __global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0,
     const int r0 = (int)blockIdx.y * 64;
     const double *L = tl.t64(k, k);
     float *A = tl.t32(m, k) + (size_t)r0 * b;
-    const size_t pbase = (size_t)(m - k - 1) * tl.bb() + (size_t)r0 * b;
+    const size_t prow0 = (size_t)(m - k - 1) * b + r0;
     __shared__ __align__(16) float Xt[16][64];   // [l][row]
     __shared__ __align__(16) float Lt[16][32];   // [l][col]
     __shared__ float Ab[64][33];
@@ -131,7 +155,7 @@ __global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0,
             const float v = Ab[r][c];
             const size_t off = (size_t)r * b + c0 + c;
             A[off] = v;
-            panel_store<FMT>(panel, pbase + off, v);
+            panel_store<FMT>(panel, tl, prow0 + r, c0 + c, v);
         }
         __syncthreads();
     }
@@ -373,9 +397,12 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
                                                                                                 panel, st));
         // updates whose two operands are FP64 band tiles stay in FP64 (they
         // carry the nearest-neighbour entries that set the diagonal pivots)
-        if (e == cudaSuccess) e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, s, kt);
+        if (e == cudaSuccess) e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, s, kt, KC_UPDATE64);
+        // split TF32: the other band outputs of column k + 1 in FP64 too
+        if (e == cudaSuccess && FMT == 3) e = launch_update_band_out(tl, k, k + 1, 1, st, s, kt);
         if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, FMT, tl, k, mb.err, s, kt, 1);
         if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);
+        if (e == cudaSuccess && FMT == 3) e = launch_update_band_out(tl, k, k + 2, T - k - 2, st, s, kt);
         if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, FMT, tl, k, mb.err, s, kt, 2);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
@@ -408,7 +435,9 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     if (e == cudaSuccess) e = make_panel_maps(mb.panel[1], fmt, b, T, &ma[1], &mbm[1]);
     if (e == cudaSuccess) e = make_offband_map(tl.f32, b, Tiles::f32_tiles(T, tl.band), &mc);
     if (e != cudaSuccess) return e;
-    e = (fmt == 2) ? factor_mixed<2>(mb, ma, mbm, mc, st, s, kt) : factor_mixed<1>(mb, ma, mbm, mc, st, s, kt);
+    if (fmt == 3) e = factor_mixed<3>(mb, ma, mbm, mc, st, s, kt);
+    else if (fmt == 2) e = factor_mixed<2>(mb, ma, mbm, mc, st, s, kt);
+    else e = factor_mixed<1>(mb, ma, mbm, mc, st, s, kt);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);
     // y = L^-1 z (log-det and y.y partials), x = L^-T y

@@ -2,16 +2,17 @@
 // the dominant contraction of Algorithm 2's dpotrf (Section 4.2, GEMM/SYRK
 // tasks):  C_mn -= P_m P_n^T  for every tile T > m >= n > k at step k, where
 // P_m is the factored panel tile (m, k) stored in the MMA operand format
-// (TF32-rounded FP32 or BF16) by the TRSM stage.
+// (TF32-rounded FP32, split-TF32 hi/lo copies, or BF16) by the TRSM stage.
 //
-// One CTA computes a 128 x 256 block of one output tile: a single elected
-// thread of warp 0 streams 128-byte-wide K slices of the two operands into a
-// 4-stage shared-memory ring with TMA (128-byte swizzle); one thread of warp 1
-// issues tcgen05.mma (M = 128, N = 256) into a 256-column FP32 accumulator in
-// TMEM and releases each stage with tcgen05.commit; then all four warps read
-// the accumulator back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31)
-// and subtract it from the output tile, in FP64 for band tiles and FP32 for
-// the others.  No cluster multicast is used.
+// A persistent kernel (one CTA per SM) loops over 128 x 256 blocks of the
+// output tiles: one elected thread of warp 0 streams 128-byte-wide K slices of
+// the two operands into a 3-stage shared-memory ring with TMA (128-byte
+// swizzle); one thread of warp 1 issues tcgen05.mma (M = 128, N = 256) into
+// one of two 256-column FP32 accumulators in TMEM and releases each stage with
+// tcgen05.commit; eight epilogue warps drain the other accumulator with
+// tcgen05.ld and subtract it from the output tile -- by a TMA reduce-add for
+// FP32 tiles, by a read-modify-write in FP64 for band tiles.  No cluster
+// multicast is used.
 #include "egs_internal.cuh"
 #include "tc_common.cuh"
 
@@ -37,12 +38,14 @@ struct WorkItem {
 
 // Trailing update of step k over the lower-tile storage: the output tiles
 // (m, n) with m >= n >= col0 (one_col: only n = col0).  Panel tile m of
-// step k is operand row block m - k - 1.
+// step k is operand row block m - k - 1.  skip_band: leave every band output
+// (m - n < band) to the FP64 kernels (split-TF32 mode).
 struct UpdateWork {
     Tiles tl;
     int k;
     int col0;
     int one_col;
+    int skip_band;
     __device__ bool decode(int64_t bid, WorkItem &w) const
     {
         const int nrb = tl.b / BM, ncb = tl.b / BN, per = nrb * ncb;
@@ -63,6 +66,7 @@ struct UpdateWork {
         w.rb = blk / ncb;
         w.cb = blk % ncb;
         if (w.m - k < tl.band && w.n - k < tl.band) return false;         // FP64 band x band: done in FP64
+        if (skip_band && w.m - w.n < tl.band) return false;              // band output: done in FP64
         if (w.m == w.n && w.cb * BN > w.rb * BM + BM - 1) return false;  // strictly above the diagonal
         w.ya = (w.m - k - 1) * tl.b + w.rb * BM;
         w.yb = (w.n - k - 1) * tl.b + w.cb * BN;
@@ -362,12 +366,12 @@ cudaError_t make_map(CUtensorMap *m, const void *base, int fmt, uint64_t inner, 
 {
     auto fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
-    const uint32_t esz = (fmt == 2) ? 4 : 2;
+    const uint32_t esz = (fmt == 1) ? 2 : 4;
     cuuint64_t dims[2] = {inner, rows};
     cuuint64_t strides[1] = {inner * esz};
     cuuint32_t box[2] = {128u / esz, box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, fmt == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+    CUresult r = fn(m, fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                     const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -417,11 +421,26 @@ cudaError_t make_offband_map(const float *f32, int b, size_t ntiles, CUtensorMap
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+size_t panel_buffer_bytes(int b, int T, int fmt)
+{
+    const size_t elems = (size_t)(T > 1 ? T - 1 : 1) * (size_t)b * (size_t)b;
+    if (fmt == 3) return 2 * 3 * elems * sizeof(float);
+    return elems * (fmt == 1 ? 2 : 4);
+}
+
 // Panel maps for the trailing update: the panel buffer holds rows
-// (T - 1) * b of K = b operand elements.
+// (T - 1) * b of K = b operand elements (fmt 3: an A-role array and a
+// B-role array, each of K = 3b).
 cudaError_t make_panel_maps(const void *panel, int fmt, int b, int T, CUtensorMap *mapA, CUtensorMap *mapB)
 {
     const uint64_t rows = (uint64_t)(T > 1 ? T - 1 : 1) * (uint64_t)b;
+    if (fmt == 3) {
+        const float *pa = (const float *)panel;
+        const float *pb = pa + rows * 3 * (uint64_t)b;
+        cudaError_t e = make_map(mapA, pa, fmt, 3 * (uint64_t)b, rows, BM);
+        if (e == cudaSuccess) e = make_map(mapB, pb, fmt, 3 * (uint64_t)b, rows, BN);
+        return e;
+    }
     cudaError_t e = make_map(mapA, panel, fmt, (uint64_t)b, rows, BM);
     if (e == cudaSuccess) e = make_map(mapB, panel, fmt, (uint64_t)b, rows, BN);
     return e;
@@ -433,7 +452,7 @@ cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, c
     // part 0: every trailing tile; 1: column k + 1 only; 2: columns k + 2 .. T - 1
     const int64_t r = tl.T - k - 1;
     int64_t ntiles = 0;
-    UpdateWork w{tl, k, k + 1, 0};
+    UpdateWork w{tl, k, k + 1, 0, fmt == 3 ? 1 : 0};
     if (part == 0) ntiles = r * (r + 1) / 2;
     else if (part == 1) {
         ntiles = r;
@@ -444,11 +463,12 @@ cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, c
     }
     if (ntiles <= 0) return cudaSuccess;
     const int64_t blocks = ntiles * (tl.b / BM) * (tl.b / BN);
-    const int kchunks = tl.b / (fmt == 2 ? 32 : 64);
+    // split TF32 (fmt 3) is one TF32 GEMM over K = 3b
+    const int kchunks = fmt == 3 ? 3 * tl.b / 32 : tl.b / (fmt == 2 ? 32 : 64);
     cudaError_t e;
     if (kt) kt->begin(KC_UPDATE, s);
     const int reserve = (part == 2) ? kReserveSms : 0;
-    if (fmt == 2) e = launch_gemm<2>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
+    if (fmt >= 2) e = launch_gemm<2>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
     else e = launch_gemm<1>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
     if (kt) kt->end(KC_UPDATE, s);
     return e;

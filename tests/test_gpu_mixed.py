@@ -1,10 +1,12 @@
-"""Mixed precision (FP64 band, TF32 / BF16 off-band on tcgen05, one FP64
-refinement step of the quadratic form) against the FP64 CPU oracle.
+"""Mixed precision (FP64 band, FP32 / TF32 / BF16 off-band on tcgen05, one
+FP64 refinement step of the quadratic form) against the FP64 CPU oracle.
 
 Stated bars per result (Eq. 1 assembled from the mixed factor's FP64
 log-determinant and the refined quadratic form):
-  TF32: |dl|/|l| <= 1e-6;  BF16: |dl|/|l| <= 5e-5 (BF16 keeps 8 significant
-  bits, so the off-band factor carries ~4e-3 relative rounding per entry).
+  FP32 (split TF32 off-band, every band-tile update in FP64): |dl|/|l| <= 1e-6;
+  TF32: |dl|/|l| <= 1e-6 at these sizes (the error grows about linearly with
+  n);  BF16: |dl|/|l| <= 5e-5 (BF16 keeps 8 significant bits, so the off-band
+  factor carries ~4e-3 relative rounding per entry).
 Single-precision off-band tiles cannot factor very smooth, long-range fields
 (condition numbers beyond 1/eps_FP32); there the mixed path must report
 EGS_ERR_NOT_PD cleanly rather than return a wrong number.
@@ -19,7 +21,7 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"tf32": 1e-6, "bf16": 5e-5}
+TOL = {"fp32": 1e-6, "tf32": 1e-6, "bf16": 5e-5}
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +38,7 @@ def _case(n, theta, seed):
     return locs, z, oracle.loglik_lapack(locs, z, theta)
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
 @pytest.mark.parametrize("n,theta,tile,band", [
     (4096, (1.0, 0.1, 0.5), 256, 2),
     (3000, (1.0, 0.05, 0.8), 256, 2),    # ragged tail, general nu
@@ -53,7 +55,7 @@ def test_mixed_loglik_vs_oracle(egs, prec, n, theta, tile, band):
         abs(info["quad_unrefined"] - ref["quad"]) / ref["quad"]))
     assert info["band"] == band and info["refine_steps"] == 1
     assert rel <= TOL[prec], rel
-    if prec == "tf32":
+    if prec != "bf16":
         # one FP64 refinement step contracts when kappa * eps(factor) < 1; the
         # BF16 factor is too inexact for that to hold on these fields
         assert abs(info["quad"] - ref["quad"]) <= abs(info["quad_unrefined"] - ref["quad"]) + 1e-12 * ref["quad"]
@@ -69,12 +71,34 @@ def test_mixed_smooth_field_reports_not_pd(egs):
         egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "tf32", tile=256)
 
 
-def test_mixed_deterministic(egs):
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_mixed_deterministic(egs, prec):
     from gpu_util import locs_dev, dev
     n, theta = 3000, (1.0, 0.1, 0.5)
     locs, z, _ = _case(n, theta, 5)
-    a = [egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "tf32", tile=256)[0] for _ in range(3)]
+    a = [egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, prec, tile=256)[0] for _ in range(3)]
     assert a[0] == a[1] == a[2]
+
+
+def test_fp32_mode_tracks_fp64_at_n16384(egs):
+    """FP32 mode against the FP64 GPU path (itself pinned to the oracle at
+    1e-10 by the parity tests) at n = 16,384, tile 512, band 2: 32 tiles per
+    side, so the off-band tensor-core work and the FP64 band-output updates
+    both run over many steps."""
+    from gpu_util import locs_dev, dev
+    n, theta = 16384, (1.0, 0.1, 0.5)
+    p = ei.Problem(n=n, theta=theta, seed=11)
+    locs = p.locations()
+    dl = locs_dev(locs)
+    e = dev(p.e())
+    import torch
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    egs.egs_simulate(dl, e, theta, n, z, tile=512)
+    ll64, i64 = egs.egs_loglik_ex(dl, z, theta, n, "fp64", tile=512)
+    ll32, i32 = egs.egs_loglik_ex(dl, z, theta, n, "fp32", tile=512, band=2)
+    rel = abs(ll32 - ll64) / abs(ll64)
+    print("fp32 n=16384 rel l %.2e  dlogdet %.3e" % (rel, i32["logdet"] - i64["logdet"]))
+    assert rel <= TOL["fp32"], rel
 
 
 def test_mixed_small_n_falls_back_to_fp64(egs):
