@@ -66,9 +66,10 @@ typedef enum {
 
 typedef enum {
     EGS_FP64 = 0,     /* everything in double */
-    EGS_MIX_FP32 = 1, /* FP64 band; off-band tiles FP32; updates of band tiles in
-                         FP64, of off-band tiles on tcgen05 as split TF32
-                         (hi hi' + lo hi' + hi lo', FP32-accurate products) */
+    EGS_MIX_FP32 = 1, /* FP64 band; off-band tiles FP32; updates of band tiles
+                         FP64-accurate (DFMA, or exact BF16 slice products on
+                         tcgen05), of off-band tiles on tcgen05 as split TF32
+                         (lo hi' + hi lo' + hi hi', FP32-accurate products) */
     EGS_MIX_TF32 = 2, /* FP64 band; off-band tiles FP32, updates on tcgen05 TF32 */
     EGS_MIX_BF16 = 3  /* FP64 band; off-band operands BF16, FP32 accumulation */
 } egs_precision;
@@ -302,6 +303,21 @@ egs_status egs_serve_destroy(egs_server *server);
  */
 egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, int32_t N, int32_t K, egs_precision p, float *C,
                             void *stream);
+
+/*
+ * egs_ozaki_gemm_test - the FP64-accurate product of the EGS_MIX_FP32 band
+ * updates on its own: C = A B^T with every row of A and B cut into five exact
+ * BF16 slices (row scale a power of two) and the 15 slice products of levels
+ * 2..6 accumulated in FP32 on tcgen05 (levels 2 and 3 exactly), combined in
+ * FP64.  Error about K 2^-35 max|A_i.| max|B_j.| per entry; exact when every
+ * entry of A and B is an integer in [-127, 127].
+ *   A  device, M x K row-major FP64;  B  device, N x K row-major FP64
+ *   C  device, M x N row-major FP64, written
+ * M % 128 == 0, N % 32 == 0, K % 64 == 0, K <= 512.  Synchronises stream;
+ * allocates its slices with cudaMallocAsync on stream.
+ */
+egs_status egs_ozaki_gemm_test(const double *A, const double *B, int32_t M, int32_t N, int32_t K, double *C,
+                               void *stream);
 
 #ifdef __cplusplus
 }

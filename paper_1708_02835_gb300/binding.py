@@ -99,6 +99,7 @@ def load_library(build_if_missing: bool = True):
         "egs_loglik": (c.c_int, [vp, vp, pd, i64, c.c_int, pd, c.POINTER(egs_info), vp]),
         "egs_loglik_ex": (c.c_int, [vp, vp, pd, i64, c.c_int, c.POINTER(egs_opts), pd, c.POINTER(egs_info), vp]),
         "egs_tc_gemm_test": (c.c_int, [vp, vp, i32, i32, i32, c.c_int, vp, vp]),
+        "egs_ozaki_gemm_test": (c.c_int, [vp, vp, i32, i32, i32, vp, vp]),
         "egs_batch_create": (c.c_int, [i32, c.POINTER(i64), i32, c.c_int, c.POINTER(vp)]),
         "egs_batch_run": (c.c_int, [vp, c.POINTER(vp), c.POINTER(vp), pd, pd, c.POINTER(c.c_int), vp]),
         "egs_batch_destroy": (c.c_int, [vp]),
@@ -250,6 +251,13 @@ def egs_tc_gemm_test(A, B, C, precision="tf32", stream=None):
     M, K = A.shape
     N = B.shape[0]
     _check(load_library().egs_tc_gemm_test(_ptr(A), _ptr(B), M, N, K, _prec(precision), _ptr(C), _stream(stream)))
+
+
+def egs_ozaki_gemm_test(A, B, C, stream=None):
+    """C = A B^T (FP64) by exact BF16 slicing on tcgen05 (A: M x K, B: N x K)."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(load_library().egs_ozaki_gemm_test(_ptr(A), _ptr(B), M, N, K, _ptr(C), _stream(stream)))
 
 
 class egs_batch:

@@ -153,51 +153,6 @@ cudaError_t launch_update_f64(const Tiles &tl, int k, int64_t ntri, DevStatus *s
     return cudaGetLastError();
 }
 
-// Mixed storage, FP32-accurate mode: every update whose output is a band tile
-// (m - n < band) runs in FP64, also when a panel operand is an FP32 off-band
-// tile.  Outputs (m, n) for n = col0 + blockIdx.x / band and
-// m = n + blockIdx.x % band; pairs with both operands in the band
-// (m - k < band, which implies n - k < band) are left to k_update_f64, so A_mk
-// is always FP32 here and A_nk is FP64 when n - k < band.  SB x SB sub-blocks.
-template <int SB>
-__global__ void __launch_bounds__(256) k_update_band_out(Tiles tl, int k, int col0, DevStatus *st)
-{
-    if (failed(st)) return;
-    const int b = tl.b;
-    const int n = col0 + (int)blockIdx.x / tl.band;
-    const int m = n + (int)blockIdx.x % tl.band;
-    if (m >= tl.T || m - k < tl.band) return;
-    const int nsub = b / SB;
-    const int sr = (int)blockIdx.y / nsub, sc = (int)blockIdx.y % nsub;
-    if (m == n && sc > sr) return;
-    const float *Am = tl.t32(m, k) + (size_t)sr * SB * b;
-    double *C = tl.t64(m, n) + (size_t)sr * SB * b + sc * SB;
-    if (tl.is64(n, k)) {
-        const double *An = tl.t64(n, k) + (size_t)sc * SB * b;
-        if (SB == 64) gemm_sub64(Am, b, An, b, b, C, b);
-        else gemm_sub32(Am, b, An, b, b, C, b);
-    } else {
-        const float *An = tl.t32(n, k) + (size_t)sc * SB * b;
-        if (SB == 64) gemm_sub64(Am, b, An, b, b, C, b);
-        else gemm_sub32(Am, b, An, b, b, C, b);
-    }
-}
-
-cudaError_t launch_update_band_out(const Tiles &tl, int k, int col0, int ncols, DevStatus *st, cudaStream_t s,
-                                   KernelTimer *kt, int cls)
-{
-    if (ncols <= 0) return cudaSuccess;
-    const unsigned gx = (unsigned)ncols * (unsigned)tl.band;
-    const int nsub = tl.b / 64;
-    if ((int64_t)ncols * nsub * nsub < 304) {
-        const int n32 = tl.b / 32;
-        EGS_LAUNCH(kt, cls, s, k_update_band_out<32><<<dim3(gx, (unsigned)(n32 * n32)), 256, 0, s>>>(tl, k, col0, st));
-    } else {
-        EGS_LAUNCH(kt, cls, s, k_update_band_out<64><<<dim3(gx, (unsigned)(nsub * nsub)), 256, 0, s>>>(tl, k, col0, st));
-    }
-    return cudaGetLastError();
-}
-
 cudaError_t launch_potrf_tiles_f64(double *tiles, const TileGeom &g, DevStatus *st, cudaStream_t s, KernelTimer *kt)
 {
     const int T = g.T;

@@ -146,6 +146,8 @@ struct MixedBuffers {
     double *zp, *y, *x, *d, *res, *rows, *cols;  // T*b vectors
     double *partials; // 2T
     int *err;
+    void *oz;         // FP32 mode: BF16 slices of the panel rows (ozaki_slices_bytes)
+    double *ozs;      // FP32 mode: their row scales, (T-1) b doubles
 };
 
 // One mixed-precision evaluation (fmt 3 = split TF32, 2 = TF32, 1 = BF16); the
@@ -159,7 +161,7 @@ struct Layout {
     size_t tiles, locs, z, zpad, partials, status, total;
 };
 struct MixedLayout {
-    size_t f64, f32, sig, panel, locs, z, vec, partials, status, err, total;
+    size_t f64, f32, sig, panel, oz, locs, z, vec, partials, status, err, total;
 };
 struct EvalSetup {
     TileGeom g;
@@ -185,10 +187,16 @@ cudaError_t launch_trsm_f64(const Tiles &tl, int k, int nrows, DevStatus *st, cu
 // FP64 update of the first ntri tiles of step k's trailing triangle (row order).
 cudaError_t launch_update_f64(const Tiles &tl, int k, int64_t ntri, DevStatus *st, cudaStream_t s, KernelTimer *kt,
                               int cls = KC_UPDATE);
-// FP64 update of the band tiles of columns col0 .. col0 + ncols - 1 whose
-// panel operands are not both FP64 band tiles (mixed storage, FP32 mode).
-cudaError_t launch_update_band_out(const Tiles &tl, int k, int col0, int ncols, DevStatus *st, cudaStream_t s,
-                                   KernelTimer *kt, int cls = KC_UPDATE64);
+// FP32 mixed mode: FP64-accurate updates of the band tiles whose panel
+// operands are not both FP64 band tiles, by exact BF16 slicing on tcgen05
+// (ozaki.cu).  The slices of every panel row of step k are written first.
+size_t ozaki_slices_bytes(int b, int T);
+cudaError_t make_ozaki_maps(const void *oz, int b, int T, CUtensorMap *mapA, CUtensorMap *mapB);
+cudaError_t launch_ozaki_slices(const Tiles &tl, int k, void *oz, double *scale, const DevStatus *st, cudaStream_t s,
+                                KernelTimer *kt);
+// Band tiles of columns col0 .. col0 + ncols - 1 at step k.
+cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &mapB, const Tiles &tl, int k, int col0,
+                                  int ncols, const double *scale, int *err, cudaStream_t s, KernelTimer *kt);
 cudaError_t launch_forward_solve(const Tiles &tl, double *zpad, double *partials, DevStatus *st, cudaStream_t s,
                                  KernelTimer *kt);
 cudaError_t launch_finalize(const double *partials, int T, int64_t n, DevStatus *st, cudaStream_t s, KernelTimer *kt);
@@ -203,9 +211,9 @@ cudaError_t launch_pad_vector(const double *z, int64_t n, double *zpad, int64_t 
 
 // Operand formats of the tensor-core update: 1 = BF16, 2 = TF32 (FP32
 // storage), 3 = split TF32 (the A-role copy of each panel row holds
-// [hi | lo | hi], the B-role copy [hi | hi | lo], hi = tf32(x),
+// [lo | hi | hi], the B-role copy [hi | lo | hi], hi = tf32(x),
 // lo = tf32(x - hi), so one TF32 GEMM over K = 3b gives
-// hi hi^T + lo hi^T + hi lo^T, an FP32-accurate product).
+// lo hi^T + hi lo^T + hi hi^T, an FP32-accurate product).
 // Bytes of one panel buffer ((T-1) * b rows) in format fmt.
 size_t panel_buffer_bytes(int b, int T, int fmt);
 // Tensor maps over one panel buffer and the tcgen05 trailing update of step k.

@@ -14,8 +14,9 @@
 //          from the others.  FP32 mode (split TF32): each update takes the
 //          precision of its output tile, as in a mixed-precision tile
 //          Cholesky that keeps the band in double -- band outputs in FP64 on
-//          the stored FP32 / FP64 values, off-band outputs on tcgen05 as
-//          hi hi^T + lo hi^T + hi lo^T (FP32-accurate products).
+//          the stored FP32 / FP64 values (band x band on DFMA, the others as
+//          exact BF16 slice products on tcgen05, ozaki.cu), off-band outputs
+//          on tcgen05 as lo hi^T + hi lo^T + hi hi^T (FP32-accurate products).
 // The log-determinant 2 sum log L_ii is reduced in FP64 from the FP64
 // diagonal tiles.  The quadratic form Z^T Sigma^-1 Z is won back in FP64 by
 // iterative refinement: x0 = L^-T L^-1 Z, r = Z - Sigma x0 with Sigma the FP64
@@ -42,8 +43,9 @@ __device__ __forceinline__ float to_tf32(float x)
 
 // Element (row, col) of the panel operand buffer; row counts over all panel
 // tiles ((T-1) b rows), col < b.  FMT 3 (split TF32) writes hi = tf32(v) and
-// lo = tf32(v - hi) (v - hi is exact in FP32) as [hi | lo | hi] into the
-// A-role array and [hi | hi | lo] into the B-role array that follows it.
+// lo = tf32(v - hi) (v - hi is exact in FP32) as [lo | hi | hi] into the
+// A-role array and [hi | lo | hi] into the B-role array that follows it, so
+// the accumulator takes the two small cross terms before hi hi^T.
 template <int FMT>
 __device__ __forceinline__ void panel_store(void *panel, const Tiles &tl, size_t row, int col, float v)
 {
@@ -52,12 +54,12 @@ __device__ __forceinline__ void panel_store(void *panel, const Tiles &tl, size_t
         float *pa = reinterpret_cast<float *>(panel) + row * ld + col;
         float *pb = pa + (size_t)(tl.T - 1) * tl.b * ld;
         const float hi = to_tf32(v), lo = to_tf32(v - hi);
-        pa[0] = hi;
-        pa[tl.b] = lo;
+        pa[0] = lo;
+        pa[tl.b] = hi;
         pa[2 * tl.b] = hi;
         pb[0] = hi;
-        pb[tl.b] = hi;
-        pb[2 * tl.b] = lo;
+        pb[tl.b] = lo;
+        pb[2 * tl.b] = hi;
     } else if (FMT == 2) {
         reinterpret_cast<float *>(panel)[row * tl.b + col] = to_tf32(v);
     } else {
@@ -359,7 +361,8 @@ cudaError_t backward_solve(const Tiles &tl, double *v, const DevStatus *st, cuda
 // Panels alternate between two buffers.
 template <int FMT>
 cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CUtensorMap *mbm,
-                         const CUtensorMap &mc, DevStatus *st, cudaStream_t s, KernelTimer *kt)
+                         const CUtensorMap &mc, const CUtensorMap *moz, DevStatus *st, cudaStream_t s,
+                         KernelTimer *kt)
 {
     const Tiles &tl = mb.tl;
     const int T = tl.T, b = tl.b;
@@ -397,12 +400,15 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
                                                                                                 panel, st));
         // updates whose two operands are FP64 band tiles stay in FP64 (they
         // carry the nearest-neighbour entries that set the diagonal pivots)
+        // FP32 mode: slice every panel row for the FP64-accurate band outputs
+        if (e == cudaSuccess && FMT == 3) e = launch_ozaki_slices(tl, k, mb.oz, mb.ozs, st, s, kt);
         if (e == cudaSuccess) e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, s, kt, KC_UPDATE64);
-        // split TF32: the other band outputs of column k + 1 in FP64 too
-        if (e == cudaSuccess && FMT == 3) e = launch_update_band_out(tl, k, k + 1, 1, st, s, kt);
+        if (e == cudaSuccess && FMT == 3)
+            e = launch_band_out_ozaki(moz[0], moz[1], tl, k, k + 1, 1, mb.ozs, mb.err, s, kt);
         if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, FMT, tl, k, mb.err, s, kt, 1);
         if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);
-        if (e == cudaSuccess && FMT == 3) e = launch_update_band_out(tl, k, k + 2, T - k - 2, st, s, kt);
+        if (e == cudaSuccess && FMT == 3)
+            e = launch_band_out_ozaki(moz[0], moz[1], tl, k, k + 2, T - k - 2, mb.ozs, mb.err, s, kt);
         if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, FMT, tl, k, mb.err, s, kt, 2);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
@@ -430,14 +436,15 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     cudaError_t e = launch_matern_tiles(X, Y, n, tl, P, mb.sig, s, kt);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
-    CUtensorMap ma[2], mbm[2], mc;
+    CUtensorMap ma[2], mbm[2], mc, moz[2];
     e = make_panel_maps(mb.panel[0], fmt, b, T, &ma[0], &mbm[0]);
     if (e == cudaSuccess) e = make_panel_maps(mb.panel[1], fmt, b, T, &ma[1], &mbm[1]);
     if (e == cudaSuccess) e = make_offband_map(tl.f32, b, Tiles::f32_tiles(T, tl.band), &mc);
+    if (e == cudaSuccess && fmt == 3) e = make_ozaki_maps(mb.oz, b, T, &moz[0], &moz[1]);
     if (e != cudaSuccess) return e;
-    if (fmt == 3) e = factor_mixed<3>(mb, ma, mbm, mc, st, s, kt);
-    else if (fmt == 2) e = factor_mixed<2>(mb, ma, mbm, mc, st, s, kt);
-    else e = factor_mixed<1>(mb, ma, mbm, mc, st, s, kt);
+    if (fmt == 3) e = factor_mixed<3>(mb, ma, mbm, mc, moz, st, s, kt);
+    else if (fmt == 2) e = factor_mixed<2>(mb, ma, mbm, mc, moz, st, s, kt);
+    else e = factor_mixed<1>(mb, ma, mbm, mc, moz, st, s, kt);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);
     // y = L^-1 z (log-det and y.y partials), x = L^-T y

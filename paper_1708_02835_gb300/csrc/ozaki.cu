@@ -1,0 +1,454 @@
+// FP64-accurate products on the BF16 tensor cores by exact slicing (the
+// error-free splitting of Ozaki, Ogita, Oishi and Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 59 (2012)), used
+// by the FP32 mixed mode for every update whose output is an FP64 band tile.
+//
+// Each operand row x (length K) is scaled by a power of two sigma = 2^e with
+// |x| < sigma, u = x 128 / sigma, and cut into five slices
+//   q_1 = rint(u),  q_i = rint((u - q_1 - ... - q_{i-1}) 2^{7(i-1)}) 2^{-7(i-1)},
+// each an integer of at most 8 bits times a power of two, so exact in BF16;
+// x = (sigma / 128) (q_1 + ... + q_5) up to 2^-35 |sigma|.  For a pair of rows
+//   x . y = s_x s_y sum_{i,j} q_i(x) . q_j(y)        (s = sigma / 128)
+// and the slice products are accumulated in FP32 on tcgen05 by level:
+//   acc0 = q_1 . q_1                  integers, |acc0| <= K 2^14 <= 2^23 (K <= 512)
+//   acc1 = q_1 . q_2 + q_2 . q_1      multiples of 2^-7, |acc1| <= 2^23 units
+//   acc2 = the 12 pairs with 4 <= i + j <= 6
+// so acc0 and acc1 are exact in FP32 (the tensor core adds exact BF16
+// products; every partial sum is a representable integer multiple of the
+// level's unit below 2^24 units), and acc2 carries only a rounding error
+// relative to its own, 2^-14-smaller, magnitude.  The FP64 epilogue forms
+// s_x s_y ((acc0 + acc1) + acc2).  Dropping the pairs with i + j > 6 leaves
+// an error of about K 2^-35 s_x s_y 2^14, i.e. 35-bit products, which is the
+// accuracy the band updates need (FP32-accurate products there are not
+// enough; exact FP64 ones are).
+//
+// Kernel: persistent, one CTA per SM, 192 threads.  Warp 0 (one lane) loads
+// the five A slices (128 rows) and five B slices (32 rows) of a 64-element K
+// chunk with TMA (128-byte swizzle) into a 2-stage ring; warp 1 (one lane)
+// issues the 15 MMAs (M = 128, N = 32, K = 16) of every K step into three
+// 32-column TMEM accumulators, double-buffered across work items; warps 2-5
+// read the accumulators with tcgen05.ld and apply the FP64 epilogue.
+#include "egs_internal.cuh"
+#include "tc_common.cuh"
+
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+namespace egs {
+
+namespace {
+
+constexpr int OS = 5;  // slices per operand
+constexpr int OBM = 128, OBN = 32, OSTAGES = 2, OKC = 64;
+constexpr int OA_SL = OBM * 128, OB_SL = OBN * 128;  // bytes of one slice box
+constexpr int OSTAGE = OS * (OA_SL + OB_SL);
+constexpr int OSMEM = OSTAGES * OSTAGE + 1024;
+constexpr int ONUM_THREADS = 192;
+constexpr uint32_t OTMEM_COLS = 256;  // 2 buffers x 3 accumulators x 32 columns, rounded up
+constexpr int NPAIRS = 15;
+
+__device__ __forceinline__ bool ofailed(const DevStatus *st)
+{
+    return st && *(volatile const unsigned long long *)&st->fail_index != kNoFail;
+}
+
+// One warp slices one row of K <= 1024 values (lane owns columns lane + 32 j).
+// Slice i of the row goes to dst[i * slice_stride + c]; the row scale
+// sigma / 128 to *scale.
+template <typename E>
+__device__ __forceinline__ void slice_row(const E *__restrict__ src, int K, __nv_bfloat16 *__restrict__ dst,
+                                          size_t slice_stride, double *scale)
+{
+    const int lane = threadIdx.x & 31;
+    double x[32];
+    double mx = 0.0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int c = lane + 32 * j;
+        x[j] = (c < K) ? (double)src[c] : 0.0;
+        mx = fmax(mx, fabs(x[j]));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    int e = 0;
+    frexp(mx, &e);  // mx = f 2^e with f in [0.5, 1), so |x| < 2^e (mx = 0: e = 0)
+    if (lane == 0) *scale = ldexp(1.0, e - 7);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int c = lane + 32 * j;
+        if (c < K) {
+            double u = ldexp(x[j], 7 - e);  // |u| < 128, exact
+#pragma unroll
+            for (int i = 0; i < OS; ++i) {
+                const double q = ldexp(rint(ldexp(u, 7 * i)), -7 * i);  // exact in BF16
+                dst[(size_t)i * slice_stride + c] = __float2bfloat16_rn((float)q);
+                u -= q;  // exact
+            }
+        }
+    }
+}
+
+// Panel rows of step k (all (T - k - 1) b of them, FP64 band tiles and FP32
+// off-band tiles) -> slices; 8 rows per CTA of 256 threads.
+__global__ void __launch_bounds__(256) k_ozaki_slices_panel(Tiles tl, int k, __nv_bfloat16 *oz, double *scale,
+                                                            size_t R, const DevStatus *st)
+{
+    if (ofailed(st)) return;
+    const int b = tl.b;
+    const size_t pr = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int t = (int)(pr / b), r = (int)(pr % b);
+    const int m = k + 1 + t;
+    __nv_bfloat16 *dst = oz + pr * b;
+    if (tl.is64(m, k)) slice_row(tl.t64(m, k) + (size_t)r * b, b, dst, R * b, scale + pr);
+    else slice_row(tl.t32(m, k) + (size_t)r * b, b, dst, R * b, scale + pr);
+}
+
+// Rows of a dense row-major FP64 matrix (rows x K) -> slices.
+__global__ void __launch_bounds__(256) k_ozaki_slices_dense(const double *X, int rows, int K, __nv_bfloat16 *oz,
+                                                            double *scale)
+{
+    const int r = (int)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    slice_row(X + (size_t)r * K, K, oz + (size_t)r * K, (size_t)rows * K, scale + r);
+}
+
+struct OzItem {
+    int m, n;    // output tile
+    int rb, cb;  // 128-row block, 32-column block
+    int ya, yb;  // operand rows (within one slice) of the A and B boxes
+};
+
+// Band outputs of step k not covered by the FP64 band x band update: tiles
+// (m, n), n = col0 .. col0 + ncols - 1, m = n .. n + band - 1 < T, with
+// m - k >= band.  C_mn -= P_m P_n^T in FP64.
+struct OzBandWork {
+    Tiles tl;
+    int k, col0;
+    __device__ bool decode(int64_t item, OzItem &w) const
+    {
+        const int nrb = tl.b / OBM, ncb = tl.b / OBN, per = nrb * ncb;
+        const int64_t t = item / per;
+        const int blk = (int)(item % per);
+        w.n = col0 + (int)(t / tl.band);
+        w.m = w.n + (int)(t % tl.band);
+        w.rb = blk / ncb;
+        w.cb = blk % ncb;
+        if (w.m >= tl.T || w.m - k < tl.band) return false;
+        if (w.m == w.n && w.cb * OBN > w.rb * OBM + OBM - 1) return false;  // strictly above the diagonal
+        w.ya = (w.m - k - 1) * tl.b + w.rb * OBM;
+        w.yb = (w.n - k - 1) * tl.b + w.cb * OBN;
+        return true;
+    }
+    __device__ void apply(const OzItem &w, int r, const double (&v)[OBN]) const
+    {
+        double *C = tl.t64(w.m, w.n) + (size_t)(w.rb * OBM + r) * tl.b + w.cb * OBN;
+        double2 c[OBN / 2];
+#pragma unroll
+        for (int i = 0; i < OBN / 2; ++i) c[i] = *reinterpret_cast<const double2 *>(C + 2 * i);
+#pragma unroll
+        for (int i = 0; i < OBN / 2; ++i) {
+            c[i].x -= v[2 * i];
+            c[i].y -= v[2 * i + 1];
+        }
+#pragma unroll
+        for (int i = 0; i < OBN / 2; ++i) *reinterpret_cast<double2 *>(C + 2 * i) = c[i];
+    }
+};
+
+// C = A B^T (A: M x K, B: N x K), used to test the pipeline.
+struct OzDenseWork {
+    double *C;
+    int N, ncb;
+    __device__ bool decode(int64_t item, OzItem &w) const
+    {
+        w.rb = (int)(item / ncb);
+        w.cb = (int)(item % ncb);
+        w.m = w.n = 0;
+        w.ya = w.rb * OBM;
+        w.yb = w.cb * OBN;
+        return true;
+    }
+    __device__ void apply(const OzItem &w, int r, const double (&v)[OBN]) const
+    {
+        double *Cp = C + (size_t)(w.rb * OBM + r) * N + w.cb * OBN;
+#pragma unroll
+        for (int i = 0; i < OBN / 2; ++i) *reinterpret_cast<double2 *>(Cp + 2 * i) = make_double2(v[2 * i], v[2 * i + 1]);
+    }
+};
+
+// mapA / mapB: 2-D maps over the slice arrays viewed as (OS * rows) x K BF16,
+// boxes {64, 128} and {64, 32}; slice i of operand row y is map row
+// i * RA + y (i * RB + y).
+template <class Work>
+__global__ void __launch_bounds__(ONUM_THREADS, 1)
+k_tc_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Work work,
+           const double *__restrict__ scA, const double *__restrict__ scB, int RA, int RB, int64_t nitems, int kchunks,
+           int *err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full[OSTAGES], empty[OSTAGES], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ int last_chunk[OSTAGES];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OSTAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+            last_chunk[s] = -1;
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&tfull[b], 1);
+            tc::mbar_init(&tempty[b], 4);
+        }
+        abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, OTMEM_COLS);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tbase = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tc::prefetch_tmap(&mapA);
+            tc::prefetch_tmap(&mapB);
+            int g = 0;
+            for (int64_t item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
+                OzItem wi;
+                if (!work.decode(item, wi)) continue;
+                for (int c = 0; c < kchunks; ++c, ++g) {
+                    const int s = g % OSTAGES;
+                    const uint32_t ph = (uint32_t)(g / OSTAGES) & 1u;
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1u, &abort_flag)) break;
+                    tc::mbar_arrive_expect_tx(&full[s], OSTAGE);
+                    uint8_t *sa = smem + s * OSTAGE, *sb = sa + OS * OA_SL;
+#pragma unroll
+                    for (int i = 0; i < OS; ++i) {
+                        tc::tma_load_2d(&mapA, &full[s], sa + i * OA_SL, c * OKC, i * RA + wi.ya);
+                        tc::tma_load_2d(&mapB, &full[s], sb + i * OB_SL, c * OKC, i * RB + wi.yb);
+                    }
+                    last_chunk[s] = g;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // slice pairs (a, b) and their accumulator: level 2, level 3, levels 4..6
+            constexpr int PA[NPAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
+            constexpr int PB[NPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
+            constexpr int PACC[NPAIRS] = {0, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2};
+            constexpr int PFIRST[NPAIRS] = {1, 1, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            constexpr uint32_t idesc = tc::idesc_f32acc(OBM, OBN, 1);
+            int g = 0, t = 0;
+            for (int64_t item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
+                OzItem wi;
+                if (!work.decode(item, wi)) continue;
+                const int buf = t & 1;
+                const uint32_t use = (uint32_t)(t >> 1);
+                if (!tc::mbar_wait(&tempty[buf], (use & 1u) ^ 1u, &abort_flag)) break;
+                tc::tc_fence_after();
+                const uint32_t d = tbase + (uint32_t)buf * (3 * OBN);
+                for (int c = 0; c < kchunks; ++c, ++g) {
+                    const int s = g % OSTAGES;
+                    const uint32_t ph = (uint32_t)(g / OSTAGES) & 1u;
+                    if (!tc::mbar_wait(&full[s], ph, &abort_flag)) break;
+                    tc::tc_fence_after();
+                    const uint32_t a0 = tc::smem_u32(smem + s * OSTAGE);
+                    const uint32_t b0 = a0 + OS * OA_SL;
+#pragma unroll
+                    for (int j = 0; j < OKC / 16; ++j) {
+#pragma unroll
+                        for (int p = 0; p < NPAIRS; ++p) {
+                            const uint64_t ad = tc::desc_sw128(a0 + PA[p] * OA_SL + 32 * j);
+                            const uint64_t bd = tc::desc_sw128(b0 + PB[p] * OB_SL + 32 * j);
+                            tc::mma_f16(d + (uint32_t)(PACC[p] * OBN), ad, bd, idesc,
+                                        ((c | j) != 0 || !PFIRST[p]) ? 1u : 0u);
+                        }
+                    }
+                    tc::mma_commit(&empty[s]);
+                }
+                tc::mma_commit(&tfull[buf]);
+                ++t;
+            }
+        }
+    } else {
+        // warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. output
+        // rows 32 (w % 4) + lane of the 128-row block
+        const int q = warp & 3;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        int t = 0;
+        for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+            OzItem wi;
+            if (!work.decode(item, wi)) continue;
+            const int buf = t & 1;
+            const uint32_t use = (uint32_t)(t >> 1);
+            const bool ok = tc::mbar_wait(&tfull[buf], use & 1u, &abort_flag);
+            tc::tc_fence_after();
+            if (!__all_sync(0xffffffffu, ok && !abort_flag)) break;
+            const uint32_t d = tbase + (uint32_t)buf * (3 * OBN) + lane_base;
+            float a0v[32], a1v[32], a2v[32];
+            tc::tmem_ld32(d, a0v);
+            tc::tmem_ld32(d + OBN, a1v);
+            tc::tmem_ld32(d + 2 * OBN, a2v);
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[buf]);  // the accumulators are in registers now
+            const int r = q * 32 + lane;
+            const double sa = scA[wi.ya + r];
+            double v[OBN];
+#pragma unroll
+            for (int c = 0; c < OBN; ++c)
+                v[c] = sa * __ldg(scB + wi.yb + c) * (((double)a0v[c] + (double)a1v[c]) + (double)a2v[c]);
+            work.apply(wi, r, v);
+            ++t;
+        }
+    }
+    __syncwarp();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0) {
+        for (int s = 0; s < OSTAGES; ++s)
+            if (last_chunk[s] >= 0) {
+                volatile int dummy = 0;
+                tc::mbar_wait(&full[s], (uint32_t)(last_chunk[s] / OSTAGES) & 1u, &dummy);
+            }
+        atomicExch(err, 1);
+    }
+    tc::tc_fence_after();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, OTMEM_COLS);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 oz_encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D map over OS * rows rows of K BF16, box {64, box_rows}, 128-byte swizzle.
+cudaError_t make_slice_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t K, uint32_t box_rows)
+{
+    auto fn = oz_encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {K, (cuuint64_t)OS * rows};
+    cuuint64_t strides[1] = {K * 2};
+    cuuint32_t box[2] = {(cuuint32_t)OKC, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int oz_num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+template <class Work>
+cudaError_t launch_ozaki(const CUtensorMap &ma, const CUtensorMap &mb, const Work &w, const double *scA,
+                         const double *scB, int RA, int RB, int64_t items, int kchunks, int *err, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_tc_ozaki<Work>, cudaFuncAttributeMaxDynamicSharedMemorySize, OSMEM);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = items < oz_num_sms() ? items : oz_num_sms();
+    k_tc_ozaki<Work><<<(unsigned)grid, ONUM_THREADS, OSMEM, s>>>(ma, mb, w, scA, scB, RA, RB, items, kchunks, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t ozaki_slices_bytes(int b, int T)
+{
+    const size_t R = (size_t)(T > 1 ? T - 1 : 1) * (size_t)b;
+    return (size_t)OS * R * (size_t)b * 2;
+}
+
+cudaError_t make_ozaki_maps(const void *oz, int b, int T, CUtensorMap *mapA, CUtensorMap *mapB)
+{
+    const uint64_t R = (uint64_t)(T > 1 ? T - 1 : 1) * (uint64_t)b;
+    cudaError_t e = make_slice_map(mapA, oz, R, (uint64_t)b, OBM);
+    if (e == cudaSuccess) e = make_slice_map(mapB, oz, R, (uint64_t)b, OBN);
+    return e;
+}
+
+cudaError_t launch_ozaki_slices(const Tiles &tl, int k, void *oz, double *scale, const DevStatus *st, cudaStream_t s,
+                                KernelTimer *kt)
+{
+    const size_t rows = (size_t)(tl.T - k - 1) * tl.b;
+    if (rows == 0) return cudaSuccess;
+    const size_t R = (size_t)(tl.T - 1) * tl.b;
+    EGS_LAUNCH(kt, KC_TRSM, s,
+               k_ozaki_slices_panel<<<(unsigned)(rows / 8), 256, 0, s>>>(tl, k, (__nv_bfloat16 *)oz, scale, R, st));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &mapB, const Tiles &tl, int k, int col0,
+                                  int ncols, const double *scale, int *err, cudaStream_t s, KernelTimer *kt)
+{
+    if (ncols <= 0) return cudaSuccess;
+    const int64_t per = (int64_t)(tl.b / OBM) * (tl.b / OBN);
+    const int64_t items = (int64_t)ncols * tl.band * per;
+    const int R = (tl.T - 1) * tl.b;
+    OzBandWork w{tl, k, col0};
+    cudaError_t e;
+    if (kt) kt->begin(KC_UPDATE64, s);
+    e = launch_ozaki(mapA, mapB, w, scale, scale, R, R, items, tl.b / OKC, err, s);
+    if (kt) kt->end(KC_UPDATE64, s);
+    return e;
+}
+
+}  // namespace egs
+
+using namespace egs;
+
+extern "C" egs_status egs_ozaki_gemm_test(const double *A, const double *B, int32_t M, int32_t N, int32_t K, double *C,
+                                          void *stream)
+{
+    if (M <= 0 || N <= 0 || K <= 0 || M % OBM || N % OBN || K % OKC || K > 512)
+        return set_error(EGS_ERR_ARG, "egs_ozaki_gemm_test: M %% 128, N %% 32, K %% 64 must be 0 and K <= 512");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t sa = (size_t)OS * M * K * 2, sb = (size_t)OS * N * K * 2;
+    char *ws = nullptr;
+    const size_t bytes = sa + sb + (size_t)(M + N) * 8 + 256;
+    cudaError_t e = cudaMallocAsync((void **)&ws, bytes, s);
+    if (e != cudaSuccess) return set_error(EGS_ERR_OOM, "egs_ozaki_gemm_test: workspace");
+    __nv_bfloat16 *oa = (__nv_bfloat16 *)ws, *ob = (__nv_bfloat16 *)(ws + sa);
+    double *sca = (double *)(ws + sa + sb), *scb = sca + M;
+    int *err = (int *)(scb + N);
+    CUtensorMap ma, mb;
+    e = make_slice_map(&ma, oa, (uint64_t)M, (uint64_t)K, OBM);
+    if (e == cudaSuccess) e = make_slice_map(&mb, ob, (uint64_t)N, (uint64_t)K, OBN);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_ozaki_slices_dense<<<(unsigned)((M + 7) / 8), 256, 0, s>>>(A, M, K, oa, sca);
+        k_ozaki_slices_dense<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(B, N, K, ob, scb);
+        e = cudaGetLastError();
+    }
+    OzDenseWork w{C, N, N / OBN};
+    if (e == cudaSuccess) e = launch_ozaki(ma, mb, w, sca, scb, M, N, (int64_t)(M / OBM) * (N / OBN), K / OKC, err, s);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(ws, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error(EGS_ERR_CUDA, "egs_ozaki_gemm_test: %s", cudaGetErrorString(e));
+    if (herr) return set_error(EGS_ERR_TIMEOUT, "egs_ozaki_gemm_test: a pipeline wait timed out");
+    return EGS_OK;
+}

@@ -43,3 +43,50 @@ def test_tc_gemm_matches_fp64(M, N, K, prec):
     scale = np.abs(a64) @ np.abs(b64).T
     assert np.all(np.isfinite(got))
     assert np.all(np.abs(got - ref) <= 2.0 ** -16 * scale)
+
+
+def _rows_scaled(rng, shape, spread):
+    """Gaussian rows with row scales spread over 2^-spread .. 2^spread and
+    entries spanning a few binades inside each row."""
+    x = rng.standard_normal(shape) * np.exp2(rng.uniform(-3, 3, shape))
+    return x * np.exp2(rng.integers(-spread, spread + 1, (shape[0], 1)))
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 32, 64), (256, 96, 512), (384, 160, 256)])
+def test_ozaki_gemm_accuracy(M, N, K):
+    """FP64 slice product: |C - A B^T| <= K 2^-31 max|A_i.| max|B_j.|.  Worst
+    cases: the five slices leave each entry within 2^-35 max|row| (K 2^-34
+    in the product), the dropped pairs i + j > 6 add at most K 2^-33 and the
+    FP32 rounding of the level >= 4 accumulator about as much; a wrong slice,
+    scale or lane mapping gives errors of order one."""
+    import torch
+    import paper_1708_02835_gb300 as egs
+    rng = np.random.default_rng(7 * M + N + K)
+    a, b = _rows_scaled(rng, (M, K), 20), _rows_scaled(rng, (N, K), 20)
+    C = torch.full((M, N), float("nan"), dtype=torch.float64, device="cuda")
+    egs.egs_ozaki_gemm_test(torch.as_tensor(a).cuda(), torch.as_tensor(b).cuda(), C)
+    got = C.cpu().numpy()
+    ref = a @ b.T
+    bound = K * 2.0 ** -31 * np.outer(np.abs(a).max(axis=1), np.abs(b).max(axis=1))
+    err = np.abs(got - ref)
+    print("ozaki max err / bound %.3e" % float(np.max(err / bound)))
+    assert np.all(np.isfinite(got))
+    assert np.all(err <= bound)
+    # two orders of magnitude more accurate than an FP32 product (35 against
+    # 24 significant bits per entry)
+    fp32 = (a.astype(np.float32) @ b.astype(np.float32).T).astype(np.float64)
+    assert np.max(err / bound) < 1e-2 * np.max(np.abs(fp32 - ref) / bound)
+
+
+def test_ozaki_gemm_exact_on_small_integers():
+    """Entries that are integers in [-127, 127] fit the first slice exactly
+    and the level-2 sums (<= 512 * 127^2 < 2^24) are exact in FP32: the
+    product must equal the integer product bit for bit."""
+    import torch
+    import paper_1708_02835_gb300 as egs
+    rng = np.random.default_rng(3)
+    a = rng.integers(-127, 128, (256, 512)).astype(np.float64)
+    b = rng.integers(-127, 128, (64, 512)).astype(np.float64)
+    C = torch.empty((256, 64), dtype=torch.float64, device="cuda")
+    egs.egs_ozaki_gemm_test(torch.as_tensor(a).cuda(), torch.as_tensor(b).cuda(), C)
+    assert np.array_equal(C.cpu().numpy(), a @ b.T)
