@@ -90,7 +90,8 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
     off += 2 * align256(panel_buffer_bytes(g.b, g.T, mix_fmt(p)));
     L.oz = off;
     if (mix_fmt(p) == 3)
-        off += align256(ozaki_slices_bytes(g.b, g.T)) + align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(double));
+        off += 2 * (align256(ozaki_slices_bytes(g.b, g.T)) +
+                    align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(double)));
     L.locs = off;
     off += align256((size_t)2 * g.n * sizeof(double));
     L.z = off;
@@ -175,8 +176,12 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
         mb.cols = v + 6 * stride;
         mb.partials = (double *)(ws + ML.partials);
         mb.err = (int *)(ws + ML.err);
-        mb.oz = ws + ML.oz;
-        mb.ozs = (double *)(ws + ML.oz + align256(ozaki_slices_bytes(g.b, g.T)));
+        const size_t ozb = align256(ozaki_slices_bytes(g.b, g.T));
+        const size_t ozh = ozb + align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(double));
+        for (int i = 0; i < 2; ++i) {
+            mb.oz[i] = ws + ML.oz + i * ozh;
+            mb.ozs[i] = (double *)(ws + ML.oz + i * ozh + ozb);
+        }
         cudaMemsetAsync(mb.err, 0, sizeof(int), s);
         return run_loglik_mixed(dlocs, dlocs + n, dz, n, es.P, mix_fmt(es.p), es.refine, mb, st, s, kt, ev);
     }

@@ -146,8 +146,8 @@ struct MixedBuffers {
     double *zp, *y, *x, *d, *res, *rows, *cols;  // T*b vectors
     double *partials; // 2T
     int *err;
-    void *oz;         // FP32 mode: BF16 slices of the panel rows (ozaki_slices_bytes)
-    double *ozs;      // FP32 mode: their row scales, (T-1) b doubles
+    void *oz[2];      // FP32 mode: BF16 slices of the panel rows (ozaki_slices_bytes), step k uses k % 2
+    double *ozs[2];   // FP32 mode: their row scales, (T-1) b doubles each
 };
 
 // One mixed-precision evaluation (fmt 3 = split TF32, 2 = TF32, 1 = BF16); the
@@ -189,11 +189,9 @@ cudaError_t launch_update_f64(const Tiles &tl, int k, int64_t ntri, DevStatus *s
                               int cls = KC_UPDATE);
 // FP32 mixed mode: FP64-accurate updates of the band tiles whose panel
 // operands are not both FP64 band tiles, by exact BF16 slicing on tcgen05
-// (ozaki.cu).  The slices of every panel row of step k are written first.
+// (ozaki.cu).  The TRSM stage writes the slices of every panel row.
 size_t ozaki_slices_bytes(int b, int T);
 cudaError_t make_ozaki_maps(const void *oz, int b, int T, CUtensorMap *mapA, CUtensorMap *mapB);
-cudaError_t launch_ozaki_slices(const Tiles &tl, int k, void *oz, double *scale, const DevStatus *st, cudaStream_t s,
-                                KernelTimer *kt);
 // Band tiles of columns col0 .. col0 + ncols - 1 at step k.
 cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &mapB, const Tiles &tl, int k, int col0,
                                   int ncols, const double *scale, int *err, cudaStream_t s, KernelTimer *kt);

@@ -22,6 +22,7 @@
 // iterative refinement: x0 = L^-T L^-1 Z, r = Z - Sigma x0 with Sigma the FP64
 // copy written by the generator, x1 = x0 + L^-T L^-1 r, quad = Z^T x1.
 #include "egs_internal.cuh"
+#include "slices.cuh"
 
 #include <cuda_bf16.h>
 
@@ -67,6 +68,20 @@ __device__ __forceinline__ void panel_store(void *panel, const Tiles &tl, size_t
     }
 }
 
+// FP32 mode: FP64 band panel rows (m = k+1..k+nrows) -> split-TF32 operands
+// and the BF16 slices of the FP64-accurate band updates; one warp per row.
+__global__ void __launch_bounds__(256) k_panel_from_f64_split(Tiles tl, int k, void *panel, __nv_bfloat16 *oz,
+                                                              double *ozs, const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    const int b = tl.b, lane = threadIdx.x & 31;
+    const size_t pr = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // panel row
+    const int m = k + 1 + (int)(pr / b);
+    const double *x = tl.t64(m, k) + (pr % b) * b;
+    for (int c = lane; c < b; c += 32) panel_store<3>(panel, tl, pr, c, (float)x[c]);
+    slice_row(x, b, oz + pr * b, (size_t)(tl.T - 1) * b * b, ozs + pr);
+}
+
 // FP64 band panel tiles (m = k+1..k+nrows) -> operand format.
 template <int FMT>
 __global__ void __launch_bounds__(256) k_panel_from_f64(Tiles tl, int k, int nrows, void *panel, const DevStatus *st)
@@ -89,7 +104,8 @@ __global__ void __launch_bounds__(256) k_panel_from_f64(Tiles tl, int k, int nro
 // keeps 4 rows x 2 columns per thread with the operands transposed in shared
 // memory (one 16-byte and one 8-byte shared load per 8 FMAs).
 template <int FMT>
-__global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0, void *panel, const DevStatus *st)
+__global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0, void *panel, __nv_bfloat16 *oz,
+                                                        double *ozs, const DevStatus *st)
 {
     if (mfailed(st)) return;
     const int b = tl.b;
@@ -160,6 +176,13 @@ __global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0,
             panel_store<FMT>(panel, tl, prow0 + r, c0 + c, v);
         }
         __syncthreads();
+    }
+    if (FMT == 3) {
+        // slices of the 64 solved rows for the FP64-accurate band updates
+        // (re-read from L1/L2; one warp per row)
+        const size_t R = (size_t)(tl.T - 1) * b;
+        for (int rr = tid >> 5; rr < 64; rr += 8)
+            slice_row_f32(A + (size_t)rr * b, b, oz + (prow0 + rr) * b, R * b, ozs + prow0 + rr);
     }
 }
 
@@ -353,15 +376,16 @@ cudaError_t backward_solve(const Tiles &tl, double *v, const DevStatus *st, cuda
 }
 
 // The factorisation with one step of lookahead.  The FP64 chain of step k
-// (POTRF and the band TRSM) runs on a side stream; the main stream then runs
-// the FP32 TRSM of the off-band panel on the whole GPU, the FP64 band x band
-// update and the tensor-core update of column k + 1, signals the side stream
-// (whose chain for step k + 1 needs only that column), and updates the rest
-// of the trailing matrix (leaving a few SMs free) while the next chain runs.
-// Panels alternate between two buffers.
+// (POTRF, the band TRSM, the band rows' operands, then the FP64 band x band
+// update) runs on a side stream; the main stream runs the FP32 TRSM of the
+// off-band panel on the whole GPU and the tensor-core update of column k + 1,
+// signals the side stream (whose chain for step k + 1 needs only that column
+// and its own band x band update), and updates the rest of the trailing
+// matrix (leaving a few SMs free) while the next chain runs.  Panels (and in
+// FP32 mode the slices) alternate between two buffers.
 template <int FMT>
 cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CUtensorMap *mbm,
-                         const CUtensorMap &mc, const CUtensorMap *moz, DevStatus *st, cudaStream_t s,
+                         const CUtensorMap &mc, const CUtensorMap (*moz)[2], DevStatus *st, cudaStream_t s,
                          KernelTimer *kt)
 {
     const Tiles &tl = mb.tl;
@@ -377,38 +401,50 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         const int nb = (tl.band - 1 < T - k - 1) ? tl.band - 1 : T - k - 1;  // FP64 rows below k
         const int nf = T - k - 1 - nb;                                       // FP32 rows
         void *panel = mb.panel[k & 1];
-        // ---- chain of step k on the side stream: POTRF and the FP64 band TRSM
+        __nv_bfloat16 *oz = (__nv_bfloat16 *)mb.oz[k & 1];
+        double *ozs = mb.ozs[k & 1];
+        // ---- chain of step k on the side stream: POTRF, the FP64 band TRSM
+        // and the band rows' operands; then (after signalling the main
+        // stream) the FP64 band x band update
         e = cudaStreamWaitEvent(side, ev_col, 0);
         if (e == cudaSuccess) e = launch_potrf_diag(tl, k, st, side, kts);
         if (e == cudaSuccess && k + 1 < T) {
             e = launch_trsm_f64(tl, k, nb, st, side, kts);
             if (e == cudaSuccess && nb > 0) {
-                const size_t total = (size_t)nb * tl.bb();
-                const unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-                EGS_LAUNCH(kts, KC_TRSM, side, k_panel_from_f64<FMT><<<blocks, 256, 0, side>>>(tl, k, nb, panel, st));
+                if (FMT == 3) {
+                    EGS_LAUNCH(kts, KC_TRSM, side,
+                               k_panel_from_f64_split<<<(unsigned)((size_t)nb * b / 8), 256, 0, side>>>(tl, k, panel, oz,
+                                                                                                      ozs, st));
+                } else {
+                    const size_t total = (size_t)nb * tl.bb();
+                    const unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+                    EGS_LAUNCH(kts, KC_TRSM, side,
+                               k_panel_from_f64<FMT><<<blocks, 256, 0, side>>>(tl, k, nb, panel, st));
+                }
             }
             if (e == cudaSuccess) e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
+        // updates whose two operands are FP64 band tiles stay in FP64 (they
+        // carry the nearest-neighbour entries that set the diagonal pivots);
+        // their outputs are read by nothing else at this step
+        if (e == cudaSuccess && k + 1 < T)
+            e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, side, kts, KC_UPDATE64);
         if (k + 1 == T || e != cudaSuccess) break;
-        // ---- step k on the main stream: the FP32 TRSM (whole GPU), the FP64
-        // band x band update, column k + 1, signal, then the rest
+        // ---- step k on the main stream: the FP32 TRSM (whole GPU), column
+        // k + 1, signal, then the rest
         e = cudaStreamWaitEvent(s, ev_panel, 0);
         if (e == cudaSuccess && nf > 0)
             EGS_LAUNCH(kt, KC_TRSM, s,
-                       k_trsm_panel_f32<FMT><<<dim3((unsigned)nf, (unsigned)(b / 64)), 256, 0, s>>>(tl, k, k + 1 + nb,
-                                                                                                panel, st));
-        // updates whose two operands are FP64 band tiles stay in FP64 (they
-        // carry the nearest-neighbour entries that set the diagonal pivots)
-        // FP32 mode: slice every panel row for the FP64-accurate band outputs
-        if (e == cudaSuccess && FMT == 3) e = launch_ozaki_slices(tl, k, mb.oz, mb.ozs, st, s, kt);
-        if (e == cudaSuccess) e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, s, kt, KC_UPDATE64);
+                       k_trsm_panel_f32<FMT><<<dim3((unsigned)nf, (unsigned)(b / 64)), 256, 0, s>>>(
+                           tl, k, k + 1 + nb, panel, oz, ozs, st));
+        // FP32 mode: band outputs with an FP32 operand by exact slices
         if (e == cudaSuccess && FMT == 3)
-            e = launch_band_out_ozaki(moz[0], moz[1], tl, k, k + 1, 1, mb.ozs, mb.err, s, kt);
+            e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, k, k + 1, 1, ozs, mb.err, s, kt);
         if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, FMT, tl, k, mb.err, s, kt, 1);
         if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);
         if (e == cudaSuccess && FMT == 3)
-            e = launch_band_out_ozaki(moz[0], moz[1], tl, k, k + 2, T - k - 2, mb.ozs, mb.err, s, kt);
+            e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, k, k + 2, T - k - 2, ozs, mb.err, s, kt);
         if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, FMT, tl, k, mb.err, s, kt, 2);
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
@@ -436,11 +472,11 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     cudaError_t e = launch_matern_tiles(X, Y, n, tl, P, mb.sig, s, kt);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
-    CUtensorMap ma[2], mbm[2], mc, moz[2];
+    CUtensorMap ma[2], mbm[2], mc, moz[2][2];
     e = make_panel_maps(mb.panel[0], fmt, b, T, &ma[0], &mbm[0]);
     if (e == cudaSuccess) e = make_panel_maps(mb.panel[1], fmt, b, T, &ma[1], &mbm[1]);
     if (e == cudaSuccess) e = make_offband_map(tl.f32, b, Tiles::f32_tiles(T, tl.band), &mc);
-    if (e == cudaSuccess && fmt == 3) e = make_ozaki_maps(mb.oz, b, T, &moz[0], &moz[1]);
+    for (int i = 0; i < 2 && e == cudaSuccess && fmt == 3; ++i) e = make_ozaki_maps(mb.oz[i], b, T, &moz[i][0], &moz[i][1]);
     if (e != cudaSuccess) return e;
     if (fmt == 3) e = factor_mixed<3>(mb, ma, mbm, mc, moz, st, s, kt);
     else if (fmt == 2) e = factor_mixed<2>(mb, ma, mbm, mc, moz, st, s, kt);

@@ -5,10 +5,10 @@
 // by the FP32 mixed mode for every update whose output is an FP64 band tile.
 //
 // Each operand row x (length K) is scaled by a power of two sigma = 2^e with
-// |x| < sigma, u = x 128 / sigma, and cut into five slices
+// |x| < sigma, u = x 128 / sigma, and cut into five slices (slices.cuh)
 //   q_1 = rint(u),  q_i = rint((u - q_1 - ... - q_{i-1}) 2^{7(i-1)}) 2^{-7(i-1)},
 // each an integer of at most 8 bits times a power of two, so exact in BF16;
-// x = (sigma / 128) (q_1 + ... + q_5) up to 2^-35 |sigma|.  For a pair of rows
+// x = (sigma / 128) (q_1 + ... + q_5) up to 2^-36 sigma.  For a pair of rows
 //   x . y = s_x s_y sum_{i,j} q_i(x) . q_j(y)        (s = sigma / 128)
 // and the slice products are accumulated in FP32 on tcgen05 by level:
 //   acc0 = q_1 . q_1                  integers, |acc0| <= K 2^14 <= 2^23 (K <= 512)
@@ -30,6 +30,7 @@
 // 32-column TMEM accumulators, double-buffered across work items; warps 2-5
 // read the accumulators with tcgen05.ld and apply the FP64 epilogue.
 #include "egs_internal.cuh"
+#include "slices.cuh"
 #include "tc_common.cuh"
 
 #include <cuda_bf16.h>
@@ -39,7 +40,7 @@ namespace egs {
 
 namespace {
 
-constexpr int OS = 5;  // slices per operand
+constexpr int OS = kSlices;  // slices per operand
 constexpr int OBM = 128, OBN = 32, OSTAGES = 2, OKC = 64;
 constexpr int OA_SL = OBM * 128, OB_SL = OBN * 128;  // bytes of one slice box
 constexpr int OSTAGE = OS * (OA_SL + OB_SL);
@@ -51,57 +52,6 @@ constexpr int NPAIRS = 15;
 __device__ __forceinline__ bool ofailed(const DevStatus *st)
 {
     return st && *(volatile const unsigned long long *)&st->fail_index != kNoFail;
-}
-
-// One warp slices one row of K <= 1024 values (lane owns columns lane + 32 j).
-// Slice i of the row goes to dst[i * slice_stride + c]; the row scale
-// sigma / 128 to *scale.
-template <typename E>
-__device__ __forceinline__ void slice_row(const E *__restrict__ src, int K, __nv_bfloat16 *__restrict__ dst,
-                                          size_t slice_stride, double *scale)
-{
-    const int lane = threadIdx.x & 31;
-    double x[32];
-    double mx = 0.0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const int c = lane + 32 * j;
-        x[j] = (c < K) ? (double)src[c] : 0.0;
-        mx = fmax(mx, fabs(x[j]));
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    int e = 0;
-    frexp(mx, &e);  // mx = f 2^e with f in [0.5, 1), so |x| < 2^e (mx = 0: e = 0)
-    if (lane == 0) *scale = ldexp(1.0, e - 7);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const int c = lane + 32 * j;
-        if (c < K) {
-            double u = ldexp(x[j], 7 - e);  // |u| < 128, exact
-#pragma unroll
-            for (int i = 0; i < OS; ++i) {
-                const double q = ldexp(rint(ldexp(u, 7 * i)), -7 * i);  // exact in BF16
-                dst[(size_t)i * slice_stride + c] = __float2bfloat16_rn((float)q);
-                u -= q;  // exact
-            }
-        }
-    }
-}
-
-// Panel rows of step k (all (T - k - 1) b of them, FP64 band tiles and FP32
-// off-band tiles) -> slices; 8 rows per CTA of 256 threads.
-__global__ void __launch_bounds__(256) k_ozaki_slices_panel(Tiles tl, int k, __nv_bfloat16 *oz, double *scale,
-                                                            size_t R, const DevStatus *st)
-{
-    if (ofailed(st)) return;
-    const int b = tl.b;
-    const size_t pr = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int t = (int)(pr / b), r = (int)(pr % b);
-    const int m = k + 1 + t;
-    __nv_bfloat16 *dst = oz + pr * b;
-    if (tl.is64(m, k)) slice_row(tl.t64(m, k) + (size_t)r * b, b, dst, R * b, scale + pr);
-    else slice_row(tl.t32(m, k) + (size_t)r * b, b, dst, R * b, scale + pr);
 }
 
 // Rows of a dense row-major FP64 matrix (rows x K) -> slices.
@@ -387,17 +337,6 @@ cudaError_t make_ozaki_maps(const void *oz, int b, int T, CUtensorMap *mapA, CUt
     cudaError_t e = make_slice_map(mapA, oz, R, (uint64_t)b, OBM);
     if (e == cudaSuccess) e = make_slice_map(mapB, oz, R, (uint64_t)b, OBN);
     return e;
-}
-
-cudaError_t launch_ozaki_slices(const Tiles &tl, int k, void *oz, double *scale, const DevStatus *st, cudaStream_t s,
-                                KernelTimer *kt)
-{
-    const size_t rows = (size_t)(tl.T - k - 1) * tl.b;
-    if (rows == 0) return cudaSuccess;
-    const size_t R = (size_t)(tl.T - 1) * tl.b;
-    EGS_LAUNCH(kt, KC_TRSM, s,
-               k_ozaki_slices_panel<<<(unsigned)(rows / 8), 256, 0, s>>>(tl, k, (__nv_bfloat16 *)oz, scale, R, st));
-    return cudaGetLastError();
 }
 
 cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &mapB, const Tiles &tl, int k, int col0,
