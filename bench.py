@@ -4,9 +4,12 @@
 One step = one full evaluation of Eq. 1 by Algorithm 2 (Matern generation,
 tile Cholesky, forward solve, log-determinant, quadratic form; in mixed
 precision also the FP64 refinement) on the n = 102,400 workload: a jittered
-320 x 320 grid over [0, 1]^2, theta = (1, 0.1, 0.5), tile 512, FP64 band of
-2 tiles.  Inputs are resident in HBM when the timed region starts; the tile
-matrix (up to 42 GB) is regenerated every step, far larger than L2.
+320 x 320 grid over [0, 1]^2, theta = (1, 0.1, 0.5), tile 512.  Default: the
+FP32 mixed mode (split-TF32 off-band updates, FP64-accurate band updates) with
+an FP64 band of 3 tiles, the narrowest band that keeps |dl|/|l| <= 1e-6 at
+this size (band 2: 5.2e-6); --band 2 --precision fp32|tf32|bf16 gives the
+other variants.  Inputs are resident in HBM when the timed region starts; the
+tile matrix (up to 42 GB) is regenerated every step, far larger than L2.
 
 Usage:
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32|bf16|fp32]
@@ -40,15 +43,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="egs", choices=["egs", "reference"])
-    ap.add_argument("--precision", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--n", type=int, default=102400, help="development override; the workload is n=102400")
     ap.add_argument("--tile", type=int, default=512)
-    ap.add_argument("--band", type=int, default=2)
+    ap.add_argument("--band", type=int, default=3)
     ap.add_argument("--theta", default="1.0,0.1,0.5")
     ap.add_argument("--e2e-steps", type=int, default=-1, help="steps of the end-to-end leg (default: = steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="config3",
-                    choices=["config3", "config2-mle", "config4-batched", "config5-serve"],
+                    choices=["config3", "config2-mle", "config3-mle", "config4-batched", "config5-serve"],
                     help="config3 (default): one n=102,400 evaluation per step; the others are the "
                          "MLE, batched and serving workloads")
     ap.add_argument("--evals", type=int, default=50, help="config2-mle: likelihood evaluations")
@@ -60,7 +63,8 @@ def parse():
 def workload_name(a) -> str:
     m = int(round(math.sqrt(a.n)))
     grid = "%dx%d jittered grid" % (m, m) if m * m == a.n else "jittered grid"
-    return "n=%d (%s over [0,1]^2), theta=(%s), tile %d, band %d" % (a.n, grid, a.theta, a.tile, a.band)
+    return "n=%d (%s over [0,1]^2), theta=(%s), tile %d, %s, FP64 band %d" % (
+        a.n, grid, a.theta, a.tile, a.precision, a.band)
 
 
 def flop_counts(n: int, b: int) -> dict:
@@ -216,13 +220,16 @@ def _to_dev(a):
 
 def run_mle(a, egs):
     """Config 2: n = 25,600 (160 x 160), theta = (1, 0.2, 1.3), Z simulated on the
-    GPU by Algorithm 1; one MLE run of --evals derivative-free evaluations."""
+    GPU by Algorithm 1; one MLE run of --evals derivative-free evaluations in
+    FP64 and one in --precision, theta-hat compared.  config3-mle: the same
+    on the config-3 field (theta = (1, 0.1, 0.5)) at n = 25,600, where an FP64
+    fit is affordable (at n = 102,400 one FP64 evaluation takes ~290 s)."""
     import torch
     import egs_inputs as ei
     from paper_1708_02835_gb300 import mle
     p = ei.CONFIG2
     n = p.n if a.n == 102400 else a.n
-    theta = p.theta
+    theta = p.theta if a.workload == "config2-mle" else ei.CONFIG3.theta
     locs = ei.jittered_grid(n, seed=p.seed)
     dl, de = _to_dev(locs.reshape(-1)), _to_dev(ei.normal(p.seed, n))
     dz = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -232,15 +239,17 @@ def run_mle(a, egs):
     for prec in (["fp64", a.precision] if a.precision != "fp64" else ["fp64"]):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = mle.fit(dl, dz, n, prec, start=start, max_evals=a.evals, tile=0 if prec == "fp64" else 512)
+        r = mle.fit(dl, dz, n, prec, start=start, max_evals=a.evals, tile=0 if prec == "fp64" else 512,
+                    band=0 if prec == "fp64" else a.band)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         out[prec] = {"theta_hat": list(r.theta), "loglik": r.loglik, "evals": r.evals, "seconds": dt,
-                     "evals_per_s": r.evals / dt}
-    line = {"metric": "MLE log-likelihood evaluations/s (config 2)", "value": out["fp64"]["evals_per_s"],
+                     "evals_per_s": r.evals / dt, "fp64_fallbacks": r.fallbacks}
+    line = {"metric": "MLE log-likelihood evaluations/s (%s)" % a.workload, "value": out["fp64"]["evals_per_s"],
             "unit": "evals/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "n=%d (160x160 jittered grid), theta=(1,0.2,1.3), Z by Algorithm 1 on the GPU, "
-                                   "bounded Nelder-Mead from %s over [0.01,5]^3" % (n, start), "n": n},
+            "config": {"workload": "n=%d (160x160 jittered grid), theta=%s, Z by Algorithm 1 on the GPU, "
+                                   "bounded Nelder-Mead from %s over [0.01,5]^3" % (n, tuple(theta), start), "n": n,
+                       "band": a.band},
             "runs": out, "theta_true": list(theta)}
     if len(out) > 1:
         f, m = out["fp64"]["theta_hat"], out[a.precision]["theta_hat"]
@@ -368,7 +377,8 @@ def main():
         import paper_1708_02835_gb300 as egs
         torch.cuda.set_device(local)
         egs.load_library()
-        {"config2-mle": run_mle, "config4-batched": run_batched, "config5-serve": run_serve}[a.workload](a, egs)
+        {"config2-mle": run_mle, "config3-mle": run_mle, "config4-batched": run_batched,
+         "config5-serve": run_serve}[a.workload](a, egs)
         return
 
     import numpy as np
@@ -410,11 +420,14 @@ def main():
     e0.record(stream)
     infos = []
     for _ in range(a.steps):
-        ll, info = step(2)
+        ll, info = step(1)  # phase events only; per-launch timing runs once below
         infos.append(info)
     e1.record(stream)
     barrier()
     clocks = sampler.stop()
+    # one more (untimed) step with every launch bracketed by events, for the
+    # per-kernel-class breakdown and the roofline's kernel time
+    _, info2 = step(2)
     ms = e0.elapsed_time(e1)
     t = torch.tensor([ms], device="cuda")
     if world > 1:
@@ -445,14 +458,11 @@ def main():
         fc = flop_counts(n, tile)
         ms_step = ms_max / a.steps
         ms_factor = statistics.mean(i["ms_factor"] for i in infos)
-        upd_ms = statistics.mean(i["ms_update"] for i in infos)
+        upd_ms = info2["ms_update"]
         launches_update = fc["T"] - 1
-        classes = {"update": statistics.mean(i["ms_update"] for i in infos),
-                   "update_f64": statistics.mean(i["ms_update_f64"] for i in infos),
-                   "potrf": statistics.mean(i["ms_potrf"] for i in infos),
-                   "trsm": statistics.mean(i["ms_trsm"] for i in infos),
-                   "trsv": statistics.mean(i["ms_trsv"] for i in infos),
-                   "generate": statistics.mean(i["ms_generate"] for i in infos)}
+        classes = {k: info2["ms_" + k] for k in ("update", "update_f64", "potrf", "trsm", "trsv", "generate")}
+        classes["note"] = ("one extra untimed step with CUDA events around every launch; classes on the side "
+                           "stream include time spent waiting for SMs")
         if a.precision == "fp64":
             achieved = fc["update"] / (upd_ms / 1e3) / 1e12
             roof = {"bound": "alu", "kernel": "k_update_f64 (SYRK/GEMM trailing update)", "achieved": achieved,
@@ -481,12 +491,17 @@ def main():
                     "ms_per_launch": upd_ms / (2 * launches_update),
                     "note": "executed TF32/BF16 MMA flops (%d product(s) per update) over the tcgen05 launches' "
                             "event time (two launches per step: column k+1, then the rest)" % products}
-            upd64 = statistics.mean(i["ms_update_f64"] for i in infos)
+            upd64 = info2["ms_update_f64"]
             if upd64 > 0:
                 a64 = f64_flops / (upd64 / 1e3) / 1e12
-                roof["fp64_updates"] = {"kernel": "k_update_f64 / k_update_band_out", "achieved": a64,
-                                        "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": a64 / FP64_PEAK_TFLOPS,
-                                        "flops_per_step": f64_flops, "ms_per_step": upd64}
+                kern = "k_update_f64 (band x band, DFMA)"
+                if a.precision == "fp32":
+                    kern += " + k_tc_ozaki (other band outputs, 15 exact BF16 slice products on tcgen05)"
+                roof["fp64_accurate_updates"] = {
+                    "kernel": kern, "achieved_fp64_equivalent": a64, "fp64_peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "vs_fp64_peak": a64 / FP64_PEAK_TFLOPS, "flops_per_step": f64_flops,
+                    "ms_per_step": upd64,
+                    "note": "event time summed over the launches on both streams (they overlap other work)"}
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f64+" + a.precision,

@@ -12,7 +12,7 @@
  *
  *     C(r; theta) = theta1 / (2^(theta3 - 1) Gamma(theta3)) (r/theta2)^theta3 K_theta3(r/theta2)
  *
- * following Algorithm 2 (Section 5.4): generate Sigma, factor Sigma = L L^T by
+ * following Algorithm 2 (Section 6.5): generate Sigma, factor Sigma = L L^T by
  * tile Cholesky, solve L y = Z, reduce log|Sigma| = 2 sum_i log L_ii and
  * y^T y, and assemble l.  Every step runs in the library's own sm_103a CUDA
  * kernels.
@@ -61,7 +61,14 @@ typedef enum {
     EGS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     EGS_ERR_TIMEOUT = 5,       /* a bounded wait expired */
     EGS_ERR_BUSY = 6,          /* resource busy (serving: queue full) */
-    EGS_ERR_UNIMPLEMENTED = 7  /* feature not built */
+    EGS_ERR_UNIMPLEMENTED = 7, /* feature not built */
+    EGS_ERR_INACCURATE = 8     /* mixed precision only: the FP64 refinement step
+                                  changed the quadratic form by more than 1e-3
+                                  relative, i.e. the mixed factor is too inexact
+                                  for Sigma(theta) (condition number near
+                                  1/eps of the off-band precision); the value
+                                  is still in egs_info.loglik -- evaluate this
+                                  theta in EGS_FP64 */
 } egs_status;
 
 typedef enum {
@@ -110,6 +117,11 @@ typedef struct {
     int32_t timing;        /* nonzero: record per-phase CUDA events into egs_info */
     void *workspace;       /* caller-owned device workspace, or NULL (library allocates) */
     size_t workspace_bytes;
+    int32_t distance;      /* 0: Euclidean on (x, y); 1: great-circle distance on
+                              (longitude, latitude) in degrees by the haversine
+                              formula (Section 7.4) on a sphere of 6371 km, so
+                              theta2 is in km */
+    int32_t reserved;      /* 0 */
 } egs_opts;
 
 /* Message describing the last error on the calling thread ("" if none). */
@@ -142,7 +154,7 @@ egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3]
 
 /*
  * egs_potrf_tiles - tile Cholesky Sigma = L L^T in place (Algorithm 2,
- * dpotrf; the right-looking tile algorithm of Section 4.2: POTRF on the
+ * dpotrf; the right-looking tile algorithm of Section 5.2: POTRF on the
  * diagonal tile, TRSM on the panel, SYRK/GEMM on the trailing tiles).
  *   tiles       device, lower tiles of Sigma in EGS_FP64 layout; on return L
  *   fail_index  host; first failing row or -1.  The call synchronises stream.
@@ -150,9 +162,9 @@ egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3]
 egs_status egs_potrf_tiles(void *tiles, int64_t n, int32_t tile, int64_t *fail_index, void *stream);
 
 /*
- * egs_trsv_tiles - forward solve L y = Z (Algorithm 2, dtrsm; Section 5.4
+ * egs_trsv_tiles - forward solve L y = Z (Algorithm 2, dtrsm; Section 6.5
  * states it as L Z_new = Z_old) with the log-determinant (2 sum_i log L_ii,
- * Section 5.1) and the dot product y^T y (Algorithm 2, computeDotProduct).
+ * Section 6.1) and the dot product y^T y (Algorithm 2, computeDotProduct).
  *   tiles  device, L in EGS_FP64 lower-tile layout
  *   z      device, n doubles;  y  device, n doubles (may alias z)
  *   logdet, quad  host; the call synchronises stream.
@@ -182,7 +194,7 @@ egs_status egs_trsv_tiles_noalloc(const void *tiles, int64_t n, int32_t tile, co
                                   double *logdet, double *quad, void *stream);
 
 /*
- * egs_simulate - synthetic measurements, Algorithm 1 (Section 5.3): generate
+ * egs_simulate - synthetic measurements, Algorithm 1 (Section 6.4): generate
  * Sigma(theta) at the locations, factor Sigma = L L^T in FP64 (dpotrf) and
  * form Z = L e (dtrmm) for a caller-supplied e (normally e ~ N(0, I)).
  *   locs  2n doubles (x then y), device or host;  e  n doubles, device or host
@@ -204,7 +216,9 @@ egs_status egs_simulate(const double *locs, const double *e, const double theta[
 egs_status egs_loglik(const double *locs, const double *z, const double theta[3], int64_t n,
                       egs_precision p, double *out_loglik, egs_info *info, void *stream);
 
-/* egs_loglik with options (tile, band, refinement, caller workspace). */
+/* egs_loglik with options (tile, band, refinement, caller workspace).
+ * Mixed precision with refine >= 1 returns EGS_ERR_INACCURATE (out_loglik
+ * untouched, info filled) when the refinement step does not contract. */
 egs_status egs_loglik_ex(const double *locs, const double *z, const double theta[3], int64_t n,
                          egs_precision p, const egs_opts *opts, double *out_loglik, egs_info *info,
                          void *stream);
@@ -213,7 +227,7 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
  * Batched evaluation (independent problems: uneven n, own theta each).
  *
  * Each problem is Eq. 1 evaluated by Algorithm 2 exactly as egs_loglik does
- * in EGS_FP64; the batch runs the tile algorithm of Section 4.2 for all
+ * in EGS_FP64; the batch runs the tile algorithm of Section 5.2 for all
  * problems at once: every kernel launch covers one step of every problem, so
  * the whole batch is a few hundred launches, captured into a CUDA graph on the
  * first egs_batch_run and replayed afterwards.
@@ -241,6 +255,39 @@ size_t egs_batch_workspace_bytes(const egs_batch *batch);
 egs_status egs_loglik_batched(int32_t nprob, const int64_t *n, const double *const *locs, const double *const *z,
                               const double *theta, egs_precision p, double *out, egs_status *per_status,
                               void *stream);
+
+/*
+ * egs_predict - kriging prediction, Eq. 5 by Algorithm 3 (Section 6.6): with
+ * zero means, Z_1 = Sigma_12 Sigma_22^-1 Z_2 for m new locations given n
+ * observed ones and their measurements Z_2.  Sigma_22 is factored as in one
+ * egs_loglik_ex evaluation with the same precision and options (FP64: tile
+ * Cholesky, forward and backward solves; mixed: the refined x = Sigma_22^-1
+ * Z_2 of the evaluation); Sigma_12 is formed on the fly and never stored.
+ *   locs_obs  2n doubles (x then y), z_obs n doubles;  locs_new 2m doubles
+ *   z_new     m doubles, written;  all device or host memory
+ *   info      (nullable) the evaluation's loglik / logdet / quad at theta
+ * EGS_ERR_NOT_PD / EGS_ERR_INACCURATE as egs_loglik_ex.  Synchronises stream.
+ */
+egs_status egs_predict(const double *locs_obs, const double *z_obs, int64_t n, const double *locs_new, int64_t m,
+                       const double theta[3], egs_precision p, const egs_opts *opts, double *z_new, egs_info *info,
+                       void *stream);
+
+/*
+ * egs_loglik_ind - the independent-blocks (IND) approximation of Section 6.8:
+ * every tile outside the diagonal super tiles (super_tiles x super_tiles
+ * tiles of tile x tile) is set to zero, so Sigma is block diagonal over
+ * consecutive runs of super_tiles * tile locations (the last run holds the
+ * rest), and l_IND = sum over the blocks of Eq. 1 on each block's locations
+ * and measurements.  FP64; the blocks run as one batch of the batched
+ * scheduler (one CUDA graph).  Sums over the blocks are in block order.
+ *   locs  2n doubles (x then y), device or host;  z  n doubles, device or host
+ *   tile  0 = 128;  super_tiles >= 1 (super_tiles * tile >= n gives exact l)
+ *   info  loglik, logdet, quad summed over the blocks; band = super_tiles
+ * EGS_ERR_NOT_PD (fail_index = global row) if a block is not positive
+ * definite.  Synchronises stream; allocates its workspace per call.
+ */
+egs_status egs_loglik_ind(const double *locs, const double *z, const double theta[3], int64_t n, int32_t tile,
+                          int32_t super_tiles, double *out_loglik, egs_info *info, void *stream);
 
 /*
  * Serving loop: likelihood requests from concurrent optimisers.

@@ -108,6 +108,45 @@ def matern(theta, r) -> np.ndarray:
     return np.array([lib.ora_matern(_p(th), float(v)) for v in rs]).reshape(np.shape(r))
 
 
+EARTH_RADIUS_KM = 6371.0
+
+
+def gcd_dist(locs1, locs2, radius: float = EARTH_RADIUS_KM) -> np.ndarray:
+    """Great-circle distances (Section 7.4) between (longitude, latitude)
+    pairs in degrees, by the haversine formula
+    hav(d / r) = hav(phi2 - phi1) + cos(phi1) cos(phi2) hav(lambda2 - lambda1),
+    hav(t) = (1 - cos t) / 2, d = 2 r asin(sqrt(hav(d / r)))."""
+    a, b = _f64(locs1), _f64(locs2)
+    lam1, phi1 = np.radians(a[0])[:, None], np.radians(a[1])[:, None]
+    lam2, phi2 = np.radians(b[0])[None, :], np.radians(b[1])[None, :]
+    h = (1.0 - np.cos(phi2 - phi1)) / 2.0 + np.cos(phi1) * np.cos(phi2) * (1.0 - np.cos(lam2 - lam1)) / 2.0
+    return 2.0 * radius * np.arcsin(np.sqrt(np.clip(h, 0.0, 1.0)))
+
+
+def cov_matrix_gcd(locs, theta) -> np.ndarray:
+    """Sigma(theta) with great-circle distances in km (locations in degrees)."""
+    d = gcd_dist(locs, locs)
+    np.fill_diagonal(d, 0.0)
+    return matern(theta, d.reshape(-1)).reshape(d.shape)
+
+
+def loglik_gcd(locs, z, theta) -> dict:
+    """Eq. 1 by Algorithm 2 (LAPACK steps) on the great-circle Sigma."""
+    import scipy.linalg as sla
+
+    S = cov_matrix_gcd(locs, theta)
+    n = S.shape[0]
+    try:
+        L = sla.cholesky(S, lower=True, overwrite_a=True, check_finite=False)
+    except np.linalg.LinAlgError as exc:
+        raise NotPositiveDefinite(-1) from exc
+    y = sla.solve_triangular(L, _f64(z), lower=True, check_finite=False)
+    logdet = 2.0 * float(np.sum(np.log(np.diag(L))))
+    quad = float(y @ y)
+    return {"loglik": -0.5 * quad - 0.5 * logdet - 0.5 * n * math.log(2.0 * math.pi),
+            "logdet": logdet, "quad": quad}
+
+
 def cov_matrix(locs, theta) -> np.ndarray:
     """Dense Sigma(theta) (Section 2): Sigma_ij = C(||s_i - s_j||; theta)."""
     lib = _load()
@@ -197,6 +236,27 @@ def loglik_lapack(locs, z, theta, return_factor: bool = False) -> dict:
         out["L"] = L
         out["y"] = y
     return out
+
+
+def loglik_ind(locs, z, theta, block: int) -> dict:
+    """The IND approximation (Section 6.8) by its definition: Sigma with every
+    entry between different diagonal blocks of `block` consecutive locations
+    set to zero, then Eq. 1 by Algorithm 2 (LAPACK steps) on that matrix."""
+    import scipy.linalg as sla
+
+    S = cov_matrix(locs, theta)
+    n = S.shape[0]
+    blk = np.arange(n) // int(block)
+    S[blk[:, None] != blk[None, :]] = 0.0
+    try:
+        L = sla.cholesky(S, lower=True, overwrite_a=True, check_finite=False)
+    except np.linalg.LinAlgError as exc:
+        raise NotPositiveDefinite(-1) from exc
+    y = sla.solve_triangular(L, _f64(z), lower=True, check_finite=False)
+    logdet = 2.0 * float(np.sum(np.log(np.diag(L))))
+    quad = float(y @ y)
+    return {"loglik": -0.5 * quad - 0.5 * logdet - 0.5 * n * math.log(2.0 * math.pi),
+            "logdet": logdet, "quad": quad}
 
 
 def simulate_z(locs, theta, e) -> np.ndarray:

@@ -19,12 +19,12 @@
  *   ora_cholesky    Sigma = L L^T, textbook column-by-column (left-looking)
  *                   Cholesky (Algorithm 2, dpotrf); a pivot <= 0 reports the
  *                   failing column.
- *   ora_forward_solve  L y = Z (Algorithm 2, dtrsm; the text of Section 5.4
+ *   ora_forward_solve  L y = Z (Algorithm 2, dtrsm; the text of Section 6.5
  *                   states the solve as L Z_new = Z_old).
  *   ora_loglik      Eq. 1 through Algorithm 2:
  *                   l = -n/2 log(2 pi) - sum_i log L_ii - 1/2 y^T y,
  *                   log|Sigma| = 2 sum_i log L_ii (the "product of the diagonal
- *                   entries" of the factor in Section 5.1, taken in log form).
+ *                   entries" of the factor in Section 6.1, taken in log form).
  *   ora_brute_*     Brute-force checks in long double: determinant by LU with
  *                   partial pivoting, Z^T Sigma^-1 Z by a Gauss-Jordan inverse.
  */

@@ -14,12 +14,12 @@ import numpy as np
 from . import build as _build
 
 EGS_OK, EGS_ERR_ARG, EGS_ERR_NOT_PD, EGS_ERR_OOM, EGS_ERR_CUDA, EGS_ERR_TIMEOUT, EGS_ERR_BUSY, \
-    EGS_ERR_UNIMPLEMENTED = range(8)
+    EGS_ERR_UNIMPLEMENTED, EGS_ERR_INACCURATE = range(9)
 EGS_FP64, EGS_MIX_FP32, EGS_MIX_TF32, EGS_MIX_BF16 = range(4)
 PRECISIONS = {"fp64": EGS_FP64, "fp32": EGS_MIX_FP32, "tf32": EGS_MIX_TF32, "bf16": EGS_MIX_BF16}
 
 _STATUS_NAMES = {0: "EGS_OK", 1: "EGS_ERR_ARG", 2: "EGS_ERR_NOT_PD", 3: "EGS_ERR_OOM", 4: "EGS_ERR_CUDA",
-                 5: "EGS_ERR_TIMEOUT", 6: "EGS_ERR_BUSY", 7: "EGS_ERR_UNIMPLEMENTED"}
+                 5: "EGS_ERR_TIMEOUT", 6: "EGS_ERR_BUSY", 7: "EGS_ERR_UNIMPLEMENTED", 8: "EGS_ERR_INACCURATE"}
 
 
 class EgsError(RuntimeError):
@@ -30,6 +30,10 @@ class EgsError(RuntimeError):
 
 class NotPositiveDefinite(EgsError):
     pass
+
+
+class MixedInaccurate(EgsError):
+    """The mixed-precision factor was too inexact for Sigma(theta)."""
 
 
 class egs_info(ctypes.Structure):
@@ -47,7 +51,8 @@ class egs_info(ctypes.Structure):
 
 class egs_opts(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("band", ctypes.c_int32), ("refine", ctypes.c_int32),
-                ("timing", ctypes.c_int32), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+                ("timing", ctypes.c_int32), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("distance", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class egs_serve_config(ctypes.Structure):
@@ -108,6 +113,9 @@ def load_library(build_if_missing: bool = True):
         "egs_batch_workspace_bytes": (c.c_size_t, [vp]),
         "egs_loglik_batched": (c.c_int, [i32, c.POINTER(i64), c.POINTER(vp), c.POINTER(vp), pd, c.c_int, pd,
                                          c.POINTER(c.c_int), vp]),
+        "egs_loglik_ind": (c.c_int, [vp, vp, pd, i64, i32, i32, pd, c.POINTER(egs_info), vp]),
+        "egs_predict": (c.c_int, [vp, vp, i64, vp, i64, pd, c.c_int, c.POINTER(egs_opts), vp, c.POINTER(egs_info),
+                                  vp]),
         "egs_serve_create": (c.c_int, [c.POINTER(egs_serve_config), c.POINTER(vp)]),
         "egs_serve_add_field": (c.c_int, [vp, vp, vp, i64, c.POINTER(i64)]),
         "egs_serve_submit": (c.c_int, [vp, i64, pd, c.c_int, c.POINTER(i64)]),
@@ -128,6 +136,8 @@ def _check(status: int):
         msg = load_library().egs_last_error().decode()
         if status == EGS_ERR_NOT_PD:
             raise NotPositiveDefinite(status, msg)
+        if status == EGS_ERR_INACCURATE:
+            raise MixedInaccurate(status, msg)
         raise EgsError(status, msg)
 
 
@@ -215,13 +225,18 @@ def egs_trsv_tiles_noalloc(tiles, n: int, tile: int, z, y, stream=None) -> tuple
     return ld.value, q.value
 
 
+DISTANCES = {"euclidean": 0, "great_circle": 1}
+
+
 def egs_loglik_ex(locs, z, theta, n: int, precision="fp64", tile: int = 0, band: int = 0, refine: int = 0,
-                  timing: int = 0, workspace=None, stream=None) -> tuple:
-    """One evaluation of Eq. 1; returns (loglik, info dict)."""
+                  timing: int = 0, workspace=None, stream=None, distance="euclidean") -> tuple:
+    """One evaluation of Eq. 1; returns (loglik, info dict).  distance
+    "great_circle": locations are (longitude, latitude) in degrees."""
     tp, _keep = _theta(theta)
     opts = egs_opts(tile=tile, band=band, refine=refine, timing=int(timing),
                     workspace=_ptr(workspace) if workspace is not None else None,
-                    workspace_bytes=(workspace.numel() * workspace.element_size()) if workspace is not None else 0)
+                    workspace_bytes=(workspace.numel() * workspace.element_size()) if workspace is not None else 0,
+                    distance=DISTANCES[distance])
     out = ctypes.c_double()
     info = egs_info()
     st = load_library().egs_loglik_ex(_ptr(locs), _ptr(z), tp, n, _prec(precision), ctypes.byref(opts),
@@ -258,6 +273,27 @@ def egs_ozaki_gemm_test(A, B, C, stream=None):
     M, K = A.shape
     N = B.shape[0]
     _check(load_library().egs_ozaki_gemm_test(_ptr(A), _ptr(B), M, N, K, _ptr(C), _stream(stream)))
+
+
+def egs_predict(locs_obs, z_obs, n: int, locs_new, m: int, theta, z_new, precision="fp64", tile: int = 0,
+                band: int = 0, refine: int = 0, stream=None, distance="euclidean") -> dict:
+    """Kriging prediction Z_1 = Sigma_12 Sigma_22^-1 Z_2 (Eq. 5, Algorithm 3) into z_new; returns the info dict."""
+    tp, _keep = _theta(theta)
+    opts = egs_opts(tile=tile, band=band, refine=refine, distance=DISTANCES[distance])
+    info = egs_info()
+    _check(load_library().egs_predict(_ptr(locs_obs), _ptr(z_obs), n, _ptr(locs_new), m, tp, _prec(precision),
+                                      ctypes.byref(opts), _ptr(z_new), ctypes.byref(info), _stream(stream)))
+    return info.as_dict()
+
+
+def egs_loglik_ind(locs, z, theta, n: int, tile: int = 0, super_tiles: int = 1, stream=None):
+    """IND approximation (Section 6.8): l summed over diagonal super tiles; returns (l, info)."""
+    tp, _keep = _theta(theta)
+    out = ctypes.c_double()
+    info = egs_info()
+    _check(load_library().egs_loglik_ind(_ptr(locs), _ptr(z), tp, n, tile, super_tiles, ctypes.byref(out),
+                                         ctypes.byref(info), _stream(stream)))
+    return out.value, info.as_dict()
 
 
 class egs_batch:

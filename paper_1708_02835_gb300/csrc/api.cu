@@ -31,7 +31,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static bool tile_ok(int32_t b) { return b >= 64 && b <= 1024 && (b % 64) == 0; }
 
-static bool is_device_ptr(const void *p)
+bool is_device_ptr(const void *p)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -145,10 +145,30 @@ egs_status eval_setup(int64_t n, const double *theta, egs_precision p, const egs
     es->locs_off = es->mixed ? es->ML.locs : es->L.locs;
     es->z_off = es->mixed ? es->ML.z : es->L.z;
     egs_matern_params_init(theta, &es->P);
+    const int dist = opts ? opts->distance : 0;
+    if (dist != EGS_DIST_EUCLIDEAN && dist != EGS_DIST_GREAT_CIRCLE)
+        return set_error(EGS_ERR_ARG, "distance = %d must be 0 (Euclidean) or 1 (great circle)", dist);
+    es->P.metric = dist;
+    es->P.radius = EGS_EARTH_RADIUS_KM;
     return EGS_OK;
 }
 
 DevStatus *eval_status(const EvalSetup &es, char *ws) { return (DevStatus *)(ws + (es.mixed ? es.ML.status : es.L.status)); }
+
+double *eval_solution(const EvalSetup &es, char *ws)
+{
+    if (!es.mixed) return (double *)(ws + es.L.zpad);
+    const size_t npad = (size_t)es.g.T * es.g.b;
+    const size_t stride = align256(npad * sizeof(double)) / sizeof(double);
+    return (double *)(ws + es.ML.vec) + 2 * stride;  // mb.x
+}
+
+cudaError_t finish_solution(const EvalSetup &es, char *ws, cudaStream_t s)
+{
+    if (es.mixed) return cudaSuccess;
+    const Tiles tl{(double *)(ws + es.L.tiles), nullptr, es.g.b, es.g.T, es.g.T};
+    return backward_solve(tl, eval_solution(es, ws), eval_status(es, ws), s, nullptr);
+}
 
 cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double *dz, char *ws, cudaStream_t s,
                          KernelTimer *kt, cudaEvent_t *ev)
@@ -201,6 +221,13 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
     if (e == cudaSuccess) e = launch_trsv_tiles_f64(tiles, g, zpad, partials, st, s, kt);
     if (e == cudaSuccess && ev) cudaEventRecord(ev[3], s);
     return e;
+}
+
+bool mixed_result_ok(const EvalSetup &es, const DevStatus &h)
+{
+    if (!es.mixed || es.refine < 1) return true;
+    const double q = h.result[2], q0 = h.result[3];
+    return std::fabs(q - q0) <= kRefineTol * std::fabs(q);
 }
 
 void fill_info(const EvalSetup &es, const DevStatus &h, egs_info *info)
@@ -397,6 +424,11 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
     const int64_t fi = (h.fail_index == kNoFail) ? -1 : (int64_t)h.fail_index;
     if (fi >= 0) return set_error(EGS_ERR_NOT_PD, "not positive definite at row %lld (tile %lld)", (long long)fi,
                                   (long long)(fi / es.g.b));
+    if (!mixed_result_ok(es, h))
+        return set_error(EGS_ERR_INACCURATE,
+                         "the refinement step changed the quadratic form by %.3g relative (limit %g): the mixed "
+                         "factor is too inexact for this Sigma; evaluate in EGS_FP64",
+                         std::fabs(h.result[2] - h.result[3]) / std::fabs(h.result[2]), kRefineTol);
     if (out_loglik) *out_loglik = h.result[0];
     return EGS_OK;
 }

@@ -1,12 +1,13 @@
 // Batched evaluation of many independent likelihood problems (uneven n, own
 // theta each) in FP64: the same tile algorithm as the single-problem path
-// (Algorithm 2 with the tile Cholesky of Section 4.2), but every kernel
+// (Algorithm 2 with the tile Cholesky of Section 5.2), but every kernel
 // launch covers one step of *all* problems at once.  A launch's work items
 // are the concatenation of every problem's items for that step; the CTA finds
 // its problem by binary search in a per-launch prefix table, so a batch of
 // 512 problems with tiles of 128 needs a few hundred launches in total, and
 // the whole sequence is captured once into a CUDA graph and replayed.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -77,8 +78,7 @@ __global__ void __launch_bounds__(256) kb_gen(BatchArgs a)
         if (gi >= n || gj >= n) v = (gi == gj) ? 1.0 : 0.0;
         else if (gi == gj) v = Ps.th1;
         else {
-            const double dx = pr.X[gi] - xj, dy = pr.Y[gi] - yj;
-            v = matern_eval(&Ps, sqrt(fma(dx, dx, dy * dy)) * Ps.inv_th2);
+            v = matern_eval(&Ps, loc_dist(&Ps, pr.X[gi], pr.Y[gi], xj, yj) * Ps.inv_th2);
         }
         tile[(size_t)r * b + sc * 64 + tx] = v;
     }
@@ -414,23 +414,14 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
     return EGS_OK;
 }
 
-egs_status egs_batch_run(egs_batch *B, const double *const *locs, const double *const *z, const double *theta,
-                         double *out, egs_status *per_status, void *stream)
+}  // extern "C"
+
+namespace {
+
+// After the inputs have been staged on B->cs: the parameters, the graph
+// (captured on first use) and the statuses back to the host; synchronises.
+cudaError_t run_staged(egs_batch *B, cudaStream_t us, cudaError_t e)
 {
-    if (!B || !locs || !z || !theta) return set_error(EGS_ERR_ARG, "egs_batch_run: NULL argument");
-    cudaStream_t us = (cudaStream_t)stream;
-    for (int i = 0; i < B->nprob; ++i)
-        if (egs_matern_params_init(theta + 3 * i, &B->h_params[i]) != 0)
-            return set_error(EGS_ERR_ARG, "egs_batch_run: theta of problem %d must be finite and > 0", i);
-    cudaError_t e = cudaEventRecord(B->ev_in, us);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->cs, B->ev_in, 0);
-    // inputs: copied into the plan's staging area (device or host sources)
-    for (int i = 0; i < B->nprob && e == cudaSuccess; ++i) {
-        double *in = B->d_inputs + B->in_off[i];
-        e = cudaMemcpyAsync(in, locs[i], (size_t)2 * B->n[i] * sizeof(double), cudaMemcpyDefault, B->cs);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(in + 2 * B->n[i], z[i], (size_t)B->n[i] * sizeof(double), cudaMemcpyDefault, B->cs);
-    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->d_params, B->h_params, sizeof(egs_matern_params) * B->nprob, cudaMemcpyHostToDevice, B->cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->d_status, 0xFF, sizeof(DevStatus) * B->nprob, B->cs);
@@ -451,6 +442,31 @@ egs_status egs_batch_run(egs_batch *B, const double *const *locs, const double *
     if (e == cudaSuccess) e = cudaEventRecord(B->ev_out, B->cs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(us, B->ev_out, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(B->cs);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+egs_status egs_batch_run(egs_batch *B, const double *const *locs, const double *const *z, const double *theta,
+                         double *out, egs_status *per_status, void *stream)
+{
+    if (!B || !locs || !z || !theta) return set_error(EGS_ERR_ARG, "egs_batch_run: NULL argument");
+    cudaStream_t us = (cudaStream_t)stream;
+    for (int i = 0; i < B->nprob; ++i)
+        if (egs_matern_params_init(theta + 3 * i, &B->h_params[i]) != 0)
+            return set_error(EGS_ERR_ARG, "egs_batch_run: theta of problem %d must be finite and > 0", i);
+    cudaError_t e = cudaEventRecord(B->ev_in, us);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->cs, B->ev_in, 0);
+    // inputs: copied into the plan's staging area (device or host sources)
+    for (int i = 0; i < B->nprob && e == cudaSuccess; ++i) {
+        double *in = B->d_inputs + B->in_off[i];
+        e = cudaMemcpyAsync(in, locs[i], (size_t)2 * B->n[i] * sizeof(double), cudaMemcpyDefault, B->cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(in + 2 * B->n[i], z[i], (size_t)B->n[i] * sizeof(double), cudaMemcpyDefault, B->cs);
+    }
+    e = run_staged(B, us, e);
     if (e != cudaSuccess) return cuda_error(e, "egs_batch_run");
     egs_status worst = EGS_OK;
     for (int i = 0; i < B->nprob; ++i) {
@@ -494,6 +510,76 @@ egs_status egs_loglik_batched(int32_t nprob, const int64_t *n, const double *con
     st = egs_batch_run(B, locs, z, theta, out, per_status, stream);
     egs_batch_destroy(B);
     return st;
+}
+
+
+// Independent-blocks (IND) approximation (Section 6.8): every tile outside
+// the diagonal super tiles of super_tiles x super_tiles tiles is set to
+// zero, so Sigma is block diagonal over consecutive runs of
+// super_tiles * tile locations and l_IND is the sum of Eq. 1 over the
+// blocks.  The blocks are independent problems of the batched scheduler.
+egs_status egs_loglik_ind(const double *locs, const double *z, const double theta[3], int64_t n, int32_t tile,
+                          int32_t super_tiles, double *out_loglik, egs_info *info, void *stream)
+{
+    if (!locs || !z || !theta) return set_error(EGS_ERR_ARG, "egs_loglik_ind: NULL pointer");
+    if (n < 1) return set_error(EGS_ERR_ARG, "egs_loglik_ind: n = %lld must be >= 1", (long long)n);
+    if (super_tiles < 1) return set_error(EGS_ERR_ARG, "egs_loglik_ind: super_tiles = %d must be >= 1", super_tiles);
+    if (tile == 0) tile = 128;
+    if (tile < 64 || tile > 1024 || tile % 64) return set_error(EGS_ERR_ARG, "egs_loglik_ind: tile %d invalid", tile);
+    egs_matern_params P;
+    if (egs_matern_params_init(theta, &P) != 0) return set_error(EGS_ERR_ARG, "egs_loglik_ind: theta must be finite and > 0");
+    const int64_t bs = (int64_t)super_tiles * tile;
+    const int64_t nblk = (n + bs - 1) / bs;
+    if (nblk > (1 << 20)) return set_error(EGS_ERR_ARG, "egs_loglik_ind: too many blocks");
+    std::vector<int64_t> ns((size_t)nblk);
+    for (int64_t i = 0; i < nblk; ++i) ns[(size_t)i] = std::min(bs, n - i * bs);
+    egs_batch *B = nullptr;
+    egs_status sc = egs_batch_create((int32_t)nblk, ns.data(), tile, EGS_FP64, &B);
+    if (sc != EGS_OK) return sc;
+    for (int i = 0; i < B->nprob; ++i) B->h_params[i] = P;
+    cudaStream_t us = (cudaStream_t)stream;
+    cudaError_t e = cudaEventRecord(B->ev_in, us);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->cs, B->ev_in, 0);
+    // block i: x[i bs ..], y[i bs ..] (y starts at locs + n), z[i bs ..]
+    for (int i = 0; i < B->nprob && e == cudaSuccess; ++i) {
+        double *in = B->d_inputs + B->in_off[i];
+        const size_t bytes = (size_t)B->n[i] * sizeof(double);
+        const int64_t off = (int64_t)i * bs;
+        e = cudaMemcpyAsync(in, locs + off, bytes, cudaMemcpyDefault, B->cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(in + B->n[i], locs + n + off, bytes, cudaMemcpyDefault, B->cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(in + 2 * B->n[i], z + off, bytes, cudaMemcpyDefault, B->cs);
+    }
+    e = run_staged(B, us, e);
+    if (e != cudaSuccess) {
+        egs_batch_destroy(B);
+        return cuda_error(e, "egs_loglik_ind");
+    }
+    // fixed-order FP64 sums over the blocks
+    double ll = 0.0, ld = 0.0, q = 0.0;
+    int64_t fail = -1;
+    for (int i = 0; i < B->nprob; ++i) {
+        const DevStatus &h = B->h_status[i];
+        if (h.fail_index != kNoFail && fail < 0) fail = (int64_t)i * bs + (int64_t)h.fail_index;
+        ll += h.result[0];
+        ld += h.result[1];
+        q += h.result[2];
+    }
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->loglik = fail < 0 ? ll : NAN;
+        info->logdet = ld;
+        info->quad = q;
+        info->quad_unrefined = q;
+        info->fail_index = fail;
+        info->fail_tile = fail >= 0 ? fail / tile : -1;
+        info->tile = tile;
+        info->band = super_tiles;
+        info->launches = B->launches_per_run;
+    }
+    egs_batch_destroy(B);
+    if (fail >= 0) return set_error(EGS_ERR_NOT_PD, "egs_loglik_ind: not positive definite at row %lld", (long long)fail);
+    if (out_loglik) *out_loglik = ll;
+    return EGS_OK;
 }
 
 }  // extern "C"

@@ -1,5 +1,5 @@
 // FP64 tile Cholesky (Algorithm 2, dpotrf) by the right-looking tile algorithm
-// of Section 4.2: for k = 0..T-1
+// of Section 5.2: for k = 0..T-1
 //   POTRF  L_kk = chol(A_kk)
 //   TRSM   A_mk <- A_mk L_kk^-T            (m > k)
 //   SYRK   A_mm <- A_mm - A_mk A_mk^T       (m > k)

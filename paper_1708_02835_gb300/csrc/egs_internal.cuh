@@ -115,6 +115,9 @@ struct KernelTimer {
         if (kt) (kt)->end((cls), (s));   \
     } while (0)
 
+// True for device (or managed) memory; host pointers are staged by the calls.
+bool is_device_ptr(const void *p);
+
 // Error reporting (api.cu): thread-local message, returns code.
 egs_status set_error(egs_status code, const char *fmt, ...);
 egs_status cuda_error(cudaError_t e, const char *what);
@@ -178,7 +181,15 @@ egs_status eval_setup(int64_t n, const double *theta, egs_precision p, const egs
 cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double *dz, char *ws, cudaStream_t s,
                          KernelTimer *kt, cudaEvent_t *ev);
 DevStatus *eval_status(const EvalSetup &es, char *ws);
+// After eval_enqueue: mixed -> x = Sigma^-1 Z (refined); FP64 -> y = L^-1 Z
+// (finish_solution turns it into Sigma^-1 Z with the backward solve).
+double *eval_solution(const EvalSetup &es, char *ws);
+cudaError_t finish_solution(const EvalSetup &es, char *ws, cudaStream_t s);
 void fill_info(const EvalSetup &es, const DevStatus &h, egs_info *info);
+// Mixed precision with refinement: did the FP64 refinement step contract?
+// (|quad - quad_unrefined| <= kRefineTol |quad|; always true otherwise.)
+constexpr double kRefineTol = 1e-3;
+bool mixed_result_ok(const EvalSetup &es, const DevStatus &h);
 int32_t default_tile(int64_t n, egs_precision p);
 
 // Building blocks shared by the FP64 and mixed drivers.
@@ -197,6 +208,8 @@ cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &ma
                                   int ncols, const double *scale, int *err, cudaStream_t s, KernelTimer *kt);
 cudaError_t launch_forward_solve(const Tiles &tl, double *zpad, double *partials, DevStatus *st, cudaStream_t s,
                                  KernelTimer *kt);
+// L^T x = v in place (any Tiles storage).
+cudaError_t backward_solve(const Tiles &tl, double *v, const DevStatus *st, cudaStream_t s, KernelTimer *kt);
 cudaError_t launch_finalize(const double *partials, int T, int64_t n, DevStatus *st, cudaStream_t s, KernelTimer *kt);
 
 // Z = L e over FP64 lower tiles (diagonal tiles with a zero upper triangle).

@@ -68,9 +68,7 @@ k_matern_tiles(const double *__restrict__ X, const double *__restrict__ Y, int64
         } else if (gi == gj) {
             v = P->th1;
         } else {
-            const double dx = X[gi] - xj, dy = Y[gi] - yj;
-            const double rdist = sqrt(fma(dx, dx, dy * dy));
-            v = matern_eval(P, rdist * inv_th2);
+            v = matern_eval(P, loc_dist(P, X[gi], Y[gi], xj, yj) * inv_th2);
         }
         const size_t off = (size_t)r * b + sc * 64 + tx;
         if (is64) t64[off] = v;

@@ -127,6 +127,24 @@ __device__ __forceinline__ double matern_general(const egs_matern_params *__rest
     return front * knu;
 }
 
+// Distance between locations i and j.  Euclidean: sqrt(dx^2 + dy^2).  Great
+// circle (Section 7.4): the haversine formula on (longitude, latitude) in
+// degrees, hav(d / R) = hav(phi_j - phi_i) + cos(phi_i) cos(phi_j)
+// hav(lambda_j - lambda_i), hav(t) = sin^2(t / 2), d = 2 R asin(sqrt(hav)).
+__device__ __forceinline__ double loc_dist(const egs_matern_params *__restrict__ Pp, double xi, double yi, double xj,
+                                           double yj)
+{
+    if (Pp->metric == EGS_DIST_EUCLIDEAN) {
+        const double dx = xi - xj, dy = yi - yj;
+        return sqrt(fma(dx, dx, dy * dy));
+    }
+    const double rad = 0.017453292519943295769;  // pi / 180
+    const double p1 = yi * rad, p2 = yj * rad;
+    const double s1 = sin(0.5 * (p2 - p1)), s2 = sin(0.5 * (xj - xi) * rad);
+    const double h = fma(cos(p1) * cos(p2), s2 * s2, s1 * s1);
+    return 2.0 * Pp->radius * asin(sqrt(fmin(h, 1.0)));
+}
+
 // C(x * theta2) for x = r / theta2 >= 0.
 __device__ __forceinline__ double matern_eval(const egs_matern_params *__restrict__ Pp, double x)
 {

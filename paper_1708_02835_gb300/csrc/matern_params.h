@@ -9,6 +9,11 @@
 #define EGS_TEMME_MAX 24 /* terms of Temme's series (x <= 1.25) */
 #define EGS_CF_MAX 140   /* depth of the backward recurrence (x > 1.25) */
 
+/* distance between two locations */
+#define EGS_DIST_EUCLIDEAN 0    /* (x, y) in the plane */
+#define EGS_DIST_GREAT_CIRCLE 1 /* (longitude, latitude) in degrees, haversine */
+#define EGS_EARTH_RADIUS_KM 6371.0
+
 /* kind of covariance evaluation */
 #define EGS_MATERN_GENERAL 0 /* any theta3: Temme / backward recurrence */
 #define EGS_MATERN_HALF 1    /* theta3 = 1/2: theta1 exp(-x) */
@@ -27,7 +32,8 @@ typedef struct {
     int kind;
     int N;         /* nu = mu + N */
     int half_mu;   /* |mu| = 1/2: C_k = 0 for k >= 1, the recurrence is not needed */
-    int pad1;
+    int metric;    /* EGS_DIST_EUCLIDEAN or EGS_DIST_GREAT_CIRCLE */
+    double radius; /* sphere radius of the great-circle distance */
     double t_k2[EGS_TEMME_MAX + 1]; /* 1 / (k^2 - mu^2) */
     double t_km[EGS_TEMME_MAX + 1]; /* 1 / (k - mu) */
     double t_kp[EGS_TEMME_MAX + 1]; /* 1 / (k + mu) */

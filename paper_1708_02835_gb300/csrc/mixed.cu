@@ -1,7 +1,7 @@
 // Mixed-precision evaluation of Eq. 1 (Algorithm 2) with an FP64 diagonal band.
 //
 // Storage: tiles with i - j < band (the diagonal band) stay FP64; the others
-// are FP32.  Per step k of the right-looking tile Cholesky (Section 4.2):
+// are FP32.  Per step k of the right-looking tile Cholesky (Section 5.2):
 //   POTRF  L_kk in FP64;
 //   TRSM   band rows (m - k < band) in FP64, the other rows in FP32 with
 //          L_kk rounded to FP32; every solved tile is also written to the
@@ -366,6 +366,10 @@ __global__ void __launch_bounds__(1024) k_finalize_mixed(const double *__restric
     }
 }
 
+}  // namespace
+
+// L^T x = v in place on v (T b doubles): block column substitution from the
+// last tile, FP64 arithmetic (FP32 off-band tiles are read as FP32).
 cudaError_t backward_solve(const Tiles &tl, double *v, const DevStatus *st, cudaStream_t s, KernelTimer *kt)
 {
     for (int k = tl.T - 1; k >= 0; --k) {
@@ -374,6 +378,8 @@ cudaError_t backward_solve(const Tiles &tl, double *v, const DevStatus *st, cuda
     }
     return cudaGetLastError();
 }
+
+namespace {
 
 // The factorisation with one step of lookahead.  The FP64 chain of step k
 // (POTRF, the band TRSM, the band rows' operands, then the FP64 band x band

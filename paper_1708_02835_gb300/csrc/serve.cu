@@ -99,6 +99,9 @@ void finish_slot(egs_server *S, Slot &sl)
     } else if (h.fail_index != egs::kNoFail) {
         r.status = EGS_ERR_NOT_PD;
         r.loglik = NAN;
+    } else if (!egs::mixed_result_ok(sl.es, h)) {
+        r.status = EGS_ERR_INACCURATE;
+        r.loglik = NAN;
     } else {
         r.status = EGS_OK;
         r.loglik = h.result[0];

@@ -1,6 +1,6 @@
 // Forward solve L y = Z on the lower-tile layout (Algorithm 2, dtrsm; the
-// text of Section 5.4 writes it as L Z_new = Z_old), fused with the
-// log-determinant log|Sigma| = 2 sum_i log L_ii (Section 5.1, taken in log
+// text of Section 6.5 writes it as L Z_new = Z_old), fused with the
+// log-determinant log|Sigma| = 2 sum_i log L_ii (Section 6.1, taken in log
 // form) and the dot product y^T y (Algorithm 2, computeDotProduct), then the
 // assembly l = -1/2 y^T y - 1/2 log|Sigma| - n/2 log(2 pi) (Eq. 1).
 //

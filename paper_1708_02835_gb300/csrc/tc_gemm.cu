@@ -1,5 +1,5 @@
 // Tensor-core (tcgen05) trailing update of the mixed-precision tile Cholesky,
-// the dominant contraction of Algorithm 2's dpotrf (Section 4.2, GEMM/SYRK
+// the dominant contraction of Algorithm 2's dpotrf (Section 5.2, GEMM/SYRK
 // tasks):  C_mn -= P_m P_n^T  for every tile T > m >= n > k at step k, where
 // P_m is the factored panel tile (m, k) stored in the MMA operand format
 // (TF32-rounded FP32, split-TF32 hi/lo copies, or BF16) by the TRSM stage.

@@ -1,4 +1,4 @@
-"""Maximum-likelihood driver (Section 5.3): maximise l(theta) of Eq. 1 over
+"""Maximum-likelihood driver (Section 6.3): maximise l(theta) of Eq. 1 over
 bounded theta with a derivative-free optimiser; every evaluation is one call
 of the library's GPU log-likelihood.
 
@@ -6,7 +6,10 @@ The paper drives BOBYQA through NLopt.  NLopt is not part of this stack, so
 the driver uses its own bounded Nelder-Mead simplex (Nelder & Mead, Computer
 Journal 7, 1965) on u = log(theta), with the bounds enforced by projection
 onto the box.  An evaluation whose covariance is not positive definite counts
-as l = -inf.  Every evaluation is appended to an optional JSONL trace; a run
+as l = -inf.  With a mixed precision, a theta whose mixed factorisation fails
+(EGS_ERR_NOT_PD) or is flagged too inexact by its refinement step
+(EGS_ERR_INACCURATE) is re-evaluated in FP64 (fallback_fp64, on by default),
+so that the optimiser never follows a mixed-precision artefact.  Every evaluation is appended to an optional JSONL trace; a run
 given an existing trace replays its recorded values instead of re-evaluating,
 so an interrupted fit resumes where it stopped.
 """
@@ -26,6 +29,7 @@ class FitResult:
     loglik: float
     evals: int
     history: list = field(default_factory=list)  # (theta, loglik) per evaluation
+    fallbacks: int = 0  # mixed-precision evaluations redone in FP64
 
 
 class _Objective:
@@ -125,18 +129,31 @@ def nelder_mead_bounded(f, x0, lower, upper, max_evals=50, step=0.5, trace_path=
 
 def fit(locs, z, n: int, precision="fp64", start=(0.5, 0.05, 0.5), lower=(0.01, 0.01, 0.01),
         upper=(5.0, 5.0, 5.0), max_evals: int = 50, tile: int = 0, band: int = 0, trace_path=None,
-        stream=None) -> FitResult:
+        stream=None, fallback_fp64: bool = True) -> FitResult:
     """Maximum-likelihood estimate of theta with every l(theta) evaluated on the GPU.
 
     locs (2n doubles, x then y) and z (n doubles) should be device tensors so
     they stay resident across evaluations."""
     from . import binding as egs
 
+    fallbacks = []
+
+    def fp64(theta):
+        try:
+            return egs.egs_loglik_ex(locs, z, theta, n, "fp64", stream=stream)[0]
+        except egs.NotPositiveDefinite:
+            return -math.inf
+
     def loglik(theta):
         try:
             ll, _ = egs.egs_loglik_ex(locs, z, theta, n, precision, tile=tile, band=band, stream=stream)
             return ll
-        except egs.NotPositiveDefinite:
-            return -math.inf
+        except (egs.NotPositiveDefinite, egs.MixedInaccurate):
+            if precision == "fp64" or not fallback_fp64:
+                return -math.inf
+            fallbacks.append(tuple(theta))
+            return fp64(theta)
 
-    return nelder_mead_bounded(loglik, start, lower, upper, max_evals=max_evals, trace_path=trace_path)
+    r = nelder_mead_bounded(loglik, start, lower, upper, max_evals=max_evals, trace_path=trace_path)
+    r.fallbacks = len(fallbacks)
+    return r

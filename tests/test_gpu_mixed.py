@@ -114,3 +114,23 @@ def test_mixed_tile_must_be_multiple_of_256(egs):
     locs = ei.jittered_grid(1000)
     with pytest.raises(egs.EgsError):
         egs.egs_loglik_ex(locs_dev(locs), dev(np.ones(1000)), (1, 0.1, 0.5), 1000, "tf32", tile=320)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+@pytest.mark.parametrize("theta", [(1.0, 0.15, 1.3), (1.0, 0.3, 1.0), (1.0, 0.5, 0.5), (2.0, 0.05, 2.0)])
+def test_mixed_never_returns_a_gross_error(egs, prec, theta):
+    """Smooth or long-range fields push Sigma's condition number towards
+    1/eps of the off-band precision.  The mixed path must then either fail
+    cleanly (EGS_ERR_NOT_PD, or EGS_ERR_INACCURATE when the FP64 refinement
+    step does not contract) or return a value close to the oracle's."""
+    from gpu_util import locs_dev, dev
+    n = 3000
+    locs, z, ref = _case(n, theta, 4)
+    try:
+        ll, info = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, prec, tile=256)
+    except (egs.NotPositiveDefinite, egs.MixedInaccurate) as e:
+        print("%s theta=%s: %s" % (prec, theta, type(e).__name__))
+        return
+    rel = abs(ll - ref["loglik"]) / abs(ref["loglik"])
+    print("%s theta=%s: rel l %.2e" % (prec, theta, rel))
+    assert rel <= 1e-3, rel

@@ -1,6 +1,6 @@
 """The MLE driver's bounded Nelder-Mead (host logic, CPU) and one GPU fit.
 
-Section 5.3: theta-hat maximises Eq. 1 under bounds; the paper uses BOBYQA,
+Section 6.3: theta-hat maximises Eq. 1 under bounds; the paper uses BOBYQA,
 this driver a bounded simplex in log(theta) (same role: derivative-free,
 bound-constrained).
 """
