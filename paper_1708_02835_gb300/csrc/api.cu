@@ -92,6 +92,8 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
     if (mix_fmt(p) == 3)
         off += 2 * (align256(ozaki_slices_bytes(g.b, g.T)) +
                     align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(double)));
+    L.l32 = off;
+    off += align256(bb * sizeof(float));
     L.locs = off;
     off += align256((size_t)2 * g.n * sizeof(double));
     L.z = off;
@@ -196,6 +198,7 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
         mb.cols = v + 6 * stride;
         mb.partials = (double *)(ws + ML.partials);
         mb.err = (int *)(ws + ML.err);
+        mb.l32 = (float *)(ws + ML.l32);
         const size_t ozb = align256(ozaki_slices_bytes(g.b, g.T));
         const size_t ozh = ozb + align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(double));
         for (int i = 0; i < 2; ++i) {

@@ -149,6 +149,7 @@ struct MixedBuffers {
     double *zp, *y, *x, *d, *res, *rows, *cols;  // T*b vectors
     double *partials; // 2T
     int *err;
+    float *l32;       // b x b: L_kk rounded to FP32 for the off-band TRSM of step k
     void *oz[2];      // FP32 mode: BF16 slices of the panel rows (ozaki_slices_bytes), step k uses k % 2
     double *ozs[2];   // FP32 mode: their row scales, (T-1) b doubles each
 };
@@ -164,7 +165,7 @@ struct Layout {
     size_t tiles, locs, z, zpad, partials, status, total;
 };
 struct MixedLayout {
-    size_t f64, f32, sig, panel, oz, locs, z, vec, partials, status, err, total;
+    size_t f64, f32, sig, panel, oz, l32, locs, z, vec, partials, status, err, total;
 };
 struct EvalSetup {
     TileGeom g;

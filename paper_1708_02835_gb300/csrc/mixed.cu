@@ -98,20 +98,29 @@ __global__ void __launch_bounds__(256) k_panel_from_f64(Tiles tl, int k, int nro
     }
 }
 
+// L_kk rounded to FP32 once per step (the FP32 TRSM reads it many times; a
+// conversion from FP64 runs on the FP64 pipe, 2 per clock per SM on GB300).
+__global__ void __launch_bounds__(256) k_l32_from_f64(Tiles tl, int k, float *__restrict__ l32, const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    const double *L = tl.t64(k, k);
+    const size_t bb = tl.bb();
+    for (size_t e = (size_t)blockIdx.x * 256 + threadIdx.x; e < bb; e += (size_t)gridDim.x * 256) l32[e] = (float)L[e];
+}
+
 // TRSM of the FP32 panel rows m = m0 + blockIdx.x: X L_kk^T = A_mk in FP32
-// (L_kk rounded to FP32), 64 rows per CTA, 32-column blocks; the result
+// (L_kk rounded to FP32, l32), 64 rows per CTA, 32-column blocks; the result
 // overwrites A_mk and is written to the panel buffer.  The GEMM-style part
 // keeps 4 rows x 2 columns per thread with the operands transposed in shared
 // memory (one 16-byte and one 8-byte shared load per 8 FMAs).
 template <int FMT>
-__global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0, void *panel, __nv_bfloat16 *oz,
-                                                        double *ozs, const DevStatus *st)
+__global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0, const float *__restrict__ L,
+                                                        void *panel, __nv_bfloat16 *oz, double *ozs, const DevStatus *st)
 {
     if (mfailed(st)) return;
     const int b = tl.b;
     const int m = m0 + (int)blockIdx.x;
     const int r0 = (int)blockIdx.y * 64;
-    const double *L = tl.t64(k, k);
     float *A = tl.t32(m, k) + (size_t)r0 * b;
     const size_t prow0 = (size_t)(m - k - 1) * b + r0;
     __shared__ __align__(16) float Xt[16][64];   // [l][row]
@@ -133,7 +142,7 @@ __global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0,
             }
             for (int e = tid; e < 32 * 16; e += 256) {
                 const int c = e >> 4, l = e & 15;
-                Lt[l][c] = (float)L[(size_t)(c0 + c) * b + p + l];
+                Lt[l][c] = L[(size_t)(c0 + c) * b + p + l];
             }
             __syncthreads();
 #pragma unroll
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0,
             for (int j = 0; j < 2; ++j) Ab[4 * tr + i][2 * tc + j] = acc[i][j];
         for (int e = tid; e < 32 * 32; e += 256) {
             const int r = e >> 5, c = e & 31;
-            Ld[r][c] = (c <= r) ? (float)L[(size_t)(c0 + r) * b + c0 + c] : 0.0f;
+            Ld[r][c] = (c <= r) ? L[(size_t)(c0 + r) * b + c0 + c] : 0.0f;
         }
         __syncthreads();
         if (tid < 64) {
@@ -415,6 +424,10 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         e = cudaStreamWaitEvent(side, ev_col, 0);
         if (e == cudaSuccess) e = launch_potrf_diag(tl, k, st, side, kts);
         if (e == cudaSuccess && k + 1 < T) {
+            if (nf > 0)
+                EGS_LAUNCH(kts, KC_TRSM, side,
+                           k_l32_from_f64<<<(unsigned)((tl.bb() + 255) / 256 < 1024 ? (tl.bb() + 255) / 256 : 1024), 256,
+                                            0, side>>>(tl, k, mb.l32, st));
             e = launch_trsm_f64(tl, k, nb, st, side, kts);
             if (e == cudaSuccess && nb > 0) {
                 if (FMT == 3) {
@@ -443,7 +456,7 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         if (e == cudaSuccess && nf > 0)
             EGS_LAUNCH(kt, KC_TRSM, s,
                        k_trsm_panel_f32<FMT><<<dim3((unsigned)nf, (unsigned)(b / 64)), 256, 0, s>>>(
-                           tl, k, k + 1 + nb, panel, oz, ozs, st));
+                           tl, k, k + 1 + nb, mb.l32, panel, oz, ozs, st));
         // FP32 mode: band outputs with an FP32 operand by exact slices
         if (e == cudaSuccess && FMT == 3)
             e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, k, k + 1, 1, ozs, mb.err, s, kt);

@@ -17,8 +17,10 @@
 // so acc0 and acc1 are exact in FP32 (the tensor core adds exact BF16
 // products; every partial sum is a representable integer multiple of the
 // level's unit below 2^24 units), and acc2 carries only a rounding error
-// relative to its own, 2^-14-smaller, magnitude.  The FP64 epilogue forms
-// s_x s_y ((acc0 + acc1) + acc2).  Dropping the pairs with i + j > 6 leaves
+// relative to its own, 2^-14-smaller, magnitude.  The epilogue forms
+// acc0 + acc1 exactly as an FP32 pair (TwoSum), adds acc2 to the low part,
+// scales by the power of two s_x s_y on the exponents and subtracts the two
+// parts from the FP64 tile.  Dropping the pairs with i + j > 6 leaves
 // an error of about K 2^-35 s_x s_y 2^14, i.e. 35-bit products, which is the
 // accuracy the band updates need (FP32-accurate products there are not
 // enough; exact FP64 ones are).
@@ -52,6 +54,29 @@ constexpr int NPAIRS = 15;
 __device__ __forceinline__ bool ofailed(const DevStatus *st)
 {
     return st && *(volatile const unsigned long long *)&st->fail_index != kNoFail;
+}
+
+// log2 of a power of two held in a double (the row scales).
+__device__ __forceinline__ int pow2_exp(double p)
+{
+    return (int)((__double_as_longlong(p) >> 52) & 0x7FF) - 1023;
+}
+
+// x 2^esh as a double, exactly, built with integer operations (GB300 issues
+// 2 FP64 operations per clock per SM, so the epilogue keeps conversions and
+// scaling off the FP64 pipe).  FP32 zeros and subnormals (below 2^-126 of the
+// accumulator unit, far under the result's last bit) give 0; inf / NaN stay
+// inf / NaN.
+__device__ __forceinline__ double f32_scaled(float x, int esh)
+{
+    const uint32_t u = __float_as_uint(x);
+    const int ex = (int)((u >> 23) & 0xFFu);
+    if (ex == 0) return 0.0;
+    int e64 = (ex == 255) ? 2047 : ex - 127 + 1023 + esh;
+    if (e64 <= 0) return 0.0;
+    if (e64 > 2047) e64 = 2047;
+    const uint64_t bits = ((uint64_t)(u >> 31) << 63) | ((uint64_t)e64 << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
 }
 
 // Rows of a dense row-major FP64 matrix (rows x K) -> slices.
@@ -90,7 +115,9 @@ struct OzBandWork {
         w.yb = (w.n - k - 1) * tl.b + w.cb * OBN;
         return true;
     }
-    __device__ void apply(const OzItem &w, int r, const double (&v)[OBN]) const
+    // C -= 2^(ea + eb_c) (hi_c + lo_c): two FP64 subtractions per entry
+    __device__ void apply(const OzItem &w, int r, int ea, const int (&eb)[OBN], const float (&hi)[OBN],
+                          const float (&lo)[OBN]) const
     {
         double *C = tl.t64(w.m, w.n) + (size_t)(w.rb * OBM + r) * tl.b + w.cb * OBN;
         double2 c[OBN / 2];
@@ -98,8 +125,9 @@ struct OzBandWork {
         for (int i = 0; i < OBN / 2; ++i) c[i] = *reinterpret_cast<const double2 *>(C + 2 * i);
 #pragma unroll
         for (int i = 0; i < OBN / 2; ++i) {
-            c[i].x -= v[2 * i];
-            c[i].y -= v[2 * i + 1];
+            const int e0 = ea + eb[2 * i], e1 = ea + eb[2 * i + 1];
+            c[i].x = (c[i].x - f32_scaled(hi[2 * i], e0)) - f32_scaled(lo[2 * i], e0);
+            c[i].y = (c[i].y - f32_scaled(hi[2 * i + 1], e1)) - f32_scaled(lo[2 * i + 1], e1);
         }
 #pragma unroll
         for (int i = 0; i < OBN / 2; ++i) *reinterpret_cast<double2 *>(C + 2 * i) = c[i];
@@ -119,11 +147,17 @@ struct OzDenseWork {
         w.yb = w.cb * OBN;
         return true;
     }
-    __device__ void apply(const OzItem &w, int r, const double (&v)[OBN]) const
+    __device__ void apply(const OzItem &w, int r, int ea, const int (&eb)[OBN], const float (&hi)[OBN],
+                          const float (&lo)[OBN]) const
     {
         double *Cp = C + (size_t)(w.rb * OBM + r) * N + w.cb * OBN;
 #pragma unroll
-        for (int i = 0; i < OBN / 2; ++i) *reinterpret_cast<double2 *>(Cp + 2 * i) = make_double2(v[2 * i], v[2 * i + 1]);
+        for (int i = 0; i < OBN / 2; ++i) {
+            const int e0 = ea + eb[2 * i], e1 = ea + eb[2 * i + 1];
+            *reinterpret_cast<double2 *>(Cp + 2 * i) =
+                make_double2(f32_scaled(hi[2 * i], e0) + f32_scaled(lo[2 * i], e0),
+                             f32_scaled(hi[2 * i + 1], e1) + f32_scaled(lo[2 * i + 1], e1));
+        }
     }
 };
 
@@ -248,13 +282,24 @@ k_tc_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
             tc::tc_fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&tempty[buf]);  // the accumulators are in registers now
+            // (acc0 + acc1) exactly as hi + e (Knuth's TwoSum in FP32), then
+            // lo = e + acc2 (rounded 2^-24 below acc2, itself 2^-14 below
+            // the result); the row scales are powers of two, applied to the
+            // exponents
             const int r = q * 32 + lane;
-            const double sa = scA[wi.ya + r];
-            double v[OBN];
+            const int ea = pow2_exp(scA[wi.ya + r]);
+            int eb[OBN];
 #pragma unroll
-            for (int c = 0; c < OBN; ++c)
-                v[c] = sa * __ldg(scB + wi.yb + c) * (((double)a0v[c] + (double)a1v[c]) + (double)a2v[c]);
-            work.apply(wi, r, v);
+            for (int c = 0; c < OBN; ++c) {
+                eb[c] = pow2_exp(__ldg(scB + wi.yb + c));
+                const float x = a0v[c], y = a1v[c];
+                const float s = x + y;
+                const float bv = s - x;
+                const float e = (x - (s - bv)) + (y - bv);
+                a0v[c] = s;
+                a1v[c] = e + a2v[c];
+            }
+            work.apply(wi, r, ea, eb, a0v, a1v);
             ++t;
         }
     }

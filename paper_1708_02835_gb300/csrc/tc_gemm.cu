@@ -6,7 +6,7 @@
 //
 // A persistent kernel (one CTA per SM) loops over 128 x 256 blocks of the
 // output tiles: one elected thread of warp 0 streams 128-byte-wide K slices of
-// the two operands into a 3-stage shared-memory ring with TMA (128-byte
+// the two operands into a 4-stage shared-memory ring with TMA (128-byte
 // swizzle); one thread of warp 1 issues tcgen05.mma (M = 128, N = 256) into
 // one of two 256-column FP32 accumulators in TMEM and releases each stage with
 // tcgen05.commit; eight epilogue warps drain the other accumulator with
@@ -22,12 +22,16 @@ namespace egs {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, STAGES = 3;
+// 4 stages of 48 KB keep about 1.3 us of operands in flight (at the tensor
+// peak one stage is consumed in ~0.33 us); each epilogue warp then has one
+// 4 KB staging box for its TMA reduces.
+constexpr int BM = 128, BN = 256, STAGES = 4;
 constexpr int kReserveSms = 24;  // SMs the bulk update leaves to the lookahead chain
 constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_WARPS = 8;
 constexpr int STAGE_C = 32 * 32 * 4;  // one 32 x 32 FP32 box staged for the TMA reduce
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_WARPS * 2 * STAGE_C + 1024;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_WARPS * STAGE_C + 1024;
+static_assert(SMEM_BYTES + 512 <= 232448, "dynamic + static shared memory must fit 227 KB");
 constexpr uint32_t TMEM_COLS = 256;
 
 struct WorkItem {
@@ -282,7 +286,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        uint8_t *stage = smem + STAGES * STAGE_BYTES + (warp - 2) * 2 * STAGE_C;
+        uint8_t *stage = smem + STAGES * STAGE_BYTES + (warp - 2) * STAGE_C;
         int t = 0, issued = 0;
         for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
             WorkItem wi;
@@ -299,8 +303,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 for (int cc = half * (BN / 64); cc < (half + 1) * (BN / 64); ++cc) {
                     float v[32];
                     tc::tmem_ld32(d + (uint32_t)(cc * 32), v);
-                    uint8_t *sb = stage + (issued & 1) * STAGE_C;
-                    if (issued >= 2 && lane == 0) tc::bulk_wait_read<1>();  // the box two back has been read
+                    uint8_t *sb = stage;
+                    if (issued >= 1 && lane == 0) tc::bulk_wait_read<0>();  // the previous box has been read
                     __syncwarp();
                     // row `lane`, 16-byte chunk j at chunk position j ^ (lane & 7)
 #pragma unroll
