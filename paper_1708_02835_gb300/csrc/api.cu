@@ -94,6 +94,8 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
                     align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(double)));
     L.l32 = off;
     off += align256(bb * sizeof(float));
+    L.vinv = off;
+    off += align256((size_t)g.T * bb * sizeof(double));
     L.locs = off;
     off += align256((size_t)2 * g.n * sizeof(double));
     L.z = off;
@@ -199,6 +201,7 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
         mb.partials = (double *)(ws + ML.partials);
         mb.err = (int *)(ws + ML.err);
         mb.l32 = (float *)(ws + ML.l32);
+        mb.vinv = (double *)(ws + ML.vinv);
         const size_t ozb = align256(ozaki_slices_bytes(g.b, g.T));
         const size_t ozh = ozb + align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(double));
         for (int i = 0; i < 2; ++i) {

@@ -199,10 +199,11 @@ __device__ __forceinline__ void gemm_sub32(const EA *Am, int lda, const EB *An, 
 // ncols columns), L lower ncols x ncols at Lp (row stride ldl).  32-column
 // blocks: a GEMM-style update with the already-solved columns, then a
 // 32-wide substitution in shared memory.  256 threads; fewer rows per CTA put
-// more SMs on a panel when the panel is short.
+// more SMs on a panel when the panel is short.  cstart (a multiple of 32):
+// the columns before it are zero in A, hence in X, and are skipped.
 // ---------------------------------------------------------------------------
 template <int RB>
-__device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, double *Xp, int ldx, int ncols)
+__device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, double *Xp, int ldx, int ncols, int cstart = 0)
 {
     constexpr int RPG = RB / 8;  // rows per thread group (8 groups of 32 threads)
     __shared__ double Xs[RB][kPW + 1];
@@ -210,11 +211,11 @@ __device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, double *Xp,
     __shared__ double Ab[RB][33];
     __shared__ double Ld[32][33];
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    for (int c0 = 0; c0 < ncols; c0 += 32) {
+    for (int c0 = cstart; c0 < ncols; c0 += 32) {
         double acc[RPG];
 #pragma unroll
         for (int i = 0; i < RPG; ++i) acc[i] = Xp[(size_t)(ty * RPG + i) * ldx + c0 + tx];
-        for (int p = 0; p < c0; p += kPW) {
+        for (int p = cstart; p < c0; p += kPW) {
             for (int e = tid; e < RB * kPW; e += 256) {
                 const int r = e >> 4, l = e & 15;
                 Xs[r][l] = Xp[(size_t)r * ldx + p + l];

@@ -150,6 +150,7 @@ struct MixedBuffers {
     double *partials; // 2T
     int *err;
     float *l32;       // b x b: L_kk rounded to FP32 for the off-band TRSM of step k
+    double *vinv;     // T b x b: V_k = L_kk^-T (upper triangular) for the solves
     void *oz[2];      // FP32 mode: BF16 slices of the panel rows (ozaki_slices_bytes), step k uses k % 2
     double *ozs[2];   // FP32 mode: their row scales, (T-1) b doubles each
 };
@@ -165,7 +166,7 @@ struct Layout {
     size_t tiles, locs, z, zpad, partials, status, total;
 };
 struct MixedLayout {
-    size_t f64, f32, sig, panel, oz, l32, locs, z, vec, partials, status, err, total;
+    size_t f64, f32, sig, panel, oz, l32, vinv, locs, z, vec, partials, status, err, total;
 };
 struct EvalSetup {
     TileGeom g;
@@ -209,6 +210,9 @@ cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &ma
                                   int ncols, const double *scale, int *err, cudaStream_t s, KernelTimer *kt);
 cudaError_t launch_forward_solve(const Tiles &tl, double *zpad, double *partials, DevStatus *st, cudaStream_t s,
                                  KernelTimer *kt);
+// z_m -= L_mk y_k for m > k, y_k read from ysrc (may equal zpad).
+cudaError_t launch_gemv_panel(const Tiles &tl, int k, const double *ysrc, double *zpad, const DevStatus *st,
+                              cudaStream_t s, KernelTimer *kt);
 // L^T x = v in place (any Tiles storage).
 cudaError_t backward_solve(const Tiles &tl, double *v, const DevStatus *st, cudaStream_t s, KernelTimer *kt);
 cudaError_t launch_finalize(const double *partials, int T, int64_t n, DevStatus *st, cudaStream_t s, KernelTimer *kt);

@@ -21,7 +21,7 @@
 // diagonal tiles.  The quadratic form Z^T Sigma^-1 Z is won back in FP64 by
 // iterative refinement: x0 = L^-T L^-1 Z, r = Z - Sigma x0 with Sigma the FP64
 // copy written by the generator, x1 = x0 + L^-T L^-1 r, quad = Z^T x1.
-#include "egs_internal.cuh"
+#include "blocks.cuh"
 #include "slices.cuh"
 
 #include <cuda_bf16.h>
@@ -248,9 +248,9 @@ __device__ __forceinline__ double col_dot(const float *__restrict__ A, int b, in
     return (double)s;
 }
 
-// r_j -= L_kj^T x_k for j < k.  grid = (k, b/64); 64 columns x 4 row groups,
-// reduced in a fixed order.
-__global__ void __launch_bounds__(256) k_gemv_T(Tiles tl, int k, double *__restrict__ v, const DevStatus *st)
+// r_j -= L_kj^T x_k for j < k (x_k read from xsrc, which may equal v).
+// grid = (k, b/64); 64 columns x 4 row groups, reduced in a fixed order.
+__global__ void __launch_bounds__(256) k_gemv_T(Tiles tl, int k, const double *xsrc, double *v, const DevStatus *st)
 {
     if (mfailed(st)) return;
     __shared__ double xs[1024];
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) k_gemv_T(Tiles tl, int k, double *__restr
     const int b = tl.b, j = (int)blockIdx.x, c0 = (int)blockIdx.y * 64;
     const int tx = threadIdx.x & 63, g = threadIdx.x >> 6;
     for (int c = threadIdx.x; c < b; c += 256) {
-        xs[c] = v[(size_t)k * b + c];
+        xs[c] = xsrc[(size_t)k * b + c];
         xs32[c] = (float)xs[c];
     }
     __syncthreads();
@@ -268,6 +268,79 @@ __global__ void __launch_bounds__(256) k_gemv_T(Tiles tl, int k, double *__restr
     red[g][tx] = s;
     __syncthreads();
     if (g == 0) v[(size_t)j * b + c0 + tx] -= ((red[0][tx] + red[1][tx]) + red[2][tx]) + red[3][tx];
+}
+
+// V_k = L_kk^-T for every diagonal tile k = blockIdx.x: 16 rows of V_k per
+// CTA, each the solution of x L_kk^T = e_r (trsm_rows on identity rows; the
+// columns before the row's 32-column block are zero and skipped).  V_k is
+// upper triangular, so y = L_kk^-1 r = V_k^T r and x = L_kk^-T r = V_k r
+// become matrix-vector products spread over many SMs instead of a serial
+// substitution on one.
+__global__ void __launch_bounds__(256) k_inv_diag(Tiles tl, double *__restrict__ V, const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    const int b = tl.b, k = (int)blockIdx.x, r0 = (int)blockIdx.y * 16;
+    double *X = V + (size_t)k * tl.bb() + (size_t)r0 * b;
+    for (int e = threadIdx.x; e < 16 * b; e += 256) X[e] = (e / b + r0 == e % b) ? 1.0 : 0.0;
+    __syncthreads();
+    trsm_rows<16>(tl.t64(k, k), b, X, b, b, (r0 / 32) * 32);
+}
+
+// partials[k] = sum_i log L_kk[i][i] (fixed-order tree).
+__global__ void __launch_bounds__(256) k_logdet_tiles(Tiles tl, double *__restrict__ partials, const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    __shared__ double red[256];
+    const int b = tl.b, k = (int)blockIdx.x;
+    const double *L = tl.t64(k, k);
+    double a = 0.0;
+    for (int i = threadIdx.x; i < b; i += 256) a += log(L[(size_t)i * b + i]);
+    const double tot = block_sum(a, red);
+    if (threadIdx.x == 0) partials[k] = tot;
+}
+
+// out_k = V_k^T rhs_k (= L_kk^-1 rhs_k): 64 columns x 4 row groups per CTA,
+// rows r <= c only (V_k is upper triangular), fixed-order reduction.
+__global__ void __launch_bounds__(256) k_fwd_inv(const double *__restrict__ V, int b, int k,
+                                                 const double *__restrict__ rhs, double *__restrict__ out,
+                                                 const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    __shared__ double xs[1024];
+    __shared__ double red[4][64];
+    const double *Vk = V + (size_t)k * b * b;
+    const int c0 = (int)blockIdx.x * 64, tx = threadIdx.x & 63, g = threadIdx.x >> 6;
+    for (int r = threadIdx.x; r < b; r += 256) xs[r] = rhs[(size_t)k * b + r];
+    __syncthreads();
+    const int c = c0 + tx;
+    double sacc = 0.0;
+    for (int r = g; r < c0 + 64; r += 4) sacc = fma(Vk[(size_t)r * b + c], xs[r], sacc);
+    red[g][tx] = sacc;
+    __syncthreads();
+    if (g == 0) out[(size_t)k * b + c] = ((red[0][tx] + red[1][tx]) + red[2][tx]) + red[3][tx];
+}
+
+// out_k = V_k rhs_k (= L_kk^-T rhs_k): one warp per 8 rows, columns c >= r,
+// fixed shuffle tree.
+__global__ void __launch_bounds__(256) k_bwd_inv(const double *__restrict__ V, int b, int k,
+                                                 const double *__restrict__ rhs, double *__restrict__ out,
+                                                 const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    __shared__ double xs[1024];
+    const double *Vk = V + (size_t)k * b * b;
+    for (int c = threadIdx.x; c < b; c += 256) xs[c] = rhs[(size_t)k * b + c];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rr = 0; rr < 8; ++rr) {
+        const int r = (int)blockIdx.x * 64 + warp * 8 + rr;
+        const double *row = Vk + (size_t)r * b;
+        double sacc = 0.0;
+        for (int c = (r & ~31) + lane; c < b; c += 32) sacc = fma(row[c], xs[c], sacc);  // row[c] = 0 for c < r
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+        if (lane == 0) out[(size_t)k * b + r] = sacc;
+    }
 }
 
 // Sigma x, row part: rows[i*b + r] = sum_{j <= i} Sigma_ij[r][:] . x_j over the
@@ -335,19 +408,20 @@ __global__ void k_copy(double *__restrict__ dst, const double *__restrict__ src,
     if (i < npad) dst[i] = src[i];
 }
 
-// l from log-det partials, quad0 = y.y (partials) and quad = z.x (fixed order).
+// l from log-det partials, quad0 = y.y (y = L^-1 z) and quad = z.x (fixed order).
 __global__ void __launch_bounds__(1024) k_finalize_mixed(const double *__restrict__ partials, int T,
                                                          const double *__restrict__ zp, const double *__restrict__ x,
-                                                         int64_t npad, int64_t n, int refined, DevStatus *st)
+                                                         const double *__restrict__ y, int64_t npad, int64_t n,
+                                                         int refined, DevStatus *st)
 {
     __shared__ double red[1024];
     const int tid = threadIdx.x;
     double a = 0.0, q0 = 0.0, q = 0.0;
-    for (int t = tid; t < T; t += 1024) {
-        a += partials[t];
-        q0 += partials[T + t];
+    for (int t = tid; t < T; t += 1024) a += partials[t];
+    for (int64_t i = tid; i < npad; i += 1024) {
+        q = fma(zp[i], x[i], q);
+        q0 = fma(y[i], y[i], q0);
     }
-    for (int64_t i = tid; i < npad; i += 1024) q = fma(zp[i], x[i], q);
     double vals[3] = {a, q0, q};
     double tot[3];
     for (int v = 0; v < 3; ++v) {
@@ -383,7 +457,8 @@ cudaError_t backward_solve(const Tiles &tl, double *v, const DevStatus *st, cuda
 {
     for (int k = tl.T - 1; k >= 0; --k) {
         EGS_LAUNCH(kt, KC_TRSV, s, k_trsv_diag_T<<<1, tl.b, 0, s>>>(tl, k, v, st));
-        if (k > 0) EGS_LAUNCH(kt, KC_TRSV, s, k_gemv_T<<<dim3((unsigned)k, (unsigned)(tl.b / 64)), 256, 0, s>>>(tl, k, v, st));
+        if (k > 0)
+            EGS_LAUNCH(kt, KC_TRSV, s, k_gemv_T<<<dim3((unsigned)k, (unsigned)(tl.b / 64)), 256, 0, s>>>(tl, k, v, v, st));
     }
     return cudaGetLastError();
 }
@@ -477,6 +552,31 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
+// out = L^-1 rhs with the inverted diagonal tiles (rhs is overwritten).
+cudaError_t forward_solve_inv(const Tiles &tl, const double *V, double *rhs, double *out, const DevStatus *st,
+                              cudaStream_t s, KernelTimer *kt)
+{
+    for (int k = 0; k < tl.T; ++k) {
+        EGS_LAUNCH(kt, KC_TRSV, s, k_fwd_inv<<<(unsigned)(tl.b / 64), 256, 0, s>>>(V, tl.b, k, rhs, out, st));
+        cudaError_t e = launch_gemv_panel(tl, k, out, rhs, st, s, kt);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+// out = L^-T rhs with the inverted diagonal tiles (rhs is overwritten).
+cudaError_t backward_solve_inv(const Tiles &tl, const double *V, double *rhs, double *out, const DevStatus *st,
+                               cudaStream_t s, KernelTimer *kt)
+{
+    for (int k = tl.T - 1; k >= 0; --k) {
+        EGS_LAUNCH(kt, KC_TRSV, s, k_bwd_inv<<<(unsigned)(tl.b / 64), 256, 0, s>>>(V, tl.b, k, rhs, out, st));
+        if (k > 0)
+            EGS_LAUNCH(kt, KC_TRSV, s,
+                       k_gemv_T<<<dim3((unsigned)k, (unsigned)(tl.b / 64)), 256, 0, s>>>(tl, k, out, rhs, st));
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, int64_t n, const egs_matern_params &P,
@@ -502,14 +602,17 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     else e = factor_mixed<1>(mb, ma, mbm, mc, moz, st, s, kt);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);
-    // y = L^-1 z (log-det and y.y partials), x = L^-T y
+    // V_k = L_kk^-T for every diagonal tile and the log-det partials, then
+    // res = L^-1 z (kept for y.y), x = L^-T res
+    EGS_LAUNCH(kt, KC_TRSV, s, k_inv_diag<<<dim3((unsigned)T, (unsigned)(b / 16)), 256, 0, s>>>(tl, mb.vinv, st));
+    EGS_LAUNCH(kt, KC_TRSV, s, k_logdet_tiles<<<(unsigned)T, 256, 0, s>>>(tl, mb.partials, st));
     e = launch_pad_vector(z, n, mb.zp, npad, s, kt);
     if (e != cudaSuccess) return e;
     EGS_LAUNCH(kt, KC_OTHER, s, k_copy<<<vb, 256, 0, s>>>(mb.y, mb.zp, npad));
-    e = launch_forward_solve(tl, mb.y, mb.partials, st, s, kt);
+    e = forward_solve_inv(tl, mb.vinv, mb.y, mb.res, st, s, kt);
     if (e != cudaSuccess) return e;
-    EGS_LAUNCH(kt, KC_OTHER, s, k_copy<<<vb, 256, 0, s>>>(mb.x, mb.y, npad));
-    e = backward_solve(tl, mb.x, st, s, kt);
+    EGS_LAUNCH(kt, KC_OTHER, s, k_copy<<<vb, 256, 0, s>>>(mb.d, mb.res, npad));
+    e = backward_solve_inv(tl, mb.vinv, mb.d, mb.x, st, s, kt);
     if (e != cudaSuccess) return e;
     for (int it = 0; it < refine; ++it) {
         EGS_LAUNCH(kt, KC_OTHER, s,
@@ -517,14 +620,16 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
         EGS_LAUNCH(kt, KC_OTHER, s,
                    k_symv_cols<<<dim3((unsigned)T, (unsigned)(b / 64)), 256, 0, s>>>(mb.sig, b, T, mb.x, mb.cols, st));
         EGS_LAUNCH(kt, KC_OTHER, s, k_residual<<<vb, 256, 0, s>>>(mb.zp, mb.rows, mb.cols, mb.d, npad, st));
-        e = launch_forward_solve(tl, mb.d, nullptr, st, s, kt);
+        // correction: y = L^-1 d, rows = L^-T y (rows is free once d is formed)
+        e = forward_solve_inv(tl, mb.vinv, mb.d, mb.y, st, s, kt);
         if (e != cudaSuccess) return e;
-        e = backward_solve(tl, mb.d, st, s, kt);
+        e = backward_solve_inv(tl, mb.vinv, mb.y, mb.rows, st, s, kt);
         if (e != cudaSuccess) return e;
-        EGS_LAUNCH(kt, KC_OTHER, s, k_axpy<<<vb, 256, 0, s>>>(mb.x, mb.d, npad, st));
+        EGS_LAUNCH(kt, KC_OTHER, s, k_axpy<<<vb, 256, 0, s>>>(mb.x, mb.rows, npad, st));
     }
     EGS_LAUNCH(kt, KC_OTHER, s,
-               k_finalize_mixed<<<1, 1024, 0, s>>>(mb.partials, T, mb.zp, mb.x, npad, n, refine > 0 ? 1 : 0, st));
+               k_finalize_mixed<<<1, 1024, 0, s>>>(mb.partials, T, mb.zp, mb.x, mb.res, npad, n, refine > 0 ? 1 : 0,
+                                                   st));
     if (ev) cudaEventRecord(ev[3], s);
     return cudaGetLastError();
 }

@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(1024) k_trsv_diag_f64(Tiles tl, int k, double 
 // Panel: z_m -= L_mk y_k for m = k+1..T-1.  grid = (T-k-1, b/64), 256
 // threads; each warp owns 8 rows and reduces each row's dot product with a
 // fixed shuffle tree.  Tiles may be FP64 or (mixed mode) FP32.
-__global__ void __launch_bounds__(256) k_gemv_panel(Tiles tl, int k, double *__restrict__ zpad, DevStatus *st)
+__global__ void __launch_bounds__(256) k_gemv_panel(Tiles tl, int k, const double *ysrc, double *zpad,
+                                                    const DevStatus *st)
 {
     if (failed_s(st)) return;
     extern __shared__ double ys[];
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256) k_gemv_panel(Tiles tl, int k, double *__r
     const bool f64 = tl.is64(m, k);
     float *ys32 = reinterpret_cast<float *>(ys + b);
     for (int c = threadIdx.x; c < b; c += 256) {
-        const double v = zpad[(size_t)k * b + c];
+        const double v = ysrc[(size_t)k * b + c];
         ys[c] = v;
         ys32[c] = (float)v;
     }
@@ -130,8 +131,18 @@ cudaError_t launch_forward_solve(const Tiles &tl, double *zpad, double *partials
         if (k + 1 < T)
             EGS_LAUNCH(kt, KC_TRSV, s,
                        k_gemv_panel<<<dim3((unsigned)(T - k - 1), (unsigned)(b / 64)), 256,
-                                      (size_t)b * (sizeof(double) + sizeof(float)), s>>>(tl, k, zpad, st));
+                                      (size_t)b * (sizeof(double) + sizeof(float)), s>>>(tl, k, zpad, zpad, st));
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_panel(const Tiles &tl, int k, const double *ysrc, double *zpad, const DevStatus *st,
+                              cudaStream_t s, KernelTimer *kt)
+{
+    if (k + 1 >= tl.T) return cudaSuccess;
+    EGS_LAUNCH(kt, KC_TRSV, s,
+               k_gemv_panel<<<dim3((unsigned)(tl.T - k - 1), (unsigned)(tl.b / 64)), 256,
+                              (size_t)tl.b * (sizeof(double) + sizeof(float)), s>>>(tl, k, ysrc, zpad, st));
     return cudaGetLastError();
 }
 
