@@ -259,7 +259,9 @@ def run_mle(a, egs):
 
 def run_batched(a, egs):
     """Config 4: 512 independent problems, n ~ U{256..4096} on random sub-squares,
-    own theta each (FP64); tile picked by measuring 64 / 128 / 256."""
+    own theta each; FP64 and FP32-off-band (EGS_MIX_FP32) batches, each with its
+    tile picked by measuring 64 / 128 / 256.  The line's value is the FP64
+    batch; the FP32-off-band batch is reported beside it."""
     import numpy as np
     import torch
     import egs_inputs as ei
@@ -268,55 +270,67 @@ def run_batched(a, egs):
     dl = [_to_dev(p.locations().reshape(-1)) for p in probs]
     dz = [_to_dev(p.e()) for p in probs]
     th = np.array([p.theta for p in probs])
-    tune = {}
-    for tile in (64, 128, 256):
-        B = egs.egs_batch(ns, tile=tile)
-        B.run(dl, dz, th)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        B.run(dl, dz, th)
-        tune[tile] = time.perf_counter() - t0
-        B.close()
-    best = min(tune, key=tune.get)
-    B = egs.egs_batch(ns, tile=best)
-    for _ in range(a.warmup):
-        out, stat = B.run(dl, dz, th)
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.steps):
-        out, stat = B.run(dl, dz, th, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / a.steps
     flops = sum(n ** 3 / 3.0 for n in ns)
-    line = {"metric": "batched log-likelihood problems/s (config 4)", "value": len(ns) / (ms / 1e3),
-            "unit": "problems/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+    stream = torch.cuda.current_stream()
+
+    def measure(prec):
+        tune = {}
+        for tile in (64, 128, 256):
+            B = egs.egs_batch(ns, tile=tile, precision=prec)
+            B.run(dl, dz, th)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.run(dl, dz, th)
+            tune[tile] = time.perf_counter() - t0
+            B.close()
+        best = min(tune, key=tune.get)
+        B = egs.egs_batch(ns, tile=best, precision=prec)
+        for _ in range(a.warmup):
+            out, stat = B.run(dl, dz, th)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            out, stat = B.run(dl, dz, th, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        r = {"problems_per_s": len(ns) / (ms / 1e3), "ms_per_batch": ms, "tile": best, "graph_kernels": B.launches,
+             "autotune_seconds": tune, "potrf_tflops_equiv": flops / (ms / 1e3) / 1e12,
+             "failed": int(np.sum(stat != 0)), "workspace_gb": B.workspace_bytes / 1e9}
+        B.close()
+        return r, out
+
+    r64, out64 = measure("fp64")
+    r32, out32 = measure("fp32")
+    ok = np.isfinite(out32) & np.isfinite(out64)
+    r32["max_rel_diff_vs_fp64"] = float(np.max(np.abs(out32[ok] - out64[ok]) / np.maximum(1.0, np.abs(out64[ok]))))
+    line = {"metric": "batched log-likelihood problems/s (config 4)", "value": r64["problems_per_s"],
+            "unit": "problems/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": r64["ms_per_batch"],
             "higher_is_better": True, "dtype": "f64", "data": "synthetic (z ~ N(0, I))",
             "config": {"workload": "512 problems, n ~ U{256..4096}, jittered grids on random sub-squares, own theta",
-                       "tile": best, "graph_kernels": B.launches},
-            "autotune_seconds": tune, "potrf_tflops_equiv": flops / (ms / 1e3) / 1e12,
-            "not_pd": int(np.sum(stat != 0))}
-    B.close()
+                       "tile": r64["tile"], "graph_kernels": r64["graph_kernels"]},
+            "autotune_seconds": r64["autotune_seconds"], "potrf_tflops_equiv": r64["potrf_tflops_equiv"],
+            "not_pd": r64["failed"], "fp32_off_band": r32}
     print(json.dumps(line), flush=True)
 
 
 def run_serve(a, egs):
     """Config 5: 64 resident fields, n log-uniform in [1000, 40000], nu ~ U(0.3, 2);
     Poisson arrivals of theta updates at 0.5 / 0.8 / 0.95 of measured capacity,
-    half FP64 and half TF32; 150 GB HBM budget."""
+    half FP64 and half --precision (mixed); 150 GB HBM budget."""
     import numpy as np
     import egs_inputs as ei
     fields = ei.serving_fields(64)
     rng = np.random.default_rng(0)
-    srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=2)
+    mixed = a.precision if a.precision != "fp64" else "fp32"
+    srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=a.band)
     fids = [srv.add_field(np.ascontiguousarray(f.locations().reshape(-1)), f.e(), f.n) for f in fields]
 
     def request(i):
         f = int(rng.integers(len(fields)))
         th = tuple(float(v) * float(np.exp(rng.normal(0, 0.1))) for v in fields[f].theta)
-        return fids[f], th, ("fp64" if i % 2 == 0 else "tf32")
+        return fids[f], th, ("fp64" if i % 2 == 0 else mixed)
 
     # capacity: a closed burst of requests
     burst = [request(i) for i in range(16)]
@@ -331,7 +345,7 @@ def run_serve(a, egs):
     srv.close()
     results = {}
     for rho in (0.5, 0.8, 0.95):
-        srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=2)
+        srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=a.band)
         fids = [srv.add_field(np.ascontiguousarray(f.locations().reshape(-1)), f.e(), f.n) for f in fields]
         rate = rho * cap
         gaps = rng.exponential(1.0 / rate, a.requests)
@@ -352,14 +366,15 @@ def run_serve(a, egs):
         st = srv.stats()
         results[str(rho)] = {"rate_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                              "mean_ms": st["mean_ms"], "evals_per_s": st["evals_per_s"],
-                             "completed": st["completed"], "failed_not_pd": st["failed"],
+                             "completed": st["completed"], "failed_not_pd_or_inaccurate": st["failed"],
                              "inflight_peak": st["inflight_peak"], "bytes_peak": st["bytes_peak"]}
         srv.close()
     line = {"metric": "serve p50/p99 ms and evals/s (config 5)", "value": results["0.8"]["p50_ms"],
-            "unit": "ms (p50 at 0.8 of capacity)", "n_gpus": 1, "higher_is_better": False, "dtype": "f64/f64+tf32",
+            "unit": "ms (p50 at 0.8 of capacity)", "n_gpus": 1, "higher_is_better": False, "dtype": "f64/f64+" + mixed,
             "data": "synthetic (z ~ N(0, I))",
             "config": {"workload": "64 fields, n log-uniform [1000, 40000], nu ~ U(0.3, 2), Poisson arrivals, "
-                                   "50/50 FP64 and TF32, 150 GB budget, 8 slots", "capacity_per_s": cap},
+                                   "50/50 FP64 and %s (band %d), 150 GB budget, 8 slots" % (mixed, a.band),
+                       "capacity_per_s": cap},
             "rates": results}
     print(json.dumps(line), flush=True)
 

@@ -63,12 +63,15 @@ typedef enum {
     EGS_ERR_BUSY = 6,          /* resource busy (serving: queue full) */
     EGS_ERR_UNIMPLEMENTED = 7, /* feature not built */
     EGS_ERR_INACCURATE = 8     /* mixed precision only: the FP64 refinement step
-                                  changed the quadratic form by more than 1e-3
-                                  relative, i.e. the mixed factor is too inexact
-                                  for Sigma(theta) (condition number near
-                                  1/eps of the off-band precision); the value
-                                  is still in egs_info.loglik -- evaluate this
-                                  theta in EGS_FP64 */
+                                  changed the quadratic form by more than 1e-5
+                                  (EGS_MIX_FP32; the l it passes is then within
+                                  a few 1e-5 of FP64) or 1e-3 (TF32 / BF16: a
+                                  guard against gross errors) relative, i.e. the
+                                  mixed factor is too inexact for Sigma(theta)
+                                  (condition number near 1/eps of the off-band
+                                  precision); the value is still in
+                                  egs_info.loglik -- evaluate this theta in
+                                  EGS_FP64 */
 } egs_status;
 
 typedef enum {
@@ -242,7 +245,11 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
  *                   Synchronises stream.  Returns EGS_ERR_NOT_PD if any
  *                   problem failed (the others are still valid).
  * egs_loglik_batched  create + run + destroy in one call.
- * Only EGS_FP64 is built for batches.
+ * Batches are EGS_FP64 or EGS_MIX_FP32: an FP64 band of 2 tiles, FP32
+ * off-band tiles updated in FP32 on the CUDA cores, FP64 products for every
+ * band tile, one FP64 refinement step against an FP64 copy of Sigma (a
+ * problem of at most 2 tiles is all FP64); per_status[i] is
+ * EGS_ERR_INACCURATE when that step changes Z^T x by more than 1e-5 relative.
  */
 typedef struct egs_batch egs_batch;
 egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_precision p, egs_batch **out);

@@ -331,7 +331,9 @@ class egs_batch:
         stat = (ctypes.c_int * npb)()
         st = lib.egs_batch_run(self._h, lp, zp, th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), stat, _stream(stream))
-        if st != EGS_OK and (st != EGS_ERR_NOT_PD or raise_on_not_pd):
+        # per-problem failures (not positive definite, mixed factor too
+        # inexact) are reported in the status array unless asked to raise
+        if st != EGS_OK and (st not in (EGS_ERR_NOT_PD, EGS_ERR_INACCURATE) or raise_on_not_pd):
             _check(st)
         return out, np.array(list(stat))
 

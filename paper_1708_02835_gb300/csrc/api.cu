@@ -233,7 +233,8 @@ bool mixed_result_ok(const EvalSetup &es, const DevStatus &h)
 {
     if (!es.mixed || es.refine < 1) return true;
     const double q = h.result[2], q0 = h.result[3];
-    return std::fabs(q - q0) <= kRefineTol * std::fabs(q);
+    const double tol = es.p == EGS_MIX_FP32 ? kRefineTolFp32 : kRefineTol;
+    return std::fabs(q - q0) <= tol * std::fabs(q);
 }
 
 void fill_info(const EvalSetup &es, const DevStatus &h, egs_info *info)
@@ -434,7 +435,8 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
         return set_error(EGS_ERR_INACCURATE,
                          "the refinement step changed the quadratic form by %.3g relative (limit %g): the mixed "
                          "factor is too inexact for this Sigma; evaluate in EGS_FP64",
-                         std::fabs(h.result[2] - h.result[3]) / std::fabs(h.result[2]), kRefineTol);
+                         std::fabs(h.result[2] - h.result[3]) / std::fabs(h.result[2]),
+                         es.p == EGS_MIX_FP32 ? kRefineTolFp32 : kRefineTol);
     if (out_loglik) *out_loglik = h.result[0];
     return EGS_OK;
 }

@@ -1,5 +1,8 @@
 // Batched evaluation of many independent likelihood problems (uneven n, own
-// theta each) in FP64: the same tile algorithm as the single-problem path
+// theta each) in FP64, or in the FP32 mixed mode (FP64 band of 2 tiles, FP32
+// off-band tiles and FP32 off-band updates on the CUDA cores, FP64 updates
+// of every band tile, one FP64 refinement step against an FP64 copy of
+// Sigma, as in the single-problem FP32 mode): the same tile algorithm as the single-problem path
 // (Algorithm 2 with the tile Cholesky of Section 5.2), but every kernel
 // launch covers one step of *all* problems at once.  A launch's work items
 // are the concatenation of every problem's items for that step; the CTA finds
@@ -19,9 +22,12 @@ namespace egs {
 struct BatchProblem {
     const double *X, *Y, *z;
     int64_t n;
-    int T, pad;
-    double *tiles;     // T(T+1)/2 lower tiles of b x b
-    double *zpad;      // T*b
+    int T, band;       // band >= T: every tile FP64 (the FP64 batch)
+    double *tiles;     // FP64 tiles: T(T+1)/2 lower tiles, or the band tiles of a mixed problem
+    float *f32;        // mixed: off-band FP32 tiles
+    double *sig;       // mixed: dense FP64 copy of Sigma (lower tiles) for the refinement
+    double *zpad;      // T*b: Z, then the forward solution y
+    double *x, *d, *rows, *cols;  // mixed: T*b vectors
     double *partials;  // 2T
     DevStatus *st;
     const egs_matern_params *P;
@@ -46,7 +52,19 @@ __device__ __forceinline__ int find_problem(const BatchArgs &a, int64_t bid, int
     return lo;
 }
 
-__device__ __forceinline__ Tiles dense_tiles(const BatchProblem &p, int b) { return Tiles{p.tiles, nullptr, b, p.T, p.T}; }
+__device__ __forceinline__ Tiles dense_tiles(const BatchProblem &p, int b) { return Tiles{p.tiles, p.f32, b, p.T, p.band}; }
+
+// Vector `which` of a problem: 0 = zpad (Z / forward solution), 1 = x, 2 = d.
+__device__ __forceinline__ double *bvec(const BatchProblem &p, int which)
+{
+    return which == 0 ? p.zpad : (which == 1 ? p.x : p.d);
+}
+
+__device__ __forceinline__ int band_rows(const BatchProblem &p, int k)
+{
+    const int r = p.T - k - 1;
+    return p.band - 1 < r ? p.band - 1 : r;
+}
 
 // Matern tiles: item = (tile, 64 x 64 sub-block).
 __global__ void __launch_bounds__(256) kb_gen(BatchArgs a)
@@ -70,7 +88,11 @@ __global__ void __launch_bounds__(256) kb_gen(BatchArgs a)
     const int64_t n = pr.n;
     const int64_t gj = (int64_t)tj * b + sc * 64 + tx;
     const double xj = gj < n ? pr.X[gj] : 0.0, yj = gj < n ? pr.Y[gj] : 0.0;
-    double *tile = pr.tiles + (size_t)t * b * b;
+    const Tiles tl = dense_tiles(pr, b);
+    const bool is64 = tl.is64(ti, tj);
+    double *tile = is64 ? tl.t64(ti, tj) : nullptr;
+    float *tile32 = is64 ? nullptr : tl.t32(ti, tj);
+    double *tsig = pr.sig ? pr.sig + (size_t)t * b * b : nullptr;
     for (int rr = 0; rr < 16; ++rr) {
         const int r = sr * 64 + ty + 4 * rr;
         const int64_t gi = (int64_t)ti * b + r;
@@ -80,7 +102,10 @@ __global__ void __launch_bounds__(256) kb_gen(BatchArgs a)
         else {
             v = matern_eval(&Ps, loc_dist(&Ps, pr.X[gi], pr.Y[gi], xj, yj) * Ps.inv_th2);
         }
-        tile[(size_t)r * b + sc * 64 + tx] = v;
+        const size_t off = (size_t)r * b + sc * 64 + tx;
+        if (is64) tile[off] = v;
+        else tile32[off] = (float)v;
+        if (tsig) tsig[off] = v;
     }
 }
 
@@ -135,6 +160,20 @@ __global__ void __launch_bounds__(256) kb_trsm_panel(BatchArgs a, int k)
     trsm_rows<64>(tl.t64(k, k), b, tl.t64(m, k) + (size_t)r0 * b, b, b);
 }
 
+// Mixed problems: the off-band rows m = k + band .. T - 1 in FP32 (L_kk
+// rounded to FP32 as it is staged).
+__global__ void __launch_bounds__(256) kb_trsm_panel32(BatchArgs a, int k)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    const int b = a.b, per = b / 64;
+    const Tiles tl = dense_tiles(pr, b);
+    const int m = k + 1 + band_rows(pr, k) + (int)(local / per);
+    const int r0 = (int)(local % per) * 64;
+    trsm_rows<64, float>(tl.t64(k, k), b, tl.t32(m, k) + (size_t)r0 * b, b, b);
+}
+
 __global__ void __launch_bounds__(256) kb_update(BatchArgs a, int k)
 {
     int64_t local;
@@ -148,8 +187,21 @@ __global__ void __launch_bounds__(256) kb_update(BatchArgs a, int k)
     const int m = k + 1 + mm, nc = k + 1 + nn;
     const int sr = sub / nsub, sc = sub % nsub;
     if (m == nc && sc > sr) return;
-    gemm_sub64(tl.t64(m, k) + (size_t)sr * 64 * b, b, tl.t64(nc, k) + (size_t)sc * 64 * b, b, b,
-               tl.t64(m, nc) + (size_t)sr * 64 * b + sc * 64, b);
+    const size_t ao = (size_t)sr * 64 * b, bo = (size_t)sc * 64 * b, co = (size_t)sr * 64 * b + sc * 64;
+    if (tl.is64(m, nc)) {
+        // band (or FP64) output: FP64 products of the stored operands
+        if (tl.is64(m, k)) {
+            if (tl.is64(nc, k)) gemm_sub64(tl.t64(m, k) + ao, b, tl.t64(nc, k) + bo, b, b, tl.t64(m, nc) + co, b);
+            else gemm_sub64(tl.t64(m, k) + ao, b, tl.t32(nc, k) + bo, b, b, tl.t64(m, nc) + co, b);
+        } else {
+            if (tl.is64(nc, k)) gemm_sub64(tl.t32(m, k) + ao, b, tl.t64(nc, k) + bo, b, b, tl.t64(m, nc) + co, b);
+            else gemm_sub64(tl.t32(m, k) + ao, b, tl.t32(nc, k) + bo, b, b, tl.t64(m, nc) + co, b);
+        }
+    } else {
+        // off-band output (then m - k > band, so A_mk is FP32): FP32 update
+        if (tl.is64(nc, k)) gemm_sub64(tl.t32(m, k) + ao, b, tl.t64(nc, k) + bo, b, b, tl.t32(m, nc) + co, b);
+        else gemm_sub64(tl.t32(m, k) + ao, b, tl.t32(nc, k) + bo, b, b, tl.t32(m, nc) + co, b);
+    }
 }
 
 __global__ void kb_pad(BatchArgs a)
@@ -160,20 +212,20 @@ __global__ void kb_pad(BatchArgs a)
     if (i < (int64_t)pr.T * a.b) pr.zpad[i] = i < pr.n ? pr.z[i] : 0.0;
 }
 
-__global__ void __launch_bounds__(1024) kb_trsv_diag(BatchArgs a, int k)
+__global__ void __launch_bounds__(1024) kb_trsv_diag(BatchArgs a, int k, int which)
 {
     int64_t local;
     const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
     if (failed(pr.st)) return;
     __shared__ double ldq[2];
-    trsv_fwd_tile(dense_tiles(pr, a.b).t64(k, k), a.b, pr.zpad + (size_t)k * a.b, ldq);
-    if (threadIdx.x == 0) {
+    trsv_fwd_tile(dense_tiles(pr, a.b).t64(k, k), a.b, bvec(pr, which) + (size_t)k * a.b, which == 0 ? ldq : nullptr);
+    if (which == 0 && threadIdx.x == 0) {
         pr.partials[k] = ldq[0];
         pr.partials[pr.T + k] = ldq[1];
     }
 }
 
-__global__ void __launch_bounds__(256) kb_gemv_panel(BatchArgs a, int k)
+__global__ void __launch_bounds__(256) kb_gemv_panel(BatchArgs a, int k, int which)
 {
     int64_t local;
     const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
@@ -182,9 +234,143 @@ __global__ void __launch_bounds__(256) kb_gemv_panel(BatchArgs a, int k)
     const int b = a.b, per = b / 64;
     const int m = k + 1 + (int)(local / per);
     const int r0 = (int)(local % per) * 64;
-    for (int c = threadIdx.x; c < b; c += 256) ys[c] = pr.zpad[(size_t)k * b + c];
+    double *v = bvec(pr, which);
+    float *ys32 = reinterpret_cast<float *>(ys + b);
+    for (int c = threadIdx.x; c < b; c += 256) {
+        ys[c] = v[(size_t)k * b + c];
+        ys32[c] = (float)ys[c];
+    }
     __syncthreads();
-    gemv_rows(dense_tiles(pr, b).t64(m, k), b, r0, ys, pr.zpad + (size_t)m * b);
+    const Tiles tl = dense_tiles(pr, b);
+    if (tl.is64(m, k)) gemv_rows(tl.t64(m, k), b, r0, ys, v + (size_t)m * b);
+    else gemv_rows_f32(tl.t32(m, k), b, r0, ys32, v + (size_t)m * b);
+}
+
+// ---- mixed problems: backward solves, the FP64 refinement and l ----------
+
+// dst = src over the T*b entries (item = 256 entries).
+__global__ void kb_copy(BatchArgs a, int dst, int src)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    const int64_t i = local * 256 + threadIdx.x;
+    if (i < (int64_t)pr.T * a.b) bvec(pr, dst)[i] = bvec(pr, src)[i];
+}
+
+__global__ void __launch_bounds__(1024) kb_trsv_diag_T(BatchArgs a, int k, int which)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st) || k >= pr.T) return;
+    trsv_bwd_tile(dense_tiles(pr, a.b).t64(k, k), a.b, bvec(pr, which) + (size_t)k * a.b);
+}
+
+// r_j -= L_kj^T x_k, item = (j < k, 64-column block).
+__global__ void __launch_bounds__(256) kb_gemv_T(BatchArgs a, int k, int which)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    const int b = a.b, per = b / 64;
+    const int j = (int)(local / per), c0 = (int)(local % per) * 64;
+    double *v = bvec(pr, which);
+    gemv_T_cols(dense_tiles(pr, b), k, j, c0, v + (size_t)k * b, v + (size_t)j * b);
+}
+
+// rows[i b + r] = sum_{j <= i} Sigma_ij[r][:] . x_j; item = (i, 8 rows).
+__global__ void __launch_bounds__(256) kb_symv_rows(BatchArgs a)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    const int b = a.b, per = b / 8;
+    const int i = (int)(local / per), lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = (int)(local % per) * 8 + warp;
+    const size_t bb = (size_t)b * b;
+    double s = 0.0;
+    for (int j = 0; j <= i; ++j) {
+        const double *row = pr.sig + (size_t)tile_linear(i, j) * bb + (size_t)r * b;
+        const double *xj = pr.x + (size_t)j * b;
+        for (int c = lane; c < b; c += 32) s = fma(row[c], xj[c], s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) pr.rows[(size_t)i * b + r] = s;
+}
+
+// cols[i b + c] = sum_{m > i} Sigma_mi[:, c] . x_m; item = (i, 64 columns).
+__global__ void __launch_bounds__(256) kb_symv_cols(BatchArgs a)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    __shared__ double red[4][64];
+    const int b = a.b, per = b / 64;
+    const int i = (int)(local / per), c0 = (int)(local % per) * 64;
+    const int tx = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const size_t bb = (size_t)b * b;
+    double s = 0.0;
+    for (int m = i + 1; m < pr.T; ++m) {
+        const double *A = pr.sig + (size_t)tile_linear(m, i) * bb + c0 + tx;
+        const double *xm = pr.x + (size_t)m * b;
+        for (int r = g; r < b; r += 4) s = fma(A[(size_t)r * b], xm[r], s);
+    }
+    red[g][tx] = s;
+    __syncthreads();
+    if (g == 0) pr.cols[(size_t)i * b + c0 + tx] = ((red[0][tx] + red[1][tx]) + red[2][tx]) + red[3][tx];
+}
+
+// d = z - (rows + cols) (z padded with zeros), item = 256 entries.
+__global__ void kb_residual(BatchArgs a)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    const int64_t i = local * 256 + threadIdx.x;
+    if (i < (int64_t)pr.T * a.b) pr.d[i] = (i < pr.n ? pr.z[i] : 0.0) - (pr.rows[i] + pr.cols[i]);
+}
+
+__global__ void kb_axpy(BatchArgs a)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    if (failed(pr.st)) return;
+    const int64_t i = local * 256 + threadIdx.x;
+    if (i < (int64_t)pr.T * a.b) pr.x[i] += pr.d[i];
+}
+
+// l from the log-det partials and the refined quadratic form z . x;
+// result[3] keeps y . y (the unrefined one) for the accuracy check.
+__global__ void __launch_bounds__(256) kb_finalize_mixed(BatchArgs a)
+{
+    int64_t local;
+    const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
+    __shared__ double red[256];
+    double s = 0.0, q0 = 0.0, q = 0.0;
+    for (int t = threadIdx.x; t < pr.T; t += 256) {
+        s += pr.partials[t];
+        q0 += pr.partials[pr.T + t];
+    }
+    for (int64_t i = threadIdx.x; i < pr.n; i += 256) q = fma(pr.z[i], pr.x[i], q);
+    const double lsum = block_sum(s, red);
+    __syncthreads();
+    const double q0sum = block_sum(q0, red);
+    __syncthreads();
+    const double qsum = block_sum(q, red);
+    if (threadIdx.x == 0) {
+        DevStatus *st = pr.st;
+        if (failed(st)) {
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            st->result[0] = st->result[1] = st->result[2] = st->result[3] = nan;
+        } else {
+            const double logdet = 2.0 * lsum;
+            st->result[0] = -0.5 * qsum - 0.5 * logdet - 0.5 * (double)pr.n * 1.8378770664093454836;
+            st->result[1] = logdet;
+            st->result[2] = qsum;
+            st->result[3] = q0sum;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) kb_finalize(BatchArgs a)
@@ -223,6 +409,8 @@ using namespace egs;
 
 struct egs_batch {
     int nprob = 0, b = 0;
+    bool mixed = false;  // EGS_MIX_FP32 batch (band kBatchBand)
+    int band = 0;
     std::vector<int64_t> n;
     std::vector<int> T;
     char *ws = nullptr;
@@ -250,13 +438,18 @@ struct egs_batch {
 
 namespace {
 
-enum { L_GEN, L_POTRF, L_TRSM_SUB, L_SYRK_SUB, L_TRSM, L_UPDATE, L_PAD, L_TRSV, L_GEMV, L_FINAL };
+enum {
+    L_GEN, L_POTRF, L_TRSM_SUB, L_SYRK_SUB, L_TRSM, L_TRSM32, L_UPDATE, L_PAD, L_TRSV, L_GEMV, L_FINAL,
+    L_COPY, L_TRSV_T, L_GEMV_T, L_SYMV_R, L_SYMV_C, L_RESID, L_AXPY, L_FINAL_M
+};
+
+constexpr int kBatchBand = 2;  // FP64 band of the mixed batches (tiles)
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 void plan_launches(egs_batch *B, std::vector<int64_t> &prefix)
 {
-    const int b = B->b, nsub = b / 64, np = B->nprob;
+    const int b = B->b, nsub = b / 64, per = b / 64, np = B->nprob;
     int Tmax = 0;
     for (int t : B->T) Tmax = std::max(Tmax, t);
     auto add = [&](int kind, int k, int p, auto count) {
@@ -269,6 +462,9 @@ void plan_launches(egs_batch *B, std::vector<int64_t> &prefix)
         prefix.push_back(acc);
         B->launches.back().items = acc;
     };
+    auto band_of = [&](int q) { return B->mixed ? std::min(kBatchBand, B->T[q]) : B->T[q]; };
+    auto nb_of = [&](int q, int k) { return (int64_t)std::min(band_of(q) - 1, B->T[q] - k - 1); };
+    auto vec_items = [&](int q) { return ((int64_t)B->T[q] * b + 255) / 256; };
     add(L_GEN, 0, 0, [&](int q) { return (int64_t)B->T[q] * (B->T[q] + 1) / 2 * nsub * nsub; });
     for (int k = 0; k < Tmax; ++k) {
         for (int p = 0; p < b; p += kIB) {
@@ -279,18 +475,44 @@ void plan_launches(egs_batch *B, std::vector<int64_t> &prefix)
                 add(L_SYRK_SUB, k, p, [&](int q) { return B->T[q] > k ? n32 * (n32 + 1) / 2 : (int64_t)0; });
             }
         }
-        add(L_TRSM, k, 0, [&](int q) { return B->T[q] > k + 1 ? (int64_t)(B->T[q] - k - 1) * (b / 64) : (int64_t)0; });
+        add(L_TRSM, k, 0, [&](int q) { return B->T[q] > k + 1 ? nb_of(q, k) * per : (int64_t)0; });
+        if (B->mixed)
+            add(L_TRSM32, k, 0, [&](int q) {
+                return B->T[q] > k + 1 ? ((int64_t)(B->T[q] - k - 1) - nb_of(q, k)) * per : (int64_t)0;
+            });
         add(L_UPDATE, k, 0, [&](int q) {
             const int64_t r = B->T[q] - k - 1;
             return r > 0 ? r * (r + 1) / 2 * nsub * nsub : (int64_t)0;
         });
     }
-    add(L_PAD, 0, 0, [&](int q) { return ((int64_t)B->T[q] * b + 255) / 256; });
-    for (int k = 0; k < Tmax; ++k) {
-        add(L_TRSV, k, 0, [&](int q) { return (int64_t)(B->T[q] > k ? 1 : 0); });
-        add(L_GEMV, k, 0, [&](int q) { return B->T[q] > k + 1 ? (int64_t)(B->T[q] - k - 1) * (b / 64) : (int64_t)0; });
+    add(L_PAD, 0, 0, vec_items);
+    auto forward = [&](int which) {
+        for (int k = 0; k < Tmax; ++k) {
+            add(L_TRSV, k, which, [&](int q) { return (int64_t)(B->T[q] > k ? 1 : 0); });
+            add(L_GEMV, k, which,
+                [&](int q) { return B->T[q] > k + 1 ? (int64_t)(B->T[q] - k - 1) * per : (int64_t)0; });
+        }
+    };
+    auto backward = [&](int which) {
+        for (int k = Tmax - 1; k >= 0; --k) {
+            add(L_TRSV_T, k, which, [&](int q) { return (int64_t)(B->T[q] > k ? 1 : 0); });
+            if (k > 0) add(L_GEMV_T, k, which, [&](int q) { return B->T[q] > k ? (int64_t)k * per : (int64_t)0; });
+        }
+    };
+    forward(0);  // y = L^-1 z in zpad, log-det and y.y partials
+    if (!B->mixed) {
+        add(L_FINAL, 0, 0, [&](int) { return (int64_t)1; });
+        return;
     }
-    add(L_FINAL, 0, 0, [&](int) { return (int64_t)1; });
+    add(L_COPY, 0, 1 * 4 + 0, vec_items);  // x = y
+    backward(1);                           // x = L^-T y
+    add(L_SYMV_R, 0, 0, [&](int q) { return (int64_t)B->T[q] * (b / 8); });
+    add(L_SYMV_C, 0, 0, [&](int q) { return (int64_t)B->T[q] * per; });
+    add(L_RESID, 0, 0, vec_items);         // d = z - Sigma x
+    forward(2);
+    backward(2);                           // d = L^-T L^-1 d
+    add(L_AXPY, 0, 0, vec_items);          // x += d
+    add(L_FINAL_M, 0, 0, [&](int) { return (int64_t)1; });
 }
 
 cudaError_t enqueue_all(egs_batch *B, cudaStream_t s)
@@ -306,11 +528,22 @@ cudaError_t enqueue_all(egs_batch *B, cudaStream_t s)
         case L_TRSM_SUB: kb_trsm_sub<<<g, 256, 0, s>>>(a, L.k, L.p); break;
         case L_SYRK_SUB: kb_syrk_sub<<<g, 256, 0, s>>>(a, L.k, L.p); break;
         case L_TRSM: kb_trsm_panel<<<g, 256, 0, s>>>(a, L.k); break;
+        case L_TRSM32: kb_trsm_panel32<<<g, 256, 0, s>>>(a, L.k); break;
         case L_UPDATE: kb_update<<<g, 256, 0, s>>>(a, L.k); break;
         case L_PAD: kb_pad<<<g, 256, 0, s>>>(a); break;
-        case L_TRSV: kb_trsv_diag<<<g, B->b, 0, s>>>(a, L.k); break;
-        case L_GEMV: kb_gemv_panel<<<g, 256, (size_t)B->b * sizeof(double), s>>>(a, L.k); break;
+        case L_TRSV: kb_trsv_diag<<<g, B->b, 0, s>>>(a, L.k, L.p); break;
+        case L_GEMV:
+            kb_gemv_panel<<<g, 256, (size_t)B->b * (sizeof(double) + sizeof(float)), s>>>(a, L.k, L.p);
+            break;
         case L_FINAL: kb_finalize<<<g, 256, 0, s>>>(a); break;
+        case L_COPY: kb_copy<<<g, 256, 0, s>>>(a, L.p / 4, L.p % 4); break;
+        case L_TRSV_T: kb_trsv_diag_T<<<g, B->b, 0, s>>>(a, L.k, L.p); break;
+        case L_GEMV_T: kb_gemv_T<<<g, 256, 0, s>>>(a, L.k, L.p); break;
+        case L_SYMV_R: kb_symv_rows<<<g, 256, 0, s>>>(a); break;
+        case L_SYMV_C: kb_symv_cols<<<g, 256, 0, s>>>(a); break;
+        case L_RESID: kb_residual<<<g, 256, 0, s>>>(a); break;
+        case L_AXPY: kb_axpy<<<g, 256, 0, s>>>(a); break;
+        case L_FINAL_M: kb_finalize_mixed<<<g, 256, 0, s>>>(a); break;
         }
         ++count;
     }
@@ -326,7 +559,8 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
 {
     if (!out || !n || nprob < 1) return set_error(EGS_ERR_ARG, "egs_batch_create: bad arguments");
     *out = nullptr;
-    if (p != EGS_FP64) return set_error(EGS_ERR_UNIMPLEMENTED, "egs_batch_create: only EGS_FP64 is built");
+    if (p != EGS_FP64 && p != EGS_MIX_FP32)
+        return set_error(EGS_ERR_UNIMPLEMENTED, "egs_batch_create: batches are EGS_FP64 or EGS_MIX_FP32");
     if (tile == 0) {
         int64_t nmax = 0;
         for (int i = 0; i < nprob; ++i) nmax = std::max(nmax, n[i]);
@@ -336,8 +570,10 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
     egs_batch *B = new egs_batch;
     B->nprob = nprob;
     B->b = tile;
+    B->mixed = (p == EGS_MIX_FP32);
     size_t off = 0;
-    std::vector<size_t> tiles_off(nprob), zpad_off(nprob), part_off(nprob);
+    std::vector<size_t> tiles_off(nprob), zpad_off(nprob), part_off(nprob), f32_off(nprob), sig_off(nprob),
+        vec_off(nprob);
     size_t in_doubles = 0;
     for (int i = 0; i < nprob; ++i) {
         if (n[i] < 1) {
@@ -345,12 +581,20 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
             return set_error(EGS_ERR_ARG, "egs_batch_create: n[%d] = %lld", i, (long long)n[i]);
         }
         const int T = (int)((n[i] + tile - 1) / tile);
+        const int band = B->mixed ? std::min(kBatchBand, T) : T;
+        const size_t bb = (size_t)tile * tile, npad = (size_t)T * tile;
         B->n.push_back(n[i]);
         B->T.push_back(T);
         tiles_off[i] = off;
-        off += a256((size_t)T * (T + 1) / 2 * tile * tile * sizeof(double));
+        off += a256(Tiles::f64_tiles(T, band) * bb * sizeof(double));
+        f32_off[i] = off;
+        off += a256(Tiles::f32_tiles(T, band) * bb * sizeof(float));
+        sig_off[i] = off;
+        if (B->mixed) off += a256((size_t)T * (T + 1) / 2 * bb * sizeof(double));
+        vec_off[i] = off;
+        if (B->mixed) off += 4 * a256(npad * sizeof(double));
         zpad_off[i] = off;
-        off += a256((size_t)T * tile * sizeof(double));
+        off += a256(npad * sizeof(double));
         part_off[i] = off;
         off += a256((size_t)2 * T * sizeof(double));
         B->in_off.push_back(in_doubles);
@@ -399,7 +643,18 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
         pr.z = in + 2 * n[i];
         pr.n = n[i];
         pr.T = B->T[i];
+        pr.band = B->mixed ? std::min(kBatchBand, pr.T) : pr.T;
         pr.tiles = (double *)(B->ws + tiles_off[i]);
+        if (B->mixed) {
+            const size_t vstride = a256((size_t)pr.T * tile * sizeof(double));
+            char *v = B->ws + vec_off[i];
+            pr.f32 = (float *)(B->ws + f32_off[i]);
+            pr.sig = (double *)(B->ws + sig_off[i]);
+            pr.x = (double *)v;
+            pr.d = (double *)(v + vstride);
+            pr.rows = (double *)(v + 2 * vstride);
+            pr.cols = (double *)(v + 3 * vstride);
+        }
         pr.zpad = (double *)(B->ws + zpad_off[i]);
         pr.partials = (double *)(B->ws + part_off[i]);
         pr.st = B->d_status + i;
@@ -470,12 +725,17 @@ egs_status egs_batch_run(egs_batch *B, const double *const *locs, const double *
     if (e != cudaSuccess) return cuda_error(e, "egs_batch_run");
     egs_status worst = EGS_OK;
     for (int i = 0; i < B->nprob; ++i) {
-        const bool ok = B->h_status[i].fail_index == kNoFail;
-        if (out) out[i] = B->h_status[i].result[0];
-        if (per_status) per_status[i] = ok ? EGS_OK : EGS_ERR_NOT_PD;
-        if (!ok) worst = EGS_ERR_NOT_PD;
+        const DevStatus &h = B->h_status[i];
+        egs_status si = EGS_OK;
+        if (h.fail_index != kNoFail) si = EGS_ERR_NOT_PD;
+        else if (B->mixed && std::fabs(h.result[2] - h.result[3]) > kRefineTolFp32 * std::fabs(h.result[2]))
+            si = EGS_ERR_INACCURATE;
+        if (out) out[i] = si == EGS_OK ? h.result[0] : NAN;
+        if (per_status) per_status[i] = si;
+        if (si != EGS_OK && worst != EGS_ERR_NOT_PD) worst = si;
     }
-    if (worst != EGS_OK) set_error(worst, "egs_batch_run: at least one problem is not positive definite");
+    if (worst == EGS_ERR_NOT_PD) set_error(worst, "egs_batch_run: at least one problem is not positive definite");
+    else if (worst != EGS_OK) set_error(worst, "egs_batch_run: at least one mixed-precision problem is too inexact");
     return worst;
 }
 

@@ -200,19 +200,20 @@ __device__ __forceinline__ void gemm_sub32(const EA *Am, int lda, const EB *An, 
 // blocks: a GEMM-style update with the already-solved columns, then a
 // 32-wide substitution in shared memory.  256 threads; fewer rows per CTA put
 // more SMs on a panel when the panel is short.  cstart (a multiple of 32):
-// the columns before it are zero in A, hence in X, and are skipped.
+// the columns before it are zero in A, hence in X, and are skipped.  TX =
+// float: X and all arithmetic in FP32 (L rounded to FP32 as it is staged).
 // ---------------------------------------------------------------------------
-template <int RB>
-__device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, double *Xp, int ldx, int ncols, int cstart = 0)
+template <int RB, typename TX = double>
+__device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, TX *Xp, int ldx, int ncols, int cstart = 0)
 {
     constexpr int RPG = RB / 8;  // rows per thread group (8 groups of 32 threads)
-    __shared__ double Xs[RB][kPW + 1];
-    __shared__ double Ls[32][kPW + 1];
-    __shared__ double Ab[RB][33];
-    __shared__ double Ld[32][33];
+    __shared__ TX Xs[RB][kPW + 1];
+    __shared__ TX Ls[32][kPW + 1];
+    __shared__ TX Ab[RB][33];
+    __shared__ TX Ld[32][33];
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     for (int c0 = cstart; c0 < ncols; c0 += 32) {
-        double acc[RPG];
+        TX acc[RPG];
 #pragma unroll
         for (int i = 0; i < RPG; ++i) acc[i] = Xp[(size_t)(ty * RPG + i) * ldx + c0 + tx];
         for (int p = cstart; p < c0; p += kPW) {
@@ -222,12 +223,12 @@ __device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, double *Xp,
             }
             for (int e = tid; e < 32 * kPW; e += 256) {
                 const int c = e >> 4, l = e & 15;
-                Ls[c][l] = Lp[(size_t)(c0 + c) * ldl + p + l];
+                Ls[c][l] = (TX)Lp[(size_t)(c0 + c) * ldl + p + l];
             }
             __syncthreads();
 #pragma unroll
             for (int l = 0; l < kPW; ++l) {
-                const double lv = Ls[tx][l];
+                const TX lv = Ls[tx][l];
 #pragma unroll
                 for (int i = 0; i < RPG; ++i) acc[i] = fma(-Xs[ty * RPG + i][l], lv, acc[i]);
             }
@@ -237,12 +238,12 @@ __device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, double *Xp,
         for (int i = 0; i < RPG; ++i) Ab[ty * RPG + i][tx] = acc[i];
         for (int e = tid; e < 32 * 32; e += 256) {
             const int r = e >> 5, c = e & 31;
-            Ld[r][c] = (c <= r) ? Lp[(size_t)(c0 + r) * ldl + c0 + c] : 0.0;
+            Ld[r][c] = (c <= r) ? (TX)Lp[(size_t)(c0 + r) * ldl + c0 + c] : (TX)0;
         }
         __syncthreads();
         if (tid < RB) {
             for (int j = 0; j < 32; ++j) {
-                double s = Ab[tid][j];
+                TX s = Ab[tid][j];
                 for (int l = 0; l < j; ++l) s -= Ab[tid][l] * Ld[j][l];
                 Ab[tid][j] = s / Ld[j][j];
             }
@@ -256,35 +257,49 @@ __device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, double *Xp,
 
 // ---------------------------------------------------------------------------
 // C (64 x 64, row stride ldc) -= Am (64 x K) An (64 x K)^T with row strides
-// lda, ldb; the operands may be FP64 or FP32 (widened to FP64 on staging, so
-// the products and sums are FP64 either way).  4 x 4 outputs per thread (rows ty + 16 i, columns tx + 16 j, so a
+// lda, ldb; the operands may be FP64 or FP32 and are converted to the
+// accumulation type TC on staging (TC = double: FP64 products and sums of
+// FP64 or FP32 operands; TC = float: an FP32 update of an FP32 tile).  4 x 4 outputs per thread (rows ty + 16 i, columns tx + 16 j, so a
 // half-warp touches 128 contiguous bytes).  256 threads.
 // ---------------------------------------------------------------------------
-template <typename EA, typename EB>
-__device__ __forceinline__ void gemm_sub64(const EA *Am, int lda, const EB *An, int ldb, int K, double *C, int ldc)
+// Staging buffers of gemm_sub64, one set per accumulation type in a kernel
+// (however many operand-type combinations it instantiates).
+template <typename TC>
+struct GemmSmem {
+    TC As[kPW][65];
+    TC Bs[kPW][65];
+};
+template <typename TC>
+__device__ __forceinline__ GemmSmem<TC> &gemm_smem()
 {
-    __shared__ double As[kPW][65];
-    __shared__ double Bs[kPW][65];
+    __shared__ GemmSmem<TC> sm;
+    return sm;
+}
+
+template <typename EA, typename EB, typename TC = double>
+__device__ __forceinline__ void gemm_sub64(const EA *Am, int lda, const EB *An, int ldb, int K, TC *C, int ldc)
+{
+    GemmSmem<TC> &sm = gemm_smem<TC>();
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    double acc[4][4];
+    TC acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; ++j) acc[i][j] = (TC)0;
     for (int p = 0; p < K; p += kPW) {
         for (int e = tid; e < 64 * kPW; e += 256) {
             const int r = e >> 4, l = e & 15;
-            As[l][r] = (double)Am[(size_t)r * lda + p + l];
-            Bs[l][r] = (double)An[(size_t)r * ldb + p + l];
+            sm.As[l][r] = (TC)Am[(size_t)r * lda + p + l];
+            sm.Bs[l][r] = (TC)An[(size_t)r * ldb + p + l];
         }
         __syncthreads();
 #pragma unroll
         for (int l = 0; l < kPW; ++l) {
-            double a[4], bv[4];
+            TC a[4], bv[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[l][ty + 16 * i];
+            for (int i = 0; i < 4; ++i) a[i] = sm.As[l][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[l][tx + 16 * j];
+            for (int j = 0; j < 4; ++j) bv[j] = sm.Bs[l][tx + 16 * j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -381,6 +396,79 @@ __device__ __forceinline__ void gemv_rows(const E *__restrict__ A, int b, int r0
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
         if (lane == 0) out[r] -= s;
     }
+}
+
+// Backward substitution on one diagonal tile: L^T x = r in place on v (b
+// entries), blockDim.x = b (thread i owns row i).  32-column blocks from the
+// last: the owning warp solves its 32 x 32 block with shuffles, then every
+// thread with a smaller row index subtracts the block's contribution (L read
+// along its rows).
+__device__ __forceinline__ void trsv_bwd_tile(const double *__restrict__ L, int b, double *__restrict__ v)
+{
+    __shared__ double xv[1024];
+    __shared__ double D[32][33];
+    const int i = threadIdx.x, lane = i & 31, w = i >> 5;
+    double r = v[i];
+    for (int cb = b / 32 - 1; cb >= 0; --cb) {
+        const int c0 = cb * 32;
+        for (int e = i; e < 32 * 32; e += b) D[e >> 5][e & 31] = L[(size_t)(c0 + (e >> 5)) * b + c0 + (e & 31)];
+        __syncthreads();
+        if (w == cb) {
+            for (int jj = 31; jj >= 0; --jj) {
+                const double xj = __shfl_sync(0xffffffffu, r, jj) / D[jj][jj];
+                if (lane == jj) xv[c0 + jj] = xj;
+                if (lane < jj) r = fma(-D[jj][lane], xj, r);
+            }
+        }
+        __syncthreads();
+        if (i < c0) {
+            double s = 0.0;
+#pragma unroll 8
+            for (int jj = 0; jj < 32; ++jj) s = fma(L[(size_t)(c0 + jj) * b + i], xv[c0 + jj], s);
+            r -= s;
+        }
+    }
+    __syncthreads();
+    v[i] = xv[i];
+}
+
+__device__ __forceinline__ double col_dot(const double *__restrict__ A, int b, int c, int g, const double *xs,
+                                          const float *)
+{
+    double s = 0.0;
+    for (int r = g; r < b; r += 4) s = fma(A[(size_t)r * b + c], xs[r], s);
+    return s;
+}
+
+// Off-band (FP32) tiles: products and the partial sum in FP32 (the tile is
+// only FP32 accurate; the refinement recovers the quadratic form in FP64).
+__device__ __forceinline__ double col_dot(const float *__restrict__ A, int b, int c, int g, const double *,
+                                          const float *xs32)
+{
+    float s = 0.0f;
+    for (int r = g; r < b; r += 4) s = fmaf(A[(size_t)r * b + c], xs32[r], s);
+    return (double)s;
+}
+
+// vj[c0 .. c0+63] -= (L_kj^T xk)[c0 .. c0+63] for one tile (FP64 or FP32):
+// 64 columns x 4 row groups, reduced in a fixed order.  256 threads.
+__device__ __forceinline__ void gemv_T_cols(const Tiles &tl, int k, int j, int c0, const double *xk, double *vj)
+{
+    __shared__ double xs[1024];
+    __shared__ float xs32[1024];
+    __shared__ double red[4][64];
+    const int b = tl.b;
+    const int tx = threadIdx.x & 63, g = threadIdx.x >> 6;
+    for (int c = threadIdx.x; c < b; c += 256) {
+        xs[c] = xk[c];
+        xs32[c] = (float)xs[c];
+    }
+    __syncthreads();
+    const double s = tl.is64(k, j) ? col_dot(tl.t64(k, j), b, c0 + tx, g, xs, xs32)
+                                   : col_dot(tl.t32(k, j), b, c0 + tx, g, xs, xs32);
+    red[g][tx] = s;
+    __syncthreads();
+    if (g == 0) vj[c0 + tx] -= ((red[0][tx] + red[1][tx]) + red[2][tx]) + red[3][tx];
 }
 
 // FP32 variant for the off-band tiles of the mixed-precision solves: the

@@ -195,79 +195,19 @@ __global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0,
     }
 }
 
-// Backward substitution on a diagonal tile: L_kk^T x = r in place, b threads
-// (thread i owns row i).  32-column blocks from the last: the owning warp
-// solves its 32 x 32 block with shuffles, then every thread with a smaller
-// row index subtracts the block's contribution (L read along its rows).
+// Backward substitution on diagonal tile k: L_kk^T x = r in place (b threads).
 __global__ void __launch_bounds__(1024) k_trsv_diag_T(Tiles tl, int k, double *__restrict__ v, const DevStatus *st)
 {
     if (mfailed(st)) return;
-    __shared__ double xv[1024];
-    __shared__ double D[32][33];
-    const int i = threadIdx.x, b = tl.b, lane = i & 31, w = i >> 5;
-    const double *L = tl.t64(k, k);
-    double r = v[(size_t)k * b + i];
-    for (int cb = b / 32 - 1; cb >= 0; --cb) {
-        const int c0 = cb * 32;
-        for (int e = i; e < 32 * 32; e += b) D[e >> 5][e & 31] = L[(size_t)(c0 + (e >> 5)) * b + c0 + (e & 31)];
-        __syncthreads();
-        if (w == cb) {
-            for (int jj = 31; jj >= 0; --jj) {
-                const double xj = __shfl_sync(0xffffffffu, r, jj) / D[jj][jj];
-                if (lane == jj) xv[c0 + jj] = xj;
-                if (lane < jj) r = fma(-D[jj][lane], xj, r);
-            }
-        }
-        __syncthreads();
-        if (i < c0) {
-            double s = 0.0;
-#pragma unroll 8
-            for (int jj = 0; jj < 32; ++jj) s = fma(L[(size_t)(c0 + jj) * b + i], xv[c0 + jj], s);
-            r -= s;
-        }
-    }
-    __syncthreads();
-    v[(size_t)k * b + i] = xv[i];
-}
-
-__device__ __forceinline__ double col_dot(const double *__restrict__ A, int b, int c, int g, const double *xs,
-                                          const float *)
-{
-    double s = 0.0;
-    for (int r = g; r < b; r += 4) s = fma(A[(size_t)r * b + c], xs[r], s);
-    return s;
-}
-
-// Off-band (FP32) tiles: products and the partial sum in FP32 (the tile is
-// only FP32 accurate; the refinement recovers the quadratic form in FP64).
-__device__ __forceinline__ double col_dot(const float *__restrict__ A, int b, int c, int g, const double *,
-                                          const float *xs32)
-{
-    float s = 0.0f;
-    for (int r = g; r < b; r += 4) s = fmaf(A[(size_t)r * b + c], xs32[r], s);
-    return (double)s;
+    trsv_bwd_tile(tl.t64(k, k), tl.b, v + (size_t)k * tl.b);
 }
 
 // r_j -= L_kj^T x_k for j < k (x_k read from xsrc, which may equal v).
-// grid = (k, b/64); 64 columns x 4 row groups, reduced in a fixed order.
+// grid = (k, b/64).
 __global__ void __launch_bounds__(256) k_gemv_T(Tiles tl, int k, const double *xsrc, double *v, const DevStatus *st)
 {
     if (mfailed(st)) return;
-    __shared__ double xs[1024];
-    __shared__ float xs32[1024];
-    __shared__ double red[4][64];
-    const int b = tl.b, j = (int)blockIdx.x, c0 = (int)blockIdx.y * 64;
-    const int tx = threadIdx.x & 63, g = threadIdx.x >> 6;
-    for (int c = threadIdx.x; c < b; c += 256) {
-        xs[c] = xsrc[(size_t)k * b + c];
-        xs32[c] = (float)xs[c];
-    }
-    __syncthreads();
-    const double s = tl.is64(k, j) ? col_dot(tl.t64(k, j), b, c0 + tx, g, xs, xs32)
-                                   : col_dot(tl.t32(k, j), b, c0 + tx, g, xs, xs32);
-    red[g][tx] = s;
-    __syncthreads();
-    if (g == 0) v[(size_t)j * b + c0 + tx] -= ((red[0][tx] + red[1][tx]) + red[2][tx]) + red[3][tx];
+    gemv_T_cols(tl, k, (int)blockIdx.x, (int)blockIdx.y * 64, xsrc + (size_t)k * tl.b, v + (size_t)blockIdx.x * tl.b);
 }
 
 // V_k = L_kk^-T for every diagonal tile k = blockIdx.x: 16 rows of V_k per

@@ -26,7 +26,13 @@ namespace {
 // peak one stage is consumed in ~0.33 us); each epilogue warp then has one
 // 4 KB staging box for its TMA reduces.
 constexpr int BM = 128, BN = 256, STAGES = 4;
-constexpr int kReserveSms = 24;  // SMs the bulk update leaves to the lookahead chain
+// SMs the bulk update leaves to the lookahead chain (POTRF / TRSM / band
+// update of the next step on the side stream).  While the bulk update is
+// several times longer than that chain (many work items), 8 SMs keep the
+// chain off the critical path and the tensor cores get the rest.
+constexpr int kReserveSms = 24;
+constexpr int kReserveSmsLong = 8;
+constexpr int64_t kLongBulkItems = 72000;
 constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_WARPS = 8;
 constexpr int STAGE_C = 32 * 32 * 4;  // one 32 x 32 FP32 box staged for the TMA reduce
@@ -471,7 +477,7 @@ cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, c
     const int kchunks = fmt == 3 ? 3 * tl.b / 32 : tl.b / (fmt == 2 ? 32 : 64);
     cudaError_t e;
     if (kt) kt->begin(KC_UPDATE, s);
-    const int reserve = (part == 2) ? kReserveSms : 0;
+    const int reserve = (part != 2) ? 0 : (blocks >= kLongBulkItems ? kReserveSmsLong : kReserveSms);
     if (fmt >= 2) e = launch_gemm<2>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
     else e = launch_gemm<1>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
     if (kt) kt->end(KC_UPDATE, s);

@@ -72,3 +72,28 @@ def test_batched_not_pd_is_isolated(egs):
     assert np.isnan(out[1])
     ref = oracle.loglik(locs[0], z[0], thetas[0])["loglik"]
     assert abs(out[0] - ref) <= 1e-10 * abs(ref)
+
+
+def test_batched_fp32_mode_matches_oracle(egs):
+    """FP32-off-band batch (FP64 band of 2 tiles, FP32 off-band tiles and
+    updates, FP64 band updates, one FP64 refinement step) on the same uneven
+    problems: every l within the FP32-mode bar 1e-6 of the oracle; problems of
+    at most 2 tiles are all-FP64; a replay of the graph is bitwise equal."""
+    from gpu_util import locs_dev, dev
+    probs = _problems()
+    B = egs.egs_batch([p[0] for p in probs], tile=128, precision="fp32")
+    dl = [locs_dev(p[2]) for p in probs]
+    dz = [dev(p[3]) for p in probs]
+    thetas = np.array([p[1] for p in probs])
+    out, stat = B.run(dl, dz, thetas)
+    assert np.all(stat == 0), stat
+    worst = 0.0
+    for i, (n, th, locs, z) in enumerate(probs):
+        ref = oracle.loglik(locs, z, th)["loglik"]
+        rel = abs(out[i] - ref) / max(1.0, abs(ref))
+        worst = max(worst, rel)
+        assert rel <= 1e-6, (i, n, rel)
+    print("fp32 batch worst rel l %.2e" % worst)
+    out2, _ = B.run(dl, dz, thetas)
+    assert np.array_equal(out, out2)
+    B.close()

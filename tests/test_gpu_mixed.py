@@ -122,7 +122,10 @@ def test_mixed_never_returns_a_gross_error(egs, prec, theta):
     """Smooth or long-range fields push Sigma's condition number towards
     1/eps of the off-band precision.  The mixed path must then either fail
     cleanly (EGS_ERR_NOT_PD, or EGS_ERR_INACCURATE when the FP64 refinement
-    step does not contract) or return a value close to the oracle's."""
+    step is too large) or return a value close to the oracle's: within 5e-5
+    in the FP32 mode (its guard passes only refinement steps below 1e-5,
+    measured to keep l within ~2.5e-5), within 1e-3 in TF32 (gross errors
+    only)."""
     from gpu_util import locs_dev, dev
     n = 3000
     locs, z, ref = _case(n, theta, 4)
@@ -133,4 +136,4 @@ def test_mixed_never_returns_a_gross_error(egs, prec, theta):
         return
     rel = abs(ll - ref["loglik"]) / abs(ref["loglik"])
     print("%s theta=%s: rel l %.2e" % (prec, theta, rel))
-    assert rel <= 1e-3, rel
+    assert rel <= (5e-5 if prec == "fp32" else 1e-3), rel
