@@ -35,6 +35,8 @@ if ROOT not in sys.path:
 
 METRIC = "loglik evals/s & POTRF TFLOP/s at n=102400 FP64 vs mixed; serve p50/p99 ms"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x flop/FMA x max clock
+# k_tc_gemm, split TF32: 7.79 GB of DRAM traffic for 1.425e12 flop in one launch (ncu)
+SPLIT_TF32_DRAM_BYTES_PER_FLOP = 7.79e9 / 1.425e12
 
 
 def parse():
@@ -324,7 +326,7 @@ def run_serve(a, egs):
     fields = ei.serving_fields(64)
     rng = np.random.default_rng(0)
     mixed = a.precision if a.precision != "fp64" else "fp32"
-    srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=a.band)
+    srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=a.band, fallback_fp64=True)
     fids = [srv.add_field(np.ascontiguousarray(f.locations().reshape(-1)), f.e(), f.n) for f in fields]
 
     def request(i):
@@ -345,7 +347,7 @@ def run_serve(a, egs):
     srv.close()
     results = {}
     for rho in (0.5, 0.8, 0.95):
-        srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=a.band)
+        srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=a.band, fallback_fp64=True)
         fids = [srv.add_field(np.ascontiguousarray(f.locations().reshape(-1)), f.e(), f.n) for f in fields]
         rate = rho * cap
         gaps = rng.exponential(1.0 / rate, a.requests)
@@ -367,13 +369,15 @@ def run_serve(a, egs):
         results[str(rho)] = {"rate_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
                              "mean_ms": st["mean_ms"], "evals_per_s": st["evals_per_s"],
                              "completed": st["completed"], "failed_not_pd_or_inaccurate": st["failed"],
-                             "inflight_peak": st["inflight_peak"], "bytes_peak": st["bytes_peak"]}
+                             "inflight_peak": st["inflight_peak"], "bytes_peak": st["bytes_peak"],
+                             "mixed_rerun_in_fp64": st["fallbacks"]}
         srv.close()
     line = {"metric": "serve p50/p99 ms and evals/s (config 5)", "value": results["0.8"]["p50_ms"],
             "unit": "ms (p50 at 0.8 of capacity)", "n_gpus": 1, "higher_is_better": False, "dtype": "f64/f64+" + mixed,
             "data": "synthetic (z ~ N(0, I))",
             "config": {"workload": "64 fields, n log-uniform [1000, 40000], nu ~ U(0.3, 2), Poisson arrivals, "
-                                   "50/50 FP64 and %s (band %d), 150 GB budget, 8 slots" % (mixed, a.band),
+                                   "50/50 FP64 and %s (band %d; a mixed request the accuracy guard rejects is "
+                                   "re-run in FP64 by the server), 150 GB budget, 8 slots" % (mixed, a.band),
                        "capacity_per_s": cap},
             "rates": results}
     print(json.dumps(line), flush=True)
@@ -499,9 +503,15 @@ def main():
                 products = 3
             achieved = products * tc_flops / (upd_ms / 1e3) / 1e12
             peak = tensor_peak(a.precision)
+            # DRAM bytes per executed flop of the split-TF32 update from an ncu
+            # capture at n = 32,768 (profiles/k_tc_gemm_splittf32_n32768_tile512.md),
+            # scaled to this launch size by its flops
+            traffic = SPLIT_TF32_DRAM_BYTES_PER_FLOP * products * tc_flops / (2 * launches_update) \
+                if a.precision == "fp32" else None
             roof = {"bound": "tensor", "kernel": "k_tc_gemm (tcgen05 trailing update, %s)" % a.precision,
                     "achieved": achieved, "peak": peak["tflops"], "unit": "TFLOP/s", "frac": achieved / peak["tflops"],
-                    "traffic": None, "peak_source": peak["source"], "launches_per_step": 2 * launches_update,
+                    "traffic": traffic, "traffic_unit": "bytes per launch (ncu capture at n=32768, scaled by flops)",
+                    "peak_source": peak["source"], "launches_per_step": 2 * launches_update,
                     "flops_per_launch": products * tc_flops / (2 * launches_update),
                     "ms_per_launch": upd_ms / (2 * launches_update),
                     "note": "executed TF32/BF16 MMA flops (%d product(s) per update) over the tcgen05 launches' "

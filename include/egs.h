@@ -328,13 +328,18 @@ typedef struct {
     int32_t max_inflight;
     int32_t tile;
     int32_t band;
-    int32_t pad;
+    int32_t fallback_fp64; /* nonzero: a mixed-precision request whose
+                              evaluation returns EGS_ERR_NOT_PD or
+                              EGS_ERR_INACCURATE is run again in EGS_FP64
+                              (ahead of the queue) and answered from that run;
+                              its latency covers both */
 } egs_serve_config;
 typedef struct {
     double p50_ms, p99_ms, mean_ms, evals_per_s;
     int64_t completed, failed, rejected, inflight_peak, queued;
     size_t bytes_in_use;  /* fields + workspaces in flight now */
     size_t bytes_peak;    /* maximum of bytes_in_use so far (<= the budget) */
+    int64_t fallbacks;    /* mixed requests re-run in FP64 (fallback_fp64) */
 } egs_serve_stats_t;
 egs_status egs_serve_create(const egs_serve_config *cfg, egs_server **out);
 egs_status egs_serve_add_field(egs_server *server, const double *locs, const double *z, int64_t n, int64_t *field_id);

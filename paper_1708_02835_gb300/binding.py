@@ -57,14 +57,14 @@ class egs_opts(ctypes.Structure):
 
 class egs_serve_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("band", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("band", ctypes.c_int32), ("fallback_fp64", ctypes.c_int32)]
 
 
 class egs_serve_stats(ctypes.Structure):
     _fields_ = [("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("evals_per_s", ctypes.c_double), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("rejected", ctypes.c_int64), ("inflight_peak", ctypes.c_int64), ("queued", ctypes.c_int64),
-                ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t)]
+                ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t), ("fallbacks", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -361,9 +361,10 @@ def egs_loglik_batched(locs, z, thetas, ns, precision="fp64", stream=None):
 class egs_server:
     """Serving loop (C ABI egs_serve_*): resident fields, budgeted admission."""
 
-    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 4, tile: int = 0, band: int = 0):
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 4, tile: int = 0, band: int = 0,
+                 fallback_fp64: bool = False):
         cfg = egs_serve_config(hbm_budget_bytes=int(hbm_budget_bytes), max_inflight=int(max_inflight),
-                               tile=int(tile), band=int(band), pad=0)
+                               tile=int(tile), band=int(band), fallback_fp64=int(bool(fallback_fp64)))
         h = ctypes.c_void_p()
         _check(load_library().egs_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

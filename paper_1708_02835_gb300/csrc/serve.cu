@@ -78,7 +78,7 @@ struct egs_server {
     int device = 0;
     // statistics
     std::vector<double> lat_ms;
-    int64_t completed = 0, failed = 0, rejected = 0;
+    int64_t completed = 0, failed = 0, rejected = 0, fallbacks = 0;
     int inflight = 0, inflight_peak = 0;
     clk::time_point first_submit{}, last_done{};
     bool any_submit = false;
@@ -86,9 +86,30 @@ struct egs_server {
 
 namespace {
 
+void release_slot(egs_server *S, Slot &sl)
+{
+    cudaFreeAsync(sl.ws, sl.stream);
+    sl.ws = nullptr;
+    S->used -= sl.es.need;
+    sl.busy = false;
+    --S->inflight;
+}
+
 void finish_slot(egs_server *S, Slot &sl)
 {
     // called with S->mu held
+    if (S->cfg.fallback_fp64 && sl.req.p != EGS_FP64 && !*sl.h_err) {
+        const egs::DevStatus &h = *sl.h_status;
+        if (h.fail_index != egs::kNoFail || !egs::mixed_result_ok(sl.es, h)) {
+            // the mixed factor failed or was too inexact: answer from FP64
+            Request again = sl.req;
+            again.p = EGS_FP64;
+            ++S->fallbacks;
+            release_slot(S, sl);
+            S->queue.push_front(again);
+            return;
+        }
+    }
     Result &r = S->results[sl.req.ticket];
     r.done = true;
     const egs::DevStatus &h = *sl.h_status;
@@ -112,11 +133,7 @@ void finish_slot(egs_server *S, Slot &sl)
     S->last_done = now;
     if (r.status == EGS_OK) ++S->completed;
     else ++S->failed;
-    cudaFreeAsync(sl.ws, sl.stream);
-    sl.ws = nullptr;
-    S->used -= sl.es.need;
-    sl.busy = false;
-    --S->inflight;
+    release_slot(S, sl);
 }
 
 bool admit_one(egs_server *S, std::unique_lock<std::mutex> &lk)
@@ -336,6 +353,7 @@ egs_status egs_serve_stats(egs_server *S, egs_serve_stats_t *st)
     st->queued = (int64_t)S->queue.size();
     st->bytes_in_use = S->used;
     st->bytes_peak = S->used_peak;
+    st->fallbacks = S->fallbacks;
     const double span = S->any_submit ? std::chrono::duration<double>(S->last_done - S->first_submit).count() : 0.0;
     st->evals_per_s = span > 0 ? (double)(S->completed + S->failed) / span : 0.0;
     return EGS_OK;

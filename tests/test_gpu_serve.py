@@ -113,3 +113,28 @@ def test_bad_requests(egs):
         srv.submit(7, (1.0, 0.1, 0.5), "fp64")
     assert e.value.status == egs.EGS_ERR_ARG
     srv.close()
+
+
+def test_fallback_answers_rejected_mixed_requests_in_fp64(egs):
+    """A smooth, long-range field (nu = 1.3, theta2 = 0.15) that the TF32 mode
+    cannot factor: with fallback_fp64 the server re-runs the request in FP64
+    and answers with exactly the FP64 value; without it the request fails."""
+    import torch
+    from gpu_util import locs_dev, dev
+    n, theta = 3000, (1.0, 0.15, 1.3)
+    locs = ei.jittered_grid(n, seed=77)
+    z = ei.normal(77, n)
+    want, _ = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "fp64", tile=TILE)
+    for fallback in (True, False):
+        srv = egs.egs_server(8 << 30, max_inflight=2, tile=TILE, band=2, fallback_fp64=fallback)
+        fid = srv.add_field(np.ascontiguousarray(locs.reshape(-1)), z, n)
+        t = srv.submit(fid, theta, "tf32")
+        if fallback:
+            got, _ = srv.wait(t)
+            assert got == want
+            assert srv.stats()["fallbacks"] == 1
+        else:
+            with pytest.raises(egs.EgsError):
+                srv.wait(t)
+            assert srv.stats()["fallbacks"] == 0
+        srv.close()
