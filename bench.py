@@ -62,6 +62,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value: float, world: int, device: str) -> float:
+    """The largest per-rank value (the slowest replica's time); value itself
+    when there is one rank.  Uses the default process group."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, seconds_max: float) -> float:
+    """Units processed by all replicas over the slowest replica's time."""
+    return world * units_per_rank / seconds_max
+
+
 def workload_name(a) -> str:
     m = int(round(math.sqrt(a.n)))
     grid = "%dx%d jittered grid" % (m, m) if m * m == a.n else "jittered grid"
@@ -448,11 +465,8 @@ def main():
     # per-kernel-class breakdown and the roofline's kernel time
     _, info2 = step(2)
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * a.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = whole_job_rate(a.steps, world, ms_max / 1e3)
 
     # end-to-end leg: pinned host inputs through the public C ABI call
     e2e_steps = a.steps if a.e2e_steps < 0 else a.e2e_steps
@@ -465,11 +479,8 @@ def main():
         for _ in range(e2e_steps):
             egs.egs_loglik_ex(hl, hz, theta, n, a.precision, tile=tile, band=a.band, workspace=ws, stream=stream)
         barrier()
-        te = time.perf_counter() - t0
-        tt = torch.tensor([te], device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * e2e_steps / float(tt.item()), "unit": "evals/s",
+        te = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+        e2e = {"value": whole_job_rate(e2e_steps, world, te), "unit": "evals/s",
                "h2d_bytes_per_step": int(hl.numel() * 8 + hz.numel() * 8), "d2h_bytes_per_step": 48,
                "steps": e2e_steps}
 

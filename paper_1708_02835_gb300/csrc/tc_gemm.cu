@@ -50,6 +50,13 @@ struct WorkItem {
 // (m, n) with m >= n >= col0 (one_col: only n = col0).  Panel tile m of
 // step k is operand row block m - k - 1.  skip_band: leave every band output
 // (m - n < band) to the FP64 kernels (split-TF32 mode).
+//
+// Tiles are visited by blocks of kColBlock columns: for each block, its
+// triangle (rows inside the block) then every lower row, kColBlock tiles per
+// row.  The persistent CTAs, which work on consecutive items together, then
+// share one block's B operand tiles (a few tens of MB, resident in L2) while
+// the A rows stream past, instead of needing every B tile of a row at once.
+constexpr int kColBlock = 8;
 struct UpdateWork {
     Tiles tl;
     int k;
@@ -59,20 +66,38 @@ struct UpdateWork {
     __device__ bool decode(int64_t bid, WorkItem &w) const
     {
         const int nrb = tl.b / BM, ncb = tl.b / BN, per = nrb * ncb;
-        const int64_t t = bid / per;
+        int64_t t = bid / per;
         const int blk = (int)(bid % per);
-        int ii, jj;
         if (one_col) {
-            ii = (int)t;
-            jj = 0;
+            w.m = col0 + (int)t;
+            w.n = col0;
         } else {
-            ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-            while ((int64_t)ii * (ii + 1) / 2 > t) --ii;
-            while ((int64_t)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
-            jj = (int)(t - (int64_t)ii * (ii + 1) / 2);
+            // column block c_lo .. c_lo + wd - 1: wd (wd + 1) / 2 triangle tiles,
+            // then (T - c_lo - wd) rows of wd tiles
+            int c_lo = col0;
+            while (true) {
+                const int wd = min(kColBlock, tl.T - c_lo);
+                if (wd <= 0) return false;  // past the last tile (not reached for valid items)
+                const int64_t tri = (int64_t)wd * (wd + 1) / 2;
+                const int64_t cnt = tri + (int64_t)(tl.T - c_lo - wd) * wd;
+                if (t < cnt) {
+                    if (t < tri) {
+                        int ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+                        while ((int64_t)ii * (ii + 1) / 2 > t) --ii;
+                        while ((int64_t)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
+                        w.m = c_lo + ii;
+                        w.n = c_lo + (int)(t - (int64_t)ii * (ii + 1) / 2);
+                    } else {
+                        const int64_t u = t - tri;
+                        w.m = c_lo + wd + (int)(u / wd);
+                        w.n = c_lo + (int)(u % wd);
+                    }
+                    break;
+                }
+                t -= cnt;
+                c_lo += wd;
+            }
         }
-        w.m = col0 + ii;
-        w.n = col0 + jj;
         w.rb = blk / ncb;
         w.cb = blk % ncb;
         if (w.m - k < tl.band && w.n - k < tl.band) return false;         // FP64 band x band: done in FP64
