@@ -9,9 +9,10 @@ log-determinant and the refined quadratic form):
   factor carries ~4e-3 relative rounding per entry).
 Single-precision off-band tiles cannot factor very smooth, long-range fields
 (condition numbers beyond 1/eps_FP32); there the mixed path must report
-EGS_ERR_NOT_PD cleanly rather than return a wrong number.
-With TF32 the refined quadratic form must be closer to the oracle's than the
-unrefined one (with BF16 one refinement step need not contract).
+EGS_ERR_NOT_PD or EGS_ERR_INACCURATE cleanly rather than return a wrong number.
+In the FP32 and TF32 modes the refined quadratic form must be closer to the
+oracle's than the unrefined one (with BF16 one refinement step need not
+contract).
 """
 import numpy as np
 import pytest
