@@ -112,9 +112,11 @@ __global__ void __launch_bounds__(256) k_l32_from_f64(Tiles tl, int k, float *__
 // (L_kk rounded to FP32, l32), 64 rows per CTA, 32-column blocks; the result
 // overwrites A_mk and is written to the panel buffer.  The GEMM-style part
 // keeps 4 rows x 2 columns per thread with the operands transposed in shared
-// memory (one 16-byte and one 8-byte shared load per 8 FMAs).
+// memory (one 16-byte and one 8-byte shared load per 8 FMAs).  The kernel is
+// latency bound; 80 registers let three CTAs share an SM (802 -> 687 us per
+// launch at n = 32,768; four CTAs need 64 registers and spill).
 template <int FMT>
-__global__ void __launch_bounds__(256) k_trsm_panel_f32(Tiles tl, int k, int m0, const float *__restrict__ L,
+__global__ void __launch_bounds__(256, 3) k_trsm_panel_f32(Tiles tl, int k, int m0, const float *__restrict__ L,
                                                         void *panel, __nv_bfloat16 *oz, double *ozs, const DevStatus *st)
 {
     if (mfailed(st)) return;
