@@ -217,13 +217,15 @@ struct DenseWork {
     }
 };
 
-// Persistent kernel: one CTA per SM loops over the work items
-// blockIdx.x, blockIdx.x + gridDim.x, ...  Warp 0 (one lane) streams the
-// operands of every item through the 4-stage ring; warp 1 (one lane) issues
+// Persistent kernel: one CTA per SM.  Warp 0 (one lane) claims work items
+// from a global counter (atomicAdd; zeroed before each launch at err + 2),
+// posts each item to the other warps through a 4-slot ring in shared memory
+// (-1 ends), and streams its operands through the 4-stage ring; warp 1 (one lane) issues
 // the MMAs of item t into TMEM accumulator t % 2 (two 256-column buffers);
 // warps 2-9 drain accumulator t % 2 while the MMAs of item t + 1 run.
 // FMT: 2 = TF32 (K-slice 8 per MMA), 1 = BF16 (K-slice 16 per MMA).
 constexpr int NUM_THREADS = 320;  // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int RING = 4;           // work items fetched ahead by the producer
 constexpr uint32_t TMEM_COLS2 = 2 * TMEM_COLS;
 
 template <int FMT, class Work>
@@ -234,6 +236,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
+    __shared__ uint64_t rfull[RING], rempty[RING];
+    __shared__ int64_t ring[RING];  // work items in the order the producer fetched them; -1 ends
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ int last_chunk[STAGES];
@@ -249,9 +253,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             tc::mbar_init(&tfull[b], 1);
             tc::mbar_init(&tempty[b], 8);
         }
+        for (int r = 0; r < RING; ++r) {
+            tc::mbar_init(&rfull[r], 1);
+            tc::mbar_init(&rempty[r], 1 + 8);  // the MMA lane and the eight epilogue warps
+        }
         abort_flag = 0;
         tc::fence_mbar_init();
     }
+    unsigned long long *next = reinterpret_cast<unsigned long long *>(err + 2);
     if (warp == 0) tc::tmem_alloc(&tmem_base, TMEM_COLS2);
     tc::tc_fence_before();
     __syncthreads();
@@ -263,10 +272,20 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         if (lane == 0) {
             tc::prefetch_tmap(&mapA);
             tc::prefetch_tmap(&mapB);
-            int g = 0;
-            for (int64_t item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
+            int g = 0, r = 0;
+            while (!abort_flag) {
+                // dynamic schedule: the next unclaimed item (CTAs that start
+                // late, behind kernels of the other stream, simply take fewer)
+                const int64_t item = (int64_t)atomicAdd(next, 1ull);
                 WorkItem wi;
-                if (!work.decode(item, wi)) continue;
+                const bool valid = item < nitems && work.decode(item, wi);
+                if (item < nitems && !valid) continue;
+                const int slot = r % RING;
+                if (!tc::mbar_wait(&rempty[slot], ((uint32_t)(r / RING) & 1u) ^ 1u, &abort_flag)) break;
+                ring[slot] = valid ? item : -1;
+                tc::mbar_arrive(&rfull[slot]);
+                ++r;
+                if (!valid) break;
                 for (int c = 0; c < kchunks; ++c, ++g) {
                     const int s = g % STAGES;
                     const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
@@ -281,10 +300,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_f32acc(BM, BN, FMT);
-            int g = 0, t = 0;
-            for (int64_t item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
-                WorkItem wi;
-                if (!work.decode(item, wi)) continue;
+            int g = 0, t = 0, r = 0;
+            while (!abort_flag) {
+                const int slot = r % RING;
+                if (!tc::mbar_wait(&rfull[slot], (uint32_t)(r / RING) & 1u, &abort_flag)) break;
+                const int64_t item = ring[slot];
+                tc::mbar_arrive(&rempty[slot]);
+                ++r;
+                if (item < 0) break;
                 const int buf = t & 1;
                 const uint32_t use = (uint32_t)(t >> 1);
                 if (!tc::mbar_wait(&tempty[buf], (use & 1u) ^ 1u, &abort_flag)) break;
@@ -320,10 +343,18 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const int half = (warp - 2) >> 2;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         uint8_t *stage = smem + STAGES * STAGE_BYTES + (warp - 2) * STAGE_C;
-        int t = 0, issued = 0;
-        for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        int t = 0, issued = 0, r = 0;
+        while (true) {
+            const int slot = r % RING;
+            const bool got = tc::mbar_wait(&rfull[slot], (uint32_t)(r / RING) & 1u, &abort_flag);
+            if (!__all_sync(0xffffffffu, got && !abort_flag)) break;
+            const int64_t item = ring[slot];
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&rempty[slot]);
+            ++r;
+            if (item < 0) break;
             WorkItem wi;
-            if (!work.decode(item, wi)) continue;
+            work.decode(item, wi);
             const int buf = t & 1;
             const uint32_t use = (uint32_t)(t >> 1);
             const bool ok = tc::mbar_wait(&tfull[buf], use & 1u, &abort_flag);
@@ -435,6 +466,9 @@ cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const CUte
     if (e != cudaSuccess) return e;
     const int64_t ctas = num_sms() - reserve > 1 ? num_sms() - reserve : 1;
     const int64_t grid = items < ctas ? items : ctas;
+    // err[0] is the error flag; the 8 bytes at err + 2 hold the work counter
+    e = cudaMemsetAsync(err + 2, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
     k_tc_gemm<FMT, Work><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, mc, w, items, kchunks, err);
     return cudaGetLastError();
 }
@@ -529,9 +563,9 @@ extern "C" egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, 
     if (e == cudaSuccess) e = make_map(&mb, B, fmt, (uint64_t)K, (uint64_t)N, BN);
     if (e != cudaSuccess) return set_error(EGS_ERR_CUDA, "egs_tc_gemm_test: tensor map encoding failed");
     int *err = nullptr;
-    e = cudaMallocAsync((void **)&err, sizeof(int), s);
+    e = cudaMallocAsync((void **)&err, 16, s);  // error flag + work counter
     if (e != cudaSuccess) return set_error(EGS_ERR_OOM, "egs_tc_gemm_test: workspace");
-    cudaMemsetAsync(err, 0, sizeof(int), s);
+    cudaMemsetAsync(err, 0, 16, s);
     DenseWork w{C, N, M / BM, N / BN};
     const int kchunks = K / (fmt == 2 ? 32 : 64);
     if (fmt == 2) e = launch_gemm<2>(ma, mb, ma, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s);
