@@ -137,7 +137,11 @@ const char *egs_version(void);
 int32_t egs_default_tile(int64_t n, egs_precision p);
 
 /* Bytes of the lower-tile matrix for (n, tile, p, band).  EGS_FP64: all
- * T (T + 1) / 2 tiles are double.  Returns 0 for invalid arguments. */
+ * T (T + 1) / 2 tiles are double.  Mixed precisions (band <= 0 means 2; when
+ * T <= band every tile is double): the band tiles (i - j < band) are double,
+ * stored band by band at position i * band + (i - j), and the other tiles are
+ * float at position (i - band)(i - band + 1) / 2 + j of a second array that
+ * follows; the total of both is returned.  Returns 0 for invalid arguments. */
 size_t egs_tiles_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band);
 
 /* Bytes of device workspace egs_loglik_ex needs for (n, tile, p, band),

@@ -267,10 +267,12 @@ int32_t egs_default_tile(int64_t n, egs_precision p) { return default_tile(n, p)
 
 size_t egs_tiles_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band)
 {
-    (void)band;
-    if (n < 1 || !tile_ok(tile) || p != EGS_FP64) return 0;
+    if (n < 1 || !tile_ok(tile) || (p != EGS_FP64 && !mixed_p(p))) return 0;
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
-    return g.ntiles() * g.tile_elems() * sizeof(double);
+    if (band <= 0) band = 2;
+    if (p == EGS_FP64 || g.T <= band) return g.ntiles() * g.tile_elems() * sizeof(double);
+    return Tiles::f64_tiles(g.T, band) * g.tile_elems() * sizeof(double) +
+           Tiles::f32_tiles(g.T, band) * g.tile_elems() * sizeof(float);
 }
 
 size_t egs_loglik_workspace_bytes(int64_t n, int32_t tile, egs_precision p, int32_t band)
