@@ -35,8 +35,8 @@ if ROOT not in sys.path:
 
 METRIC = "loglik evals/s & POTRF TFLOP/s at n=102400 FP64 vs mixed; serve p50/p99 ms"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x flop/FMA x max clock
-# k_tc_gemm, split TF32: 4.58 GB of DRAM traffic for 1.425e12 flop in one launch (ncu)
-SPLIT_TF32_DRAM_BYTES_PER_FLOP = 4.583e9 / 1.425e12
+# k_tc_gemm, split TF32: 5.30 GB of DRAM traffic for 1.425e12 flop in one launch (ncu)
+SPLIT_TF32_DRAM_BYTES_PER_FLOP = 5.297e9 / 1.425e12
 
 
 def parse():
