@@ -117,7 +117,8 @@ typedef struct {
     int32_t tile;          /* 0 = default */
     int32_t band;          /* FP64 band width in tiles for mixed modes; 0 = 2 */
     int32_t refine;        /* mixed modes: FP64 refinement steps (0 = default 1, -1 = none) */
-    int32_t timing;        /* nonzero: record per-phase CUDA events into egs_info */
+    int32_t timing;        /* nonzero: record per-phase CUDA events into egs_info;
+                              >= 3: also keep a per-launch trace (egs_trace_last) */
     void *workspace;       /* caller-owned device workspace, or NULL (library allocates) */
     size_t workspace_bytes;
     int32_t distance;      /* 0: Euclidean on (x, y); 1: great-circle distance on
@@ -126,6 +127,27 @@ typedef struct {
                               theta2 is in km */
     int32_t reserved;      /* 0 */
 } egs_opts;
+
+/* One kernel launch of a traced evaluation (egs_opts.timing >= 3). */
+typedef struct {
+    int32_t kclass;   /* 0 Sigma generation, 1 diagonal POTRF, 2 panel TRSM (and the
+                         operand preparation of the mixed modes), 3 trailing update
+                         (tensor-core in the mixed modes), 4 solve, 5 other
+                         (refinement, reductions), 6 FP64-accurate band update */
+    int32_t step;     /* factorisation step k of the launch, -1 outside the factorisation */
+    int32_t stream;   /* 0: the call's stream; 1: the library's lookahead stream */
+    int32_t reserved;
+    double start_ms;  /* CUDA-event times relative to the start of Sigma generation */
+    double end_ms;
+} egs_trace_rec;
+
+/* Copies the calling thread's trace of its last egs_loglik_ex call made with
+ * timing >= 3 into out[0 .. min(cap, *count) - 1], in enqueue order, and sets
+ * *count to the number of records (call with cap = 0 to size the buffer).
+ * Events bracket each launch on its stream, so a record includes any time the
+ * launch waited for SMs.  EGS_ERR_ARG if count is NULL or out is NULL with
+ * cap > 0.  Host-only; no GPU work. */
+egs_status egs_trace_last(egs_trace_rec *out, int64_t cap, int64_t *count);
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char *egs_last_error(void);

@@ -55,6 +55,14 @@ class egs_opts(ctypes.Structure):
                 ("distance", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class egs_trace_rec(ctypes.Structure):
+    _fields_ = [("kclass", ctypes.c_int32), ("step", ctypes.c_int32), ("stream", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double)]
+
+
+TRACE_CLASSES = ("generate", "potrf", "trsm", "update", "solve", "other", "update_f64")
+
+
 class egs_serve_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("band", ctypes.c_int32), ("fallback_fp64", ctypes.c_int32)]
@@ -116,6 +124,7 @@ def load_library(build_if_missing: bool = True):
         "egs_loglik_ind": (c.c_int, [vp, vp, pd, i64, i32, i32, pd, c.POINTER(egs_info), vp]),
         "egs_predict": (c.c_int, [vp, vp, i64, vp, i64, pd, c.c_int, c.POINTER(egs_opts), vp, c.POINTER(egs_info),
                                   vp]),
+        "egs_trace_last": (c.c_int, [c.POINTER(egs_trace_rec), i64, c.POINTER(i64)]),
         "egs_serve_create": (c.c_int, [c.POINTER(egs_serve_config), c.POINTER(vp)]),
         "egs_serve_add_field": (c.c_int, [vp, vp, vp, i64, c.POINTER(i64)]),
         "egs_serve_submit": (c.c_int, [vp, i64, pd, c.c_int, c.POINTER(i64)]),
@@ -176,6 +185,17 @@ def _prec(p) -> int:
 
 def egs_last_error() -> str:
     return load_library().egs_last_error().decode()
+
+
+def egs_trace_last() -> list:
+    """Per-launch trace of this thread's last egs_loglik_ex(timing=3) call:
+    a list of (class name, step, stream, start_ms, end_ms) in enqueue order."""
+    lib = load_library()
+    cnt = ctypes.c_int64(0)
+    _check(lib.egs_trace_last(None, 0, ctypes.byref(cnt)))
+    buf = (egs_trace_rec * max(cnt.value, 1))()
+    _check(lib.egs_trace_last(buf, cnt.value, ctypes.byref(cnt)))
+    return [(TRACE_CLASSES[r.kclass], r.step, r.stream, r.start_ms, r.end_ms) for r in buf[:cnt.value]]
 
 
 def egs_version() -> str:

@@ -94,6 +94,8 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
                     align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(double)));
     L.l32 = off;
     off += align256(bb * sizeof(float));
+    L.wsp = off;
+    if (mix_fmt(p) == 3) off += align256(3 * bb * sizeof(float));
     L.vinv = off;
     off += align256((size_t)g.T * bb * sizeof(double));
     L.locs = off;
@@ -201,6 +203,7 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
         mb.partials = (double *)(ws + ML.partials);
         mb.err = (int *)(ws + ML.err);
         mb.l32 = (float *)(ws + ML.l32);
+        mb.wsp = (float *)(ws + ML.wsp);
         mb.vinv = (double *)(ws + ML.vinv);
         const size_t ozb = align256(ozaki_slices_bytes(g.b, g.T));
         const size_t ozh = ozb + align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(double));
@@ -252,6 +255,22 @@ void fill_info(const EvalSetup &es, const DevStatus &h, egs_info *info)
     info->quad_unrefined = es.mixed ? h.result[3] : h.result[2];
 }
 
+
+static thread_local std::vector<egs_trace_rec> g_trace;
+
+void store_trace(const KernelTimer &kt, cudaEvent_t origin)
+{
+    g_trace.clear();
+    g_trace.reserve(kt.recs.size());
+    for (const KernelTimer::Rec &r : kt.recs) {
+        float t0 = 0.f, t1 = 0.f;
+        if (!r.e || cudaEventElapsedTime(&t0, origin, r.b) != cudaSuccess ||
+            cudaEventElapsedTime(&t1, origin, r.e) != cudaSuccess)
+            continue;
+        g_trace.push_back(egs_trace_rec{r.cls, r.step, r.side, 0, (double)t0, (double)t1});
+    }
+}
+
 }  // namespace egs
 
 
@@ -260,6 +279,16 @@ using namespace egs;
 extern "C" {
 
 const char *egs_last_error(void) { return g_err; }
+
+egs_status egs_trace_last(egs_trace_rec *out, int64_t cap, int64_t *count)
+{
+    if (!count) return set_error(EGS_ERR_ARG, "egs_trace_last: count is NULL");
+    if (cap < 0 || (cap > 0 && !out)) return set_error(EGS_ERR_ARG, "egs_trace_last: bad buffer");
+    *count = (int64_t)g_trace.size();
+    const int64_t m = cap < *count ? cap : *count;
+    for (int64_t i = 0; i < m; ++i) out[i] = g_trace[(size_t)i];
+    return EGS_OK;
+}
 
 const char *egs_version(void) { return "egs 0.1 (sm_103a)"; }
 
@@ -377,6 +406,7 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
     KernelTimer kt;
     kt.on = opts && opts->timing >= 2;
     cudaStream_t s = (cudaStream_t)stream;
+    kt.main = s;
 
     char *ws = nullptr;
     bool own = false;
@@ -413,6 +443,7 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
     if (timing) {
         if (e == cudaSuccess)
             for (int i = 0; i < 3; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+        if (e == cudaSuccess && opts->timing >= 3) store_trace(kt, ev[0]);
         for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
     }
     if (e != cudaSuccess) return cuda_error(e, "egs_loglik");

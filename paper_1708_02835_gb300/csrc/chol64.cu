@@ -158,6 +158,7 @@ cudaError_t launch_potrf_tiles_f64(double *tiles, const TileGeom &g, DevStatus *
     const int T = g.T;
     const Tiles tl{tiles, nullptr, g.b, T, T};
     for (int k = 0; k < T; ++k) {
+        if (kt) kt->step = k;
         cudaError_t e = launch_potrf_diag(tl, k, st, s, kt);
         if (e != cudaSuccess) return e;
         if (k + 1 < T) {
@@ -167,6 +168,7 @@ cudaError_t launch_potrf_tiles_f64(double *tiles, const TileGeom &g, DevStatus *
             if (e != cudaSuccess) return e;
         }
     }
+    if (kt) kt->step = -1;
     return cudaGetLastError();
 }
 

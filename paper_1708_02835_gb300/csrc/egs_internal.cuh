@@ -73,40 +73,51 @@ enum KernelClass { KC_GEN = 0, KC_POTRF, KC_TRSM, KC_UPDATE, KC_TRSV, KC_OTHER, 
 struct KernelTimer {
     bool on = false;
     int launches = 0;
-    std::vector<cudaEvent_t> ev[KC_COUNT];
+    int step = -1;                // factorisation step of the launches that follow (-1: none)
+    cudaStream_t main = nullptr;  // the call's stream; any other counts as the side stream
+    struct Rec {
+        int cls, step, side;
+        cudaEvent_t b, e;
+    };
+    std::vector<Rec> recs;  // one per launch, in enqueue order
     void begin(int cls, cudaStream_t s)
     {
         if (!on) return;
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        cudaEventRecord(e, s);
-        ev[cls].push_back(e);
+        Rec r{cls, step, s != main ? 1 : 0, nullptr, nullptr};
+        cudaEventCreate(&r.b);
+        cudaEventRecord(r.b, s);
+        recs.push_back(r);
     }
     void end(int cls, cudaStream_t s)
     {
+        (void)cls;
         ++launches;
-        if (!on) return;
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        cudaEventRecord(e, s);
-        ev[cls].push_back(e);
+        if (!on || recs.empty()) return;
+        cudaEventCreate(&recs.back().e);
+        cudaEventRecord(recs.back().e, s);
     }
     // Summed milliseconds of a class (call after the stream has finished).
     double ms(int cls) const
     {
         double t = 0.0;
-        for (size_t i = 0; i + 1 < ev[cls].size(); i += 2) {
+        for (const Rec &r : recs) {
             float x = 0.f;
-            if (cudaEventElapsedTime(&x, ev[cls][i], ev[cls][i + 1]) == cudaSuccess) t += x;
+            if (r.cls == cls && r.e && cudaEventElapsedTime(&x, r.b, r.e) == cudaSuccess) t += x;
         }
         return t;
     }
     ~KernelTimer()
     {
-        for (auto &v : ev)
-            for (auto e : v) cudaEventDestroy(e);
+        for (const Rec &r : recs) {
+            if (r.b) cudaEventDestroy(r.b);
+            if (r.e) cudaEventDestroy(r.e);
+        }
     }
 };
+
+// Per-launch trace of the calling thread's last egs_loglik_ex with
+// timing >= 3 (start and end relative to the start of Sigma generation).
+void store_trace(const KernelTimer &kt, cudaEvent_t origin);
 
 #define EGS_LAUNCH(kt, cls, s, ...)      \
     do {                                 \
@@ -149,7 +160,8 @@ struct MixedBuffers {
     double *zp, *y, *x, *d, *res, *rows, *cols;  // T*b vectors
     double *partials; // 2T
     int *err;
-    float *l32;       // b x b: L_kk rounded to FP32 for the off-band TRSM of step k
+    float *l32;       // b x b: L_kk rounded to FP32 for the off-band TRSM of step k (TF32 / BF16 modes)
+    float *wsp;       // FP32 mode: W = L_kk^-1 in split-TF32 B layout, b x 3b
     double *vinv;     // T b x b: V_k = L_kk^-T (upper triangular) for the solves
     void *oz[2];      // FP32 mode: BF16 slices of the panel rows (ozaki_slices_bytes), step k uses k % 2
     double *ozs[2];   // FP32 mode: their row scales, (T-1) b doubles each
@@ -166,7 +178,7 @@ struct Layout {
     size_t tiles, locs, z, zpad, partials, status, total;
 };
 struct MixedLayout {
-    size_t f64, f32, sig, panel, oz, l32, vinv, locs, z, vec, partials, status, err, total;
+    size_t f64, f32, sig, panel, oz, l32, wsp, vinv, locs, z, vec, partials, status, err, total;
 };
 struct EvalSetup {
     TileGeom g;
@@ -243,6 +255,13 @@ cudaError_t make_offband_map(const float *f32, int b, size_t ntiles, CUtensorMap
 // part 0: all trailing tiles of step k; 1: column k + 1; 2: columns k + 2 onwards.
 // fmt 3 updates only the off-band outputs (m - n >= band); the band outputs
 // are left to the FP64 kernels.
+// FP32 mode: the off-band panel TRSM of step k (tiles m0 .. T - 1) on the
+// tensor cores, X = A W^T with W = L_kk^-1 (mapW over its split-TF32 B
+// layout, make_trsm_w_map) and A in split-TF32 A layout behind mapA; X
+// overwrites the FP32 tiles.
+cudaError_t make_trsm_w_map(const float *wsp, int b, CUtensorMap *mapW);
+cudaError_t launch_trsm_tc(const CUtensorMap &mapA, const CUtensorMap &mapW, const CUtensorMap &mapC, const Tiles &tl,
+                           int k, int m0, int *err, cudaStream_t s, KernelTimer *kt);
 cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, const CUtensorMap &mapC, int fmt,
                              const Tiles &tl, int k, int *err, cudaStream_t s, KernelTimer *kt, int part = 0);
 

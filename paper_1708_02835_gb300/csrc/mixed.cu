@@ -82,6 +82,125 @@ __global__ void __launch_bounds__(256) k_panel_from_f64_split(Tiles tl, int k, v
     slice_row(x, b, oz + pr * b, (size_t)(tl.T - 1) * b * b, ozs + pr);
 }
 
+// FP32 mode: solved off-band panel rows (tiles m0 .. T - 1 of column k, FP32)
+// -> split-TF32 operands and the BF16 slices of the FP64-accurate band
+// updates; one warp per row.
+__global__ void __launch_bounds__(256) k_panel_from_f32_split(Tiles tl, int k, int m0, void *panel,
+                                                              __nv_bfloat16 *oz, double *ozs, const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    const int b = tl.b, lane = threadIdx.x & 31;
+    const size_t pr = (size_t)(m0 - k - 1) * b + (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // panel row
+    const int m = k + 1 + (int)(pr / b);
+    const float *x = tl.t32(m, k) + (pr % b) * b;
+    for (int c = lane; c < b; c += 32) panel_store<3>(panel, tl, pr, c, x[c]);
+    slice_row_f32(x, b, oz + pr * b, (size_t)(tl.T - 1) * b * b, ozs + pr);
+}
+
+// FP32 mode, tensor-core TRSM: the unsolved off-band tiles (m0 .. T - 1, k)
+// in the split-TF32 A layout [lo | hi | hi] at operand rows (m - k - 1) b + r
+// of pre (four consecutive elements per thread).
+__global__ void __launch_bounds__(256) k_presplit_a(Tiles tl, int k, int m0, float *__restrict__ pre,
+                                                    const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    const int b = tl.b;
+    const size_t bb = tl.bb(), total4 = (size_t)(tl.T - m0) * bb / 4, ld = 3 * (size_t)b;
+    for (size_t e4 = (size_t)blockIdx.x * 256 + threadIdx.x; e4 < total4; e4 += (size_t)gridDim.x * 256) {
+        const size_t e = 4 * e4;
+        const int m = m0 + (int)(e / bb);
+        const size_t off = e % bb;
+        const float4 v = *reinterpret_cast<const float4 *>(tl.t32(m, k) + off);
+        float4 hi, lo;
+        hi.x = to_tf32(v.x), lo.x = to_tf32(v.x - hi.x);
+        hi.y = to_tf32(v.y), lo.y = to_tf32(v.y - hi.y);
+        hi.z = to_tf32(v.z), lo.z = to_tf32(v.z - hi.z);
+        hi.w = to_tf32(v.w), lo.w = to_tf32(v.w - hi.w);
+        float *pa = pre + ((size_t)(m - k - 1) * b + off / b) * ld + off % b;
+        *reinterpret_cast<float4 *>(pa) = lo;
+        *reinterpret_cast<float4 *>(pa + b) = hi;
+        *reinterpret_cast<float4 *>(pa + 2 * b) = hi;
+    }
+}
+
+// W = L_kk^-1 column by column, in FP64: warp w of CTA c solves L w_j = e_j
+// for column j = c + gridDim.x w by column-oriented forward substitution:
+// with p = e_j, for i = j .. b-1: w_i = p_i / L_ii, then p_r -= L_ri w_i for
+// every r > i.  Lane l keeps p_r of the rows r = l + 32 t in registers, so a
+// step's critical chain is one shuffle (w_i from its owner lane), one
+// multiply and the owner's update of row i + 1; the other rows' updates
+// overlap it.  Each p_r receives its terms in the order of i, so results are
+// bitwise reproducible.  Outputs: V_k = W^T (row j of V_k is w_j, the
+// upper-triangular inverse the solves use) and W in the split-TF32 B layout
+// of the tensor-core TRSM (row c: [hi | lo | hi] of (float) W[c][.]).
+// NT = b / 32 rows per lane.  Shared memory: (1 + warps) b doubles.
+template <int NT>
+__global__ void __launch_bounds__(128) k_inv_cols(Tiles tl, int k, double *__restrict__ V, float *__restrict__ wsp,
+                                                  const DevStatus *st)
+{
+    if (mfailed(st)) return;
+    extern __shared__ double inv_sm[];
+    const int b = tl.b, lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const double *L = tl.t64(k, k);
+    double *rinv = inv_sm, *xs = inv_sm + (size_t)(1 + wq) * b;
+    for (int i = threadIdx.x; i < b; i += blockDim.x) rinv[i] = 1.0 / L[(size_t)i * b + i];
+    for (int i = lane; i < b; i += 32) xs[i] = 0.0;
+    __syncthreads();
+    const int j = (int)blockIdx.x + (int)gridDim.x * wq;
+    double p[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) p[t] = (lane + 32 * t == j) ? 1.0 : 0.0;
+#pragma unroll
+    for (int s = 0; s < NT; ++s) {
+        if (32 * s + 31 < j) continue;  // rows of this slot lie above j: w = 0 there
+        const int ii0 = j > 32 * s ? j - 32 * s : 0;
+        double lc[NT];  // L[r][i] of the current step for the slots t >= s
+#pragma unroll
+        for (int t = s; t < NT; ++t) lc[t] = L[(size_t)(lane + 32 * t) * b + 32 * s + ii0];
+        for (int ii = ii0; ii < 32; ++ii) {
+            const int i = 32 * s + ii;
+            double ln[NT];  // the next step's column, loaded ahead
+#pragma unroll
+            for (int t = s; t < NT; ++t) ln[t] = (i + 1 < b) ? L[(size_t)(lane + 32 * t) * b + i + 1] : 0.0;
+            const double wi = __shfl_sync(0xffffffffu, p[s], ii) * rinv[i];
+            if (lane == 0) xs[i] = wi;
+#pragma unroll
+            for (int t = s; t < NT; ++t)
+                if (lane + 32 * t > i) p[t] = fma(-lc[t], wi, p[t]);
+#pragma unroll
+            for (int t = s; t < NT; ++t) lc[t] = ln[t];
+        }
+    }
+    __syncwarp();
+    double *Vj = V + (size_t)k * tl.bb() + (size_t)j * b;
+    const size_t ld3 = 3 * (size_t)b;
+    for (int c = lane; c < b; c += 32) {
+        const double x = xs[c];
+        Vj[c] = x;
+        const float v = (float)x, hi = to_tf32(v), lo = to_tf32(v - hi);
+        float *pw = wsp + (size_t)c * ld3 + j;
+        pw[0] = hi;
+        pw[b] = lo;
+        pw[2 * b] = hi;
+    }
+}
+
+cudaError_t launch_inv_cols(const Tiles &tl, int k, double *V, float *wsp, const DevStatus *st, cudaStream_t s,
+                            KernelTimer *kt)
+{
+    const int b = tl.b;
+    const unsigned grid = (unsigned)(b / 4);
+    const size_t sm = (size_t)5 * b * sizeof(double);
+    switch (b / 32) {
+    case 8: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<8><<<grid, 128, sm, s>>>(tl, k, V, wsp, st)); break;
+    case 16: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<16><<<grid, 128, sm, s>>>(tl, k, V, wsp, st)); break;
+    case 24: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<24><<<grid, 128, sm, s>>>(tl, k, V, wsp, st)); break;
+    case 32: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<32><<<grid, 128, sm, s>>>(tl, k, V, wsp, st)); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // FP64 band panel tiles (m = k+1..k+nrows) -> operand format.
 template <int FMT>
 __global__ void __launch_bounds__(256) k_panel_from_f64(Tiles tl, int k, int nrows, void *panel, const DevStatus *st)
@@ -417,19 +536,26 @@ namespace {
 // FP32 mode the slices) alternate between two buffers.
 template <int FMT>
 cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CUtensorMap *mbm,
-                         const CUtensorMap &mc, const CUtensorMap (*moz)[2], DevStatus *st, cudaStream_t s,
-                         KernelTimer *kt)
+                         const CUtensorMap &mc, const CUtensorMap (*moz)[2], const CUtensorMap *mw, DevStatus *st,
+                         cudaStream_t s, KernelTimer *kt)
 {
     const Tiles &tl = mb.tl;
     const int T = tl.T, b = tl.b;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_panel = nullptr, ev_col = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+    // The chain gates the next step, so its kernels take the SMs that the
+    // main stream's kernels free first: the side stream runs at the highest
+    // priority (otherwise each step's POTRF waits for the whole slice-product
+    // launch ahead of it to drain).
+    int prio_least = 0, prio_greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_col, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);  // the side stream starts after prior work on s
     KernelTimer *kts = kt;  // side-stream kernels are timed with events on the side stream
     for (int k = 0; k < T && e == cudaSuccess; ++k) {
+        if (kt) kt->step = k;
         const int nb = (tl.band - 1 < T - k - 1) ? tl.band - 1 : T - k - 1;  // FP64 rows below k
         const int nf = T - k - 1 - nb;                                       // FP32 rows
         void *panel = mb.panel[k & 1];
@@ -441,7 +567,7 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         e = cudaStreamWaitEvent(side, ev_col, 0);
         if (e == cudaSuccess) e = launch_potrf_diag(tl, k, st, side, kts);
         if (e == cudaSuccess && k + 1 < T) {
-            if (nf > 0)
+            if (nf > 0 && FMT != 3)
                 EGS_LAUNCH(kts, KC_TRSM, side,
                            k_l32_from_f64<<<(unsigned)((tl.bb() + 255) / 256 < 1024 ? (tl.bb() + 255) / 256 : 1024), 256,
                                             0, side>>>(tl, k, mb.l32, st));
@@ -467,13 +593,33 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         if (e == cudaSuccess && k + 1 < T)
             e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, side, kts, KC_UPDATE64);
         if (k + 1 == T || e != cudaSuccess) break;
-        // ---- step k on the main stream: the FP32 TRSM (whole GPU), column
-        // k + 1, signal, then the rest
+        // ---- step k on the main stream: the off-band TRSM (whole GPU),
+        // column k + 1, signal, then the rest
         e = cudaStreamWaitEvent(s, ev_panel, 0);
-        if (e == cudaSuccess && nf > 0)
+        if (FMT == 3) {
+            // W = L_kk^-1 (and V_k = W^T for the solves), then X = A W^T on the
+            // tensor cores: the unsolved tiles are split into the spare panel
+            // buffer (free until the next step's chain, which starts after
+            // column k + 1 below), the product overwrites them, and the solved
+            // rows are split into this step's panel and slices
+            const int m0 = k + 1 + nb;
+            if (e == cudaSuccess) e = launch_inv_cols(tl, k, mb.vinv, mb.wsp, st, s, kt);
+            if (e == cudaSuccess && nf > 0) {
+                const size_t total4 = (size_t)nf * tl.bb() / 4;
+                const unsigned g4 = (unsigned)((total4 + 255) / 256 < 2048 ? (total4 + 255) / 256 : 2048);
+                EGS_LAUNCH(kt, KC_TRSM, s,
+                           k_presplit_a<<<g4, 256, 0, s>>>(tl, k, m0, (float *)mb.panel[(k + 1) & 1], st));
+                e = launch_trsm_tc(ma[(k + 1) & 1], *mw, mc, tl, k, m0, mb.err, s, kt);
+                if (e == cudaSuccess)
+                    EGS_LAUNCH(kt, KC_TRSM, s,
+                               k_panel_from_f32_split<<<(unsigned)((size_t)nf * b / 8), 256, 0, s>>>(tl, k, m0, panel,
+                                                                                                    oz, ozs, st));
+            }
+        } else if (e == cudaSuccess && nf > 0) {
             EGS_LAUNCH(kt, KC_TRSM, s,
                        k_trsm_panel_f32<FMT><<<dim3((unsigned)nf, (unsigned)(b / 64)), 256, 0, s>>>(
                            tl, k, k + 1 + nb, mb.l32, panel, oz, ozs, st));
+        }
         // FP32 mode: band outputs with an FP32 operand by exact slices
         if (e == cudaSuccess && FMT == 3)
             e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, k, k + 1, 1, ozs, mb.err, s, kt);
@@ -483,8 +629,11 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
             e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, k, k + 2, T - k - 2, ozs, mb.err, s, kt);
         if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, FMT, tl, k, mb.err, s, kt, 2);
     }
+    if (kt) kt->step = -1;
     if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_panel, 0);  // join the side stream
+    // FP32 mode: V_k of the last diagonal tile (the others came with their TRSM)
+    if (e == cudaSuccess && FMT == 3) e = launch_inv_cols(tl, T - 1, mb.vinv, mb.wsp, st, s, kt);
     // destroying a stream or event with work still pending is legal: the
     // resources are released once that work completes, and s already waits
     // for it through ev_panel
@@ -539,14 +688,19 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     if (e == cudaSuccess) e = make_offband_map(tl.f32, b, Tiles::f32_tiles(T, tl.band), &mc);
     for (int i = 0; i < 2 && e == cudaSuccess && fmt == 3; ++i) e = make_ozaki_maps(mb.oz[i], b, T, &moz[i][0], &moz[i][1]);
     if (e != cudaSuccess) return e;
-    if (fmt == 3) e = factor_mixed<3>(mb, ma, mbm, mc, moz, st, s, kt);
-    else if (fmt == 2) e = factor_mixed<2>(mb, ma, mbm, mc, moz, st, s, kt);
-    else e = factor_mixed<1>(mb, ma, mbm, mc, moz, st, s, kt);
+    CUtensorMap mw;
+    if (fmt == 3) e = make_trsm_w_map(mb.wsp, b, &mw);
+    if (e != cudaSuccess) return e;
+    if (fmt == 3) e = factor_mixed<3>(mb, ma, mbm, mc, moz, &mw, st, s, kt);
+    else if (fmt == 2) e = factor_mixed<2>(mb, ma, mbm, mc, moz, nullptr, st, s, kt);
+    else e = factor_mixed<1>(mb, ma, mbm, mc, moz, nullptr, st, s, kt);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);
-    // V_k = L_kk^-T for every diagonal tile and the log-det partials, then
-    // res = L^-1 z (kept for y.y), x = L^-T res
-    EGS_LAUNCH(kt, KC_TRSV, s, k_inv_diag<<<dim3((unsigned)T, (unsigned)(b / 16)), 256, 0, s>>>(tl, mb.vinv, st));
+    // V_k = L_kk^-T for every diagonal tile (FP32 mode: computed during the
+    // factorisation) and the log-det partials, then res = L^-1 z (kept for
+    // y.y), x = L^-T res
+    if (fmt != 3)
+        EGS_LAUNCH(kt, KC_TRSV, s, k_inv_diag<<<dim3((unsigned)T, (unsigned)(b / 16)), 256, 0, s>>>(tl, mb.vinv, st));
     EGS_LAUNCH(kt, KC_TRSV, s, k_logdet_tiles<<<(unsigned)T, 256, 0, s>>>(tl, mb.partials, st));
     e = launch_pad_vector(z, n, mb.zp, npad, s, kt);
     if (e != cudaSuccess) return e;

@@ -186,6 +186,45 @@ struct UpdateWork {
     }
 };
 
+// FP32 mode, off-band panel TRSM of step k as a product with the inverse
+// diagonal tile: X_mk = A_mk L_kk^-T = A_mk W^T, W = L_kk^-1, for the tiles
+// m = m0 .. T - 1.  A rows: the unsolved tiles in split-TF32 A layout at
+// operand row (m - k - 1) b (the spare panel buffer of the step); B rows: W
+// in split-TF32 B layout (b rows of K = 3b).  The accumulator is X itself,
+// stored over A_mk (each output block is written by exactly one item, and
+// the operands live in other buffers, so there is no read-after-write race).
+struct TrsmWork {
+    Tiles tl;
+    int k, m0;
+    static constexpr bool kReduce = false;
+    __device__ bool reduce_here(const WorkItem &) const { return false; }
+    __device__ int reduce_row(const WorkItem &, int) const { return 0; }
+    __device__ int reduce_col(const WorkItem &, int) const { return 0; }
+    __device__ bool decode(int64_t bid, WorkItem &w) const
+    {
+        const int ncb = tl.b / BN, per = (tl.b / BM) * ncb;
+        const int blk = (int)(bid % per);
+        w.m = m0 + (int)(bid / per);
+        w.n = k;
+        w.rb = blk / ncb;
+        w.cb = blk % ncb;
+        w.ya = (w.m - k - 1) * tl.b + w.rb * BM;
+        w.yb = w.cb * BN;
+        return true;
+    }
+    __device__ void store2(const WorkItem &w, int r, int c0, const float (&v0)[32], const float (&v1)[32]) const
+    {
+        float *X = tl.t32(w.m, k) + (size_t)(w.rb * BM + r) * tl.b + w.cb * BN + c0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            *reinterpret_cast<float4 *>(X + 4 * i) = make_float4(v0[4 * i], v0[4 * i + 1], v0[4 * i + 2], v0[4 * i + 3]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            *reinterpret_cast<float4 *>(X + 32 + 4 * i) =
+                make_float4(v1[4 * i], v1[4 * i + 1], v1[4 * i + 2], v1[4 * i + 3]);
+    }
+};
+
 // Plain C = A B^T (A: M x K, B: N x K, row-major), used to test the pipeline.
 struct DenseWork {
     float *C;
@@ -514,6 +553,26 @@ cudaError_t make_panel_maps(const void *panel, int fmt, int b, int T, CUtensorMa
     }
     cudaError_t e = make_map(mapA, panel, fmt, (uint64_t)b, rows, BM);
     if (e == cudaSuccess) e = make_map(mapB, panel, fmt, (uint64_t)b, rows, BN);
+    return e;
+}
+
+// Map over W = L_kk^-1 in split-TF32 B layout (b rows of 3b floats).
+cudaError_t make_trsm_w_map(const float *wsp, int b, CUtensorMap *mapW)
+{
+    return make_map(mapW, wsp, 3, 3 * (uint64_t)b, (uint64_t)b, BN);
+}
+
+cudaError_t launch_trsm_tc(const CUtensorMap &mapA, const CUtensorMap &mapW, const CUtensorMap &mapC, const Tiles &tl,
+                           int k, int m0, int *err, cudaStream_t s, KernelTimer *kt)
+{
+    const int64_t nf = tl.T - m0;
+    if (nf <= 0) return cudaSuccess;
+    const int64_t items = nf * (tl.b / BM) * (tl.b / BN);
+    TrsmWork w{tl, k, m0};
+    if (kt) kt->begin(KC_TRSM, s);
+    // a few SMs stay free for the FP64 band update of the step on the side stream
+    cudaError_t e = launch_gemm<2>(mapA, mapW, mapC, w, items, 3 * tl.b / 32, err, s, kReserveSmsLong);
+    if (kt) kt->end(KC_TRSM, s);
     return e;
 }
 

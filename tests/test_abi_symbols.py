@@ -61,3 +61,13 @@ def test_host_only_queries(lib):
 def test_built_for_sm103a_only():
     from paper_1708_02835_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_trace_is_empty_before_any_traced_call(lib):
+    import paper_1708_02835_gb300 as egs
+    assert egs.egs_trace_last() == []
+    handle, _ = lib
+    handle.egs_trace_last.restype = ctypes.c_int
+    assert handle.egs_trace_last(None, ctypes.c_int64(0), None) == 1        # EGS_ERR_ARG: count is NULL
+    cnt = ctypes.c_int64(-1)
+    assert handle.egs_trace_last(None, ctypes.c_int64(4), ctypes.byref(cnt)) == 1   # NULL out with cap > 0
