@@ -59,7 +59,28 @@ def parse():
     ap.add_argument("--evals", type=int, default=50, help="config2-mle: likelihood evaluations")
     ap.add_argument("--requests", type=int, default=48, help="config5-serve: requests per arrival rate")
     ap.add_argument("--cpu-sample-n", type=int, default=8192)
+    ap.add_argument("--trace", default="", help="config3: write the per-launch trace of the untimed breakdown step "
+                                                 "to this CSV file")
     return ap.parse_args()
+
+
+def timeline_summary(trace) -> dict:
+    """Per-stream busy time by kernel class over the factorisation, and how
+    long the main stream stood idle (waiting for the lookahead chain), from
+    egs_trace_last() records (class, step, stream, start_ms, end_ms)."""
+    fac = [r for r in trace if r[1] >= 0]
+    if not fac:
+        return {}
+    busy = {"main": {}, "side": {}}
+    for cls, _, st, t0, t1 in fac:
+        d = busy["main" if st == 0 else "side"]
+        d[cls] = d.get(cls, 0.0) + (t1 - t0)
+    span = max(r[4] for r in fac) - min(r[3] for r in fac)
+    main_busy = sum(busy["main"].values())
+    return {"factor_span_ms": span, "main_ms": busy["main"], "side_ms": busy["side"],
+            "main_idle_ms": span - main_busy,
+            "note": "CUDA events around every launch of one untimed step; main = the call's stream, side = the "
+                    "lookahead chain's stream"}
 
 
 def max_over_ranks(value: float, world: int, device: str) -> float:
@@ -463,7 +484,13 @@ def main():
     clocks = sampler.stop()
     # one more (untimed) step with every launch bracketed by events, for the
     # per-kernel-class breakdown and the roofline's kernel time
-    _, info2 = step(2)
+    _, info2 = step(3)
+    trace = egs.egs_trace_last()
+    if a.trace and rank == 0:
+        with open(a.trace, "w") as f:
+            f.write("class,step,stream,start_ms,end_ms\n")
+            for cls, k, st, t0, t1 in trace:
+                f.write("%s,%d,%d,%.4f,%.4f\n" % (cls, k, st, t0, t1))
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, world, "cuda")
     value = whole_job_rate(a.steps, world, ms_max / 1e3)
@@ -550,6 +577,7 @@ def main():
                 "phase_ms": {"generate": statistics.mean(i["ms_generate"] for i in infos),
                              "factor": ms_factor, "solve": statistics.mean(i["ms_solve"] for i in infos)},
                 "kernel_class_ms": classes,
+                "timeline": timeline_summary(trace),
                 "loglik": infos[-1]["loglik"],
                 "roofline": roof, "clocks": clocks,
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
