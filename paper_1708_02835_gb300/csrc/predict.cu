@@ -101,10 +101,10 @@ extern "C" egs_status egs_predict(const double *locs_obs, const double *z_obs, i
     const bool host_out = !is_device_ptr(z_new);
     if (host_out) dout = (double *)(ws + es.need + extra_new);
     KernelTimer kt;
-    // Algorithm 3 lines 3-7: Sigma_22, its factorisation and X = Sigma_22^-1 Z_2
+    // Algorithm 3, the solve: Sigma_22, its factorisation and X = Sigma_22^-1 Z_2
     if (e == cudaSuccess) e = eval_enqueue(es, dlocs, dz, ws, s, &kt, nullptr);
     if (e == cudaSuccess) e = finish_solution(es, ws, s);
-    // line 8: Z_1 = Sigma_12 X, Sigma_12 formed on the fly
+    // Algorithm 3, the product: Z_1 = Sigma_12 X, Sigma_12 formed on the fly
     if (e == cudaSuccess) {
         k_predict<<<(unsigned)((m + PB - 1) / PB), 256, 0, s>>>(dnew, dnew + m, m, dlocs, dlocs + n,
                                                                eval_solution(es, ws), n, es.P, dout,
