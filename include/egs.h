@@ -342,7 +342,11 @@ egs_status egs_loglik_ind(const double *locs, const double *z, const double thet
  *   egs_serve_submit    non-blocking; returns a ticket.
  *   egs_serve_wait      timeout_ms < 0 waits forever; EGS_ERR_TIMEOUT if not
  *                       done in time (the request stays queued / running);
- *                       EGS_ERR_NOT_PD etc. from the evaluation.  A ticket is
+ *                       EGS_ERR_NOT_PD etc. from the evaluation; EGS_ERR_OOM
+ *                       if the request's workspace does not fit in the budget
+ *                       beside the resident fields even with nothing else in
+ *                       flight (it is failed at the head of the queue instead
+ *                       of blocking it).  A ticket is
  *                       consumed by the successful or failed wait that
  *                       returns its result.
  *   egs_serve_stats     p50 / p99 / mean latency, throughput, counters.

@@ -164,7 +164,19 @@ bool admit_one(egs_server *S, std::unique_lock<std::mutex> &lk)
         S->cv_done.notify_all();
         return true;
     }
-    if (S->used + es.need > S->cfg.hbm_budget_bytes) return false;  // wait for memory to free up
+    if (S->used + es.need > S->cfg.hbm_budget_bytes) {
+        if (S->inflight > 0) return false;  // wait for memory to free up
+        // nothing in flight: only resident fields hold the budget, so this
+        // request can never be admitted; fail it rather than block the queue
+        Result &r = S->results[rq.ticket];
+        r.done = true;
+        r.status = EGS_ERR_OOM;
+        r.loglik = NAN;
+        ++S->rejected;
+        S->queue.pop_front();
+        S->cv_done.notify_all();
+        return true;
+    }
     Slot &sl = *free_slot;
     char *ws = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&ws, es.need, sl.stream);
@@ -325,6 +337,10 @@ egs_status egs_serve_wait(egs_server *S, int64_t ticket, int32_t timeout_ms, dou
     S->results.erase(ticket);
     if (out_loglik) *out_loglik = r.loglik;
     if (info) *info = r.info;
+    if (r.status == EGS_ERR_OOM)
+        return set_error(r.status, "egs_serve_wait: request %lld needs more workspace than the budget leaves beside "
+                                   "the resident fields",
+                         (long long)ticket);
     if (r.status != EGS_OK) return set_error(r.status, "egs_serve_wait: request %lld failed", (long long)ticket);
     return EGS_OK;
 }

@@ -138,3 +138,32 @@ def test_fallback_answers_rejected_mixed_requests_in_fp64(egs):
                 srv.wait(t)
             assert srv.stats()["fallbacks"] == 0
         srv.close()
+
+
+def test_request_larger_than_the_budget_fails_without_blocking(egs):
+    """A request whose workspace cannot fit beside the resident fields even
+    with nothing in flight fails with EGS_ERR_OOM at the head of the queue,
+    and the requests behind it still run (bounded waits: a regression fails
+    instead of hanging)."""
+    from gpu_util import dev
+    small_n, big_n = 700, 3100
+    fields = [f for f in _fields() if f[0] in (small_n, big_n)]
+    need_small = egs.egs_loglik_workspace_bytes(small_n, TILE, "fp64", 2)
+    need_big = egs.egs_loglik_workspace_bytes(big_n, TILE, "fp64", 2)
+    assert need_big > need_small + (1 << 20)
+    budget = sum(3 * 8 * n for n, _, _ in fields) + need_small + (1 << 20)
+    srv = egs.egs_server(budget, max_inflight=2, tile=TILE, band=2)
+    fids = {n: srv.add_field(l, z, n) for n, l, z in fields}
+    th = (1.0, 0.08, 0.6)
+    t_big = srv.submit(fids[big_n], th, "fp64")
+    t_small = srv.submit(fids[small_n], th, "fp64")
+    with pytest.raises(egs.EgsError) as e:
+        srv.wait(t_big, timeout_ms=60000)
+    assert e.value.status == egs.EGS_ERR_OOM
+    got, _ = srv.wait(t_small, timeout_ms=60000)
+    n, l, z = [f for f in fields if f[0] == small_n][0]
+    want, _ = egs.egs_loglik_ex(dev(l), dev(z), th, n, "fp64", tile=TILE, band=2)
+    assert got == want
+    st = srv.stats()
+    assert st["rejected"] == 1 and st["completed"] == 1
+    srv.close()
