@@ -3,7 +3,9 @@
 // Storage: tiles with i - j < band (the diagonal band) stay FP64; the others
 // are FP32.  Per step k of the right-looking tile Cholesky (Section 5.2):
 //   POTRF  L_kk in FP64;
-//   TRSM   band rows (m - k < band) in FP64, the other rows in FP32 with
+//   TRSM   band rows (m - k < band) in FP64; the other rows in the FP32
+//          mode as the product with W = L_kk^-1 (inverted in FP64) on tcgen05
+//          in split TF32, in the TF32 / BF16 modes in FP32 arithmetic with
 //          L_kk rounded to FP32; every solved tile is also written to the
 //          panel buffer in the tensor-core operand format (TF32-rounded FP32,
 //          split TF32 hi/lo pairs, or BF16);
@@ -217,8 +219,9 @@ __global__ void __launch_bounds__(256) k_panel_from_f64(Tiles tl, int k, int nro
     }
 }
 
-// L_kk rounded to FP32 once per step (the FP32 TRSM reads it many times; a
-// conversion from FP64 runs on the FP64 pipe, 2 per clock per SM on GB300).
+// L_kk rounded to FP32 once per step for the FP32 TRSM of the TF32 / BF16
+// modes (it reads L_kk many times; a conversion from FP64 runs on the FP64
+// pipe, 2 per clock per SM on GB300).
 __global__ void __launch_bounds__(256) k_l32_from_f64(Tiles tl, int k, float *__restrict__ l32, const DevStatus *st)
 {
     if (mfailed(st)) return;
@@ -227,8 +230,9 @@ __global__ void __launch_bounds__(256) k_l32_from_f64(Tiles tl, int k, float *__
     for (size_t e = (size_t)blockIdx.x * 256 + threadIdx.x; e < bb; e += (size_t)gridDim.x * 256) l32[e] = (float)L[e];
 }
 
-// TRSM of the FP32 panel rows m = m0 + blockIdx.x: X L_kk^T = A_mk in FP32
-// (L_kk rounded to FP32, l32), 64 rows per CTA, 32-column blocks; the result
+// TRSM of the FP32 panel rows m = m0 + blockIdx.x (TF32 / BF16 modes):
+// X L_kk^T = A_mk in FP32 (L_kk rounded to FP32, l32), 64 rows per CTA,
+// 32-column blocks; the result
 // overwrites A_mk and is written to the panel buffer.  The GEMM-style part
 // keeps 4 rows x 2 columns per thread with the operands transposed in shared
 // memory (one 16-byte and one 8-byte shared load per 8 FMAs).  The kernel is
@@ -528,7 +532,7 @@ namespace {
 
 // The factorisation with one step of lookahead.  The FP64 chain of step k
 // (POTRF, the band TRSM, the band rows' operands, then the FP64 band x band
-// update) runs on a side stream; the main stream runs the FP32 TRSM of the
+// update) runs on a side stream; the main stream runs the TRSM of the
 // off-band panel on the whole GPU and the tensor-core update of column k + 1,
 // signals the side stream (whose chain for step k + 1 needs only that column
 // and its own band x band update), and updates the rest of the trailing
