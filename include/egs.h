@@ -79,7 +79,9 @@ typedef enum {
     EGS_MIX_FP32 = 1, /* FP64 band; off-band tiles FP32; updates of band tiles
                          FP64-accurate (DFMA, or exact BF16 slice products on
                          tcgen05), of off-band tiles on tcgen05 as split TF32
-                         (lo hi' + hi lo' + hi hi', FP32-accurate products) */
+                         (lo hi' + hi lo' + hi hi', FP32-accurate products);
+                         the off-band TRSM as the split-TF32 product with the
+                         FP64 inverse of the diagonal tile */
     EGS_MIX_TF32 = 2, /* FP64 band; off-band tiles FP32, updates on tcgen05 TF32 */
     EGS_MIX_BF16 = 3  /* FP64 band; off-band operands BF16, FP32 accumulation */
 } egs_precision;
