@@ -11,6 +11,12 @@ this size (band 2: 5.2e-6); --band 2 --precision fp32|tf32|bf16 gives the
 other variants.  Inputs are resident in HBM when the timed region starts; the
 tile matrix (up to 42 GB) is regenerated every step, far larger than L2.
 
+Besides the timed mixed-precision steps, the default line carries the rest of
+the metric: one FP64 evaluation of the same inputs ("fp64": evals/s, POTRF
+TFLOP/s, the FP64 update's roofline; "mixed_over_fp64", "dl_rel_vs_fp64"),
+the serving loop's p50 / p99 at 0.8 of its measured capacity ("serve"), and
+the oracle on a bounded host sample ("cpu_baseline").
+
 Usage:
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32|bf16|fp32]
   python bench.py --impl reference ...   (the CPU oracle as the reference arm)
@@ -58,7 +64,13 @@ def parse():
                          "MLE, batched and serving workloads")
     ap.add_argument("--evals", type=int, default=50, help="config2-mle: likelihood evaluations")
     ap.add_argument("--requests", type=int, default=48, help="config5-serve: requests per arrival rate")
-    ap.add_argument("--cpu-sample-n", type=int, default=8192)
+    ap.add_argument("--cpu-sample-n", type=int, default=8192,
+                    help="oracle sample size of the reference arm (one sample per step)")
+    ap.add_argument("--cpu-baseline-n", type=int, default=16384,
+                    help="oracle sample size of the cpu_baseline object of the default line (one sample)")
+    ap.add_argument("--no-fp64", action="store_true", help="config3: skip the one FP64 evaluation")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="config3: requests of the serving leg at 0.8 of capacity (0 = skip)")
     ap.add_argument("--trace", default="", help="config3: write the per-launch trace of the untimed breakdown step "
                                                  "to this CSV file")
     return ap.parse_args()
@@ -142,17 +154,20 @@ def band_out_flops(n: int, b: int, band: int) -> float:
     return tot
 
 
-def tensor_peak(precision: str) -> dict:
-    """Dense tensor peak for the operand type, from the measured bf16 figure."""
+def tensor_peak(precision: str, sustained: bool = False) -> dict:
+    """Dense tensor peak for the operand type, from the measured bf16 figure
+    (the burst figure for a kernel timed alone, the sustained one for a
+    kernel timed inside a long step)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
     try:
         with open(path) as f:
             mp = json.load(f)
-        bf16 = float(mp["bf16_tflops"])
-        src = "measured bf16 (MEASURED_PEAKS.json, burst)"
+        bf16 = float(mp[key])
+        src = "measured bf16 (MEASURED_PEAKS.json %s, %s)" % (key, "sustained" if sustained else "burst")
     except Exception:
-        bf16 = 1900.0
-        src = "fallback bf16 1.9 PFLOP/s"
+        bf16 = 1700.0 if sustained else 1900.0
+        src = "fallback bf16 %s PFLOP/s" % ("1.7 sustained" if sustained else "1.9 burst")
     if precision in ("tf32", "fp32"):
         return {"tflops": bf16 * 0.5, "source": src + " x 1/2 (nominal tf32:bf16 dense ratio 1.1:2.25)"}
     return {"tflops": bf16, "source": src}
@@ -355,49 +370,50 @@ def run_batched(a, egs):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(a, egs):
+def serve_rates(a, egs, rhos, requests: int, burst: int = 16) -> dict:
     """Config 5: 64 resident fields, n log-uniform in [1000, 40000], nu ~ U(0.3, 2);
-    Poisson arrivals of theta updates at 0.5 / 0.8 / 0.95 of measured capacity,
-    half FP64 and half --precision (mixed); 150 GB HBM budget."""
+    capacity from a closed burst, then open-loop Poisson arrivals of theta
+    updates at each fraction rho of it, half FP64 and half mixed requests;
+    150 GB HBM budget, 8 slots.  Returns capacity and per-rate statistics."""
     import numpy as np
     import egs_inputs as ei
     fields = ei.serving_fields(64)
     rng = np.random.default_rng(0)
     mixed = a.precision if a.precision != "fp64" else "fp32"
-    srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=a.band, fallback_fp64=True)
-    fids = [srv.add_field(np.ascontiguousarray(f.locations().reshape(-1)), f.e(), f.n) for f in fields]
 
-    def request(i):
+    def server():
+        srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=a.band, fallback_fp64=True)
+        return srv, [srv.add_field(np.ascontiguousarray(f.locations().reshape(-1)), f.e(), f.n) for f in fields]
+
+    def request(fids, i):
         f = int(rng.integers(len(fields)))
         th = tuple(float(v) * float(np.exp(rng.normal(0, 0.1))) for v in fields[f].theta)
         return fids[f], th, ("fp64" if i % 2 == 0 else mixed)
 
-    # capacity: a closed burst of requests
-    burst = [request(i) for i in range(16)]
+    srv, fids = server()
+    reqs = [request(fids, i) for i in range(burst)]
     t0 = time.perf_counter()
-    tickets = [srv.submit(*r) for r in burst]
+    tickets = [srv.submit(*r) for r in reqs]
     for t in tickets:
         try:
             srv.wait(t)
         except egs.EgsError:
             pass
-    cap = len(burst) / (time.perf_counter() - t0)
+    cap = len(reqs) / (time.perf_counter() - t0)
     srv.close()
     results = {}
-    for rho in (0.5, 0.8, 0.95):
-        srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=a.band, fallback_fp64=True)
-        fids = [srv.add_field(np.ascontiguousarray(f.locations().reshape(-1)), f.e(), f.n) for f in fields]
+    for rho in rhos:
+        srv, fids = server()
         rate = rho * cap
-        gaps = rng.exponential(1.0 / rate, a.requests)
+        gaps = rng.exponential(1.0 / rate, requests)
         tickets = []
-        t_start = time.perf_counter()
-        t_next = t_start
-        for i in range(a.requests):
+        t_next = time.perf_counter()
+        for i in range(requests):
             t_next += gaps[i]
             delay = t_next - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            tickets.append(srv.submit(*request(i)))
+            tickets.append(srv.submit(*request(fids, i)))
         for t in tickets:
             try:
                 srv.wait(t)
@@ -405,20 +421,60 @@ def run_serve(a, egs):
                 pass
         st = srv.stats()
         results[str(rho)] = {"rate_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                             "mean_ms": st["mean_ms"], "evals_per_s": st["evals_per_s"],
+                             "mean_ms": st["mean_ms"], "evals_per_s": st["evals_per_s"], "requests": requests,
                              "completed": st["completed"], "failed_not_pd_or_inaccurate": st["failed"],
                              "inflight_peak": st["inflight_peak"], "bytes_peak": st["bytes_peak"],
                              "mixed_rerun_in_fp64": st["fallbacks"]}
         srv.close()
-    line = {"metric": "serve p50/p99 ms and evals/s (config 5)", "value": results["0.8"]["p50_ms"],
-            "unit": "ms (p50 at 0.8 of capacity)", "n_gpus": 1, "higher_is_better": False, "dtype": "f64/f64+" + mixed,
-            "data": "synthetic (z ~ N(0, I))",
-            "config": {"workload": "64 fields, n log-uniform [1000, 40000], nu ~ U(0.3, 2), Poisson arrivals, "
-                                   "50/50 FP64 and %s (band %d; a mixed request the accuracy guard rejects is "
-                                   "re-run in FP64 by the server), 150 GB budget, 8 slots" % (mixed, a.band),
-                       "capacity_per_s": cap},
-            "rates": results}
+    return {"capacity_per_s": cap, "burst": burst, "mixed": mixed, "rates": results,
+            "workload": "64 fields, n log-uniform [1000, 40000], nu ~ U(0.3, 2), Poisson arrivals, 50/50 FP64 and "
+                        "%s (band %d; a mixed request the accuracy guard rejects is re-run in FP64 by the server), "
+                        "150 GB budget, 8 slots" % (mixed, a.band)}
+
+
+def run_serve(a, egs):
+    """Config 5 at 0.5 / 0.8 / 0.95 of measured capacity, --requests each."""
+    r = serve_rates(a, egs, (0.5, 0.8, 0.95), a.requests)
+    line = {"metric": "serve p50/p99 ms and evals/s (config 5)", "value": r["rates"]["0.8"]["p50_ms"],
+            "unit": "ms (p50 at 0.8 of capacity)", "n_gpus": 1, "higher_is_better": False,
+            "dtype": "f64/f64+" + r["mixed"], "data": "synthetic (z ~ N(0, I))",
+            "config": {"workload": r["workload"], "capacity_per_s": r["capacity_per_s"]},
+            "rates": r["rates"]}
     print(json.dumps(line), flush=True)
+
+
+def fp64_leg(a, egs, dlocs, dz, theta, stream) -> dict:
+    """One FP64 evaluation of the same workload (same locations, z, tile),
+    CUDA-event timed per phase and per kernel class: the FP64 half of the
+    metric.  One evaluation takes minutes (n^3/3 = 3.6e14 flop on the FP64
+    pipe), so it is timed once, after the mixed-precision legs."""
+    import torch
+    fc = flop_counts(a.n, a.tile)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(torch.cuda.current_device()))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ll, info = egs.egs_loglik_ex(dlocs, dz, theta, a.n, "fp64", tile=a.tile, timing=2, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    upd = info["ms_update"]
+    achieved = fc["update"] / (upd / 1e3) / 1e12
+    nlaunch = fc["T"] - 1
+    return {"evals_per_s": 1e3 / ms, "ms_per_eval": ms, "loglik": ll, "logdet": info["logdet"], "quad": info["quad"],
+            "potrf_tflops": fc["total_n3"] / (info["ms_factor"] / 1e3) / 1e12,
+            "phase_ms": {"generate": info["ms_generate"], "factor": info["ms_factor"], "solve": info["ms_solve"]},
+            "kernel_class_ms": {k: info["ms_" + k] for k in ("update", "potrf", "trsm", "trsv")},
+            "gpu_launches": info["launches"], "clocks": clocks,
+            "roofline": {"bound": "alu", "kernel": "k_update_f64 (SYRK/GEMM trailing update, DFMA)",
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe; no FP64 "
+                                        "tensor-core path is used)",
+                         "launches": nlaunch, "flops_per_launch": fc["update"] / nlaunch,
+                         "ms_per_launch": upd / nlaunch},
+            "note": "one evaluation, CUDA events on the launching stream, same inputs as the timed mixed steps"}
 
 
 def main():
@@ -511,6 +567,19 @@ def main():
                "h2d_bytes_per_step": int(hl.numel() * 8 + hz.numel() * 8), "d2h_bytes_per_step": 48,
                "steps": e2e_steps}
 
+    # the FP64 half of the metric (one evaluation of the same inputs) and the
+    # serving leg (p50 / p99 at 0.8 of capacity); every replica runs them
+    del ws
+    torch.cuda.empty_cache()
+    fp64 = None
+    if not a.no_fp64 and a.precision != "fp64":
+        fp64 = fp64_leg(a, egs, dlocs, dz, theta, stream)
+    torch.cuda.empty_cache()
+    serve = None
+    if a.serve_requests > 0:
+        serve = serve_rates(a, egs, (0.8,), a.serve_requests)
+    torch.cuda.empty_cache()
+
     if rank == 0:
         fc = flop_counts(n, tile)
         ms_step = ms_max / a.steps
@@ -539,21 +608,28 @@ def main():
                 tc_flops -= bo
                 f64_flops += bo
                 products = 3
-            achieved = products * tc_flops / (upd_ms / 1e3) / 1e12
-            peak = tensor_peak(a.precision)
+            executed = products * tc_flops / (upd_ms / 1e3) / 1e12
+            achieved = tc_flops / (upd_ms / 1e3) / 1e12
+            peak = tensor_peak(a.precision, sustained=True)
+            peak_burst = tensor_peak(a.precision, sustained=False)
             # DRAM bytes per executed flop of the split-TF32 update from an ncu
-            # capture at n = 32,768 (profiles/k_tc_gemm_splittf32_n32768_tile512.md),
-            # scaled to this launch size by its flops
+            # capture at n = 32,768, scaled to this launch size by its flops
             traffic = SPLIT_TF32_DRAM_BYTES_PER_FLOP * products * tc_flops / (2 * launches_update) \
                 if a.precision == "fp32" else None
             roof = {"bound": "tensor", "kernel": "k_tc_gemm (tcgen05 trailing update, %s)" % a.precision,
                     "achieved": achieved, "peak": peak["tflops"], "unit": "TFLOP/s", "frac": achieved / peak["tflops"],
                     "traffic": traffic, "traffic_unit": "bytes per launch (ncu capture at n=32768, scaled by flops)",
-                    "peak_source": peak["source"], "launches_per_step": 2 * launches_update,
-                    "flops_per_launch": products * tc_flops / (2 * launches_update),
+                    "peak_source": peak["source"] + "; the kernel runs inside a %.1f s step" % (ms_step / 1e3),
+                    "launches_per_step": 2 * launches_update,
+                    "flops_per_launch": tc_flops / (2 * launches_update),
                     "ms_per_launch": upd_ms / (2 * launches_update),
-                    "note": "executed TF32/BF16 MMA flops (%d product(s) per update) over the tcgen05 launches' "
-                            "event time (two launches per step: column k+1, then the rest)" % products}
+                    "executed_tflops": executed, "executed_frac": executed / peak["tflops"],
+                    "executed_frac_of_burst": executed / peak_burst["tflops"],
+                    "products_per_update": products,
+                    "note": "achieved = algorithmic flops of the off-band trailing updates (2 b^3 per tile GEMM, the "
+                            "n^3/3 convention) over the tcgen05 launches' event time (two launches per step: column "
+                            "k+1, then the rest); executed_* count the %d TF32/BF16 MMA product(s) per update that "
+                            "the kernel issues" % products}
             upd64 = info2["ms_update_f64"]
             if upd64 > 0:
                 a64 = f64_flops / (upd64 / 1e3) / 1e12
@@ -582,8 +658,21 @@ def main():
                 "roofline": roof, "clocks": clocks,
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "e2e": e2e}
+        if fp64 is not None:
+            line["fp64"] = fp64
+            line["mixed_over_fp64"] = (value / world) / fp64["evals_per_s"]
+            line["dl_rel_vs_fp64"] = abs(infos[-1]["loglik"] - fp64["loglik"]) / abs(fp64["loglik"])
+            line["dlogdet_vs_fp64"] = infos[-1]["logdet"] - fp64["logdet"]
+        if serve is not None:
+            r = serve["rates"]["0.8"]
+            line["serve"] = {"p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "evals_per_s": r["evals_per_s"],
+                             "capacity_per_s": serve["capacity_per_s"], "rate_per_s": r["rate_per_s"],
+                             "requests": r["requests"], "completed": r["completed"],
+                             "mixed_rerun_in_fp64": r["mixed_rerun_in_fp64"], "inflight_peak": r["inflight_peak"],
+                             "workload": serve["workload"] + "; capacity from a closed burst of %d requests, then "
+                                         "Poisson arrivals at 0.8 of it" % serve["burst"]}
         if not a.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(a, theta, min(a.cpu_sample_n, n))
+            line["cpu_baseline"] = cpu_baseline(a, theta, min(a.cpu_baseline_n, n))
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

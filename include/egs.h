@@ -189,6 +189,7 @@ egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3]
  * diagonal tile, TRSM on the panel, SYRK/GEMM on the trailing tiles).
  *   tiles       device, lower tiles of Sigma in EGS_FP64 layout; on return L
  *   fail_index  host; first failing row or -1.  The call synchronises stream.
+ * EGS_ERR_ARG if tiles is not device memory.
  */
 egs_status egs_potrf_tiles(void *tiles, int64_t n, int32_t tile, int64_t *fail_index, void *stream);
 
@@ -199,6 +200,7 @@ egs_status egs_potrf_tiles(void *tiles, int64_t n, int32_t tile, int64_t *fail_i
  *   tiles  device, L in EGS_FP64 lower-tile layout
  *   z      device, n doubles;  y  device, n doubles (may alias z)
  *   logdet, quad  host; the call synchronises stream.
+ * EGS_ERR_ARG if tiles, z or y is not device memory.
  */
 egs_status egs_trsv_tiles(const void *tiles, int64_t n, int32_t tile, const double *z, double *y,
                           double *logdet, double *quad, void *stream);
@@ -217,7 +219,10 @@ egs_status egs_trsv_tiles(const void *tiles, int64_t n, int32_t tile, const doub
  * ceil(n / tile) <= 2048, otherwise EGS_ERR_ARG with a message (use
  * egs_trsv_tiles).  The first call on a device looks up the array's device
  * address (once per device, with that device current); make that first call
- * before any stream capture.  All calls share the one array and it keeps the
+ * before any stream capture.  After cudaDeviceReset the next call on that
+ * device looks the address up again (the module is reloaded), so that call
+ * too should come before any capture.  z, y and tiles must be device memory
+ * (EGS_ERR_ARG otherwise).  All calls share the one array and it keeps the
  * last call's contents: calls that overlap on the GPU (for example on two
  * streams) race and must be serialised by the caller.  Synchronises stream.
  */

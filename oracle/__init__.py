@@ -268,6 +268,30 @@ def simulate_z(locs, theta, e) -> np.ndarray:
     return L @ _f64(e)
 
 
+def simulate_loglik(locs, theta, e) -> dict:
+    """Algorithm 1 followed by Algorithm 2 at the same theta, sharing the one
+    factorisation both take of Sigma(theta): L = dpotrf(Sigma), Z = L e
+    (Algorithm 1), then y = L^-1 Z, log|Sigma| = 2 sum log L_ii, Z^T Sigma^-1 Z
+    = y^T y and Eq. 1 (Algorithm 2).  Returns l, logdet, quad and z; the same
+    numbers as simulate_z followed by loglik_lapack, for one Cholesky instead
+    of two at large n."""
+    import scipy.linalg as sla
+
+    S = cov_matrix(locs, theta)
+    n = S.shape[0]
+    try:
+        L = sla.cholesky(S, lower=True, overwrite_a=True, check_finite=False)
+    except np.linalg.LinAlgError as exc:
+        raise NotPositiveDefinite(-1) from exc
+    del S
+    z = L @ _f64(e)
+    y = sla.solve_triangular(L, z, lower=True, check_finite=False)
+    logdet = 2.0 * float(np.sum(np.log(np.diag(L))))
+    quad = float(y @ y)
+    return {"loglik": -0.5 * quad - 0.5 * logdet - 0.5 * n * math.log(2.0 * math.pi),
+            "logdet": logdet, "quad": quad, "z": z}
+
+
 def predict(locs_obs, z_obs, locs_new, theta) -> np.ndarray:
     """Eq. 5 via Algorithm 3: Z1 = Sigma_12 Sigma_22^{-1} Z2."""
     import scipy.linalg as sla

@@ -12,6 +12,8 @@ namespace egs {
 
 static thread_local char g_err[512];
 
+void clear_error() { g_err[0] = 0; }
+
 egs_status set_error(egs_status code, const char *fmt, ...)
 {
     va_list ap;
@@ -329,6 +331,8 @@ egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3]
     if (!locs || !tiles) return set_error(EGS_ERR_ARG, "NULL pointer");
     egs_status st = check_theta(theta);
     if (st != EGS_OK) return st;
+    if (!is_device_ptr(locs) || !is_device_ptr(tiles))
+        return set_error(EGS_ERR_ARG, "egs_matern_tiles: locs and tiles must be device memory");
     egs_matern_params P;
     egs_matern_params_init(theta, &P);
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
@@ -343,6 +347,7 @@ egs_status egs_potrf_tiles(void *tiles, int64_t n, int32_t tile, int64_t *fail_i
     if (n < 1) return set_error(EGS_ERR_ARG, "n = %lld must be >= 1", (long long)n);
     if (!tile_ok(tile)) return set_error(EGS_ERR_ARG, "tile = %d must be a multiple of 64 in [64, 1024]", tile);
     if (!tiles) return set_error(EGS_ERR_ARG, "NULL pointer");
+    if (!is_device_ptr(tiles)) return set_error(EGS_ERR_ARG, "egs_potrf_tiles: tiles must be device memory");
     cudaStream_t s = (cudaStream_t)stream;
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
     DevStatus *st = nullptr;
@@ -368,6 +373,8 @@ egs_status egs_trsv_tiles(const void *tiles, int64_t n, int32_t tile, const doub
     if (n < 1) return set_error(EGS_ERR_ARG, "n = %lld must be >= 1", (long long)n);
     if (!tile_ok(tile)) return set_error(EGS_ERR_ARG, "tile = %d must be a multiple of 64 in [64, 1024]", tile);
     if (!tiles || !z || !y) return set_error(EGS_ERR_ARG, "NULL pointer");
+    if (!is_device_ptr(tiles) || !is_device_ptr(z) || !is_device_ptr(y))
+        return set_error(EGS_ERR_ARG, "egs_trsv_tiles: tiles, z and y must be device memory");
     cudaStream_t s = (cudaStream_t)stream;
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
     const size_t npad = (size_t)g.T * g.b;

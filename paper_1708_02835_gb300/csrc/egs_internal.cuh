@@ -129,7 +129,9 @@ void store_trace(const KernelTimer &kt, cudaEvent_t origin);
 // True for device (or managed) memory; host pointers are staged by the calls.
 bool is_device_ptr(const void *p);
 
-// Error reporting (api.cu): thread-local message, returns code.
+// Error reporting (api.cu): thread-local message, returns code.  clear_error
+// empties the message at the start of a call.
+void clear_error();
 egs_status set_error(egs_status code, const char *fmt, ...);
 egs_status cuda_error(cudaError_t e, const char *what);
 

@@ -3,12 +3,19 @@ overlapping requests on separate streams.
 
 Each result must be identical (bitwise) whether the request ran alone or in
 a mix of concurrent requests, and identical to a direct egs_loglik_ex call
-with the same tile and band: the evaluation kernels are deterministic.
+with the same tile and band: the evaluation kernels are deterministic.  Every
+served value is also checked against the FP64 CPU oracle (Eq. 1 by
+Algorithm 2) within the bar of its precision: |dl|/|l| <= 1e-10 in FP64 and
+<= 1e-6 in the FP32 and TF32 mixed modes (the bars of the mixed-precision
+parity tests at these sizes).
 """
 import numpy as np
 import pytest
 
 import egs_inputs as ei
+import oracle
+
+TOL = {"fp64": 1e-10, "fp32": 1e-6, "tf32": 1e-6}
 
 pytestmark = pytest.mark.gpu
 
@@ -34,11 +41,16 @@ def _fields():
 def _requests():
     rng = np.random.default_rng(3)
     reqs = []
-    for i in range(14):
+    for i in range(15):
         f = int(rng.integers(len(FIELDS)))
         th = (float(rng.uniform(0.5, 2.0)), float(rng.uniform(0.03, 0.1)), float(rng.uniform(0.4, 0.9)))
-        reqs.append((f, th, "fp64" if i % 2 == 0 else "tf32"))
+        reqs.append((f, th, ("fp64", "tf32", "fp32")[i % 3]))
     return reqs
+
+
+def _oracle_loglik(fields, f, th):
+    n, l, z = fields[f]
+    return oracle.loglik_lapack(l.reshape(2, n), z, th)["loglik"]
 
 
 def _serve(egs, fields, reqs, max_inflight, budget=64 << 30):
@@ -65,15 +77,21 @@ def test_same_alone_and_in_mix(egs):
     assert st1["inflight_peak"] == 1 and st4["inflight_peak"] > 1
     assert st4["completed"] == len(reqs) and st4["failed"] == 0
     assert st4["p99_ms"] >= st4["p50_ms"] > 0 and st4["evals_per_s"] > 0
+    worst = {}
     for (f, th, p), v in zip(reqs, alone):
         n, l, z = fields[f]
         direct, _ = egs.egs_loglik_ex(dev(l), dev(z), th, n, p, tile=TILE, band=2)
         assert v == direct
+        ref = _oracle_loglik(fields, f, th)
+        rel = abs(v - ref) / abs(ref)
+        worst[p] = max(worst.get(p, 0.0), rel)
+        assert rel <= TOL[p], (p, n, th, rel)
+    print("served values vs oracle, worst |dl|/|l| per precision:", worst)
 
 
 def test_budget_is_never_exceeded(egs):
     fields, reqs = _fields(), _requests()
-    need = max(egs.egs_loglik_workspace_bytes(n, TILE, p, 2) for n in FIELDS for p in ("fp64", "tf32"))
+    need = max(egs.egs_loglik_workspace_bytes(n, TILE, p, 2) for n in FIELDS for p in ("fp64", "tf32", "fp32"))
     field_bytes = sum(3 * 8 * n for n in FIELDS)
     budget = field_bytes + need + 1024
     out, st = _serve(egs, fields, reqs, 4, budget=budget)
@@ -125,6 +143,8 @@ def test_fallback_answers_rejected_mixed_requests_in_fp64(egs):
     locs = ei.jittered_grid(n, seed=77)
     z = ei.normal(77, n)
     want, _ = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "fp64", tile=TILE)
+    ref = oracle.loglik_lapack(locs, z, theta)["loglik"]
+    assert abs(want - ref) <= TOL["fp64"] * abs(ref)
     for fallback in (True, False):
         srv = egs.egs_server(8 << 30, max_inflight=2, tile=TILE, band=2, fallback_fp64=fallback)
         fid = srv.add_field(np.ascontiguousarray(locs.reshape(-1)), z, n)

@@ -86,3 +86,18 @@ def test_batches_and_servers():
     assert _status(egs.egs_server, 0)[0] == egs.EGS_ERR_ARG                                     # zero budget
     assert _status(egs.egs_server, 1 << 30, max_inflight=0)[0] == egs.EGS_ERR_ARG
     assert _status(egs.egs_server, 1 << 30, max_inflight=65)[0] == egs.EGS_ERR_ARG
+
+
+def test_solves_reject_host_pointers():
+    """The factor, right-hand side and solution of the tile solves (and the
+    tiles of the factorisation and the generator) are device memory; host
+    arrays are answered with EGS_ERR_ARG before any kernel sees them."""
+    tiles = np.zeros(64 * 64)
+    z, y = np.zeros(64), np.zeros(64)
+    for fn in (egs.egs_trsv_tiles, egs.egs_trsv_tiles_noalloc):
+        st, msg = _status(fn, tiles, 64, 64, z, y)
+        assert st == egs.EGS_ERR_ARG and "device" in msg
+    st, msg = _status(egs.egs_potrf_tiles, tiles, 64, 64)
+    assert st == egs.EGS_ERR_ARG and "device" in msg
+    st, msg = _status(egs.egs_matern_tiles, np.zeros(128), 64, GOOD, 64, tiles)
+    assert st == egs.EGS_ERR_ARG and "device" in msg

@@ -179,3 +179,31 @@ def test_planted_mistakes_are_caught(mut):
         except AssertionError:
             caught += 1
     assert caught >= 1
+
+
+@pytest.mark.parametrize("n,th", [(40, (1.3, 0.2, 1.3)), (64, (0.7, 0.15, 0.8))])
+def test_simulate_loglik_against_brute_force(n, th):
+    """Algorithm 1 then Algorithm 2 on one factorisation: the returned z is
+    L e, and l, log|Sigma|, Z^T Sigma^-1 Z match the long-double brute force
+    on that z."""
+    p = ei.Problem(n=n, theta=th, seed=n)
+    locs, e = p.locations(), p.e()
+    r = oracle.simulate_loglik(locs, th, e)
+    assert np.allclose(r["z"], oracle.simulate_z(locs, th, e), rtol=0, atol=1e-14)
+    ll, ld, q = brute_loglik(locs, r["z"], th)
+    assert abs(r["logdet"] - ld) <= 1e-11 * max(1.0, abs(ld))
+    assert abs(r["quad"] - q) <= 1e-11 * abs(q)
+    assert abs(r["loglik"] - ll) <= 1e-12 * abs(ll)
+    # Z = L e, so Z^T Sigma^-1 Z = e^T e (Algorithm 1 and Eq. 1 together)
+    assert abs(r["quad"] - float(e @ e)) <= 1e-11 * float(e @ e)
+
+
+def test_simulate_loglik_matches_separate_calls():
+    n, th = 900, (1.0, 0.2, 1.3)
+    p = ei.Problem(n=n, theta=th, seed=2)
+    locs, e = p.locations(), p.e()
+    r = oracle.simulate_loglik(locs, th, e)
+    z = oracle.simulate_z(locs, th, e)
+    ref = oracle.loglik_lapack(locs, z, th)
+    for k in ("loglik", "logdet", "quad"):
+        assert abs(r[k] - ref[k]) <= 1e-12 * abs(ref[k]), k

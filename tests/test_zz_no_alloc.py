@@ -51,3 +51,23 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(egs.EgsError) as e:
         egs.egs_trsv_tiles_noalloc(dummy, 200000, 512, dummy, dummy)
     assert e.value.status == egs.EGS_ERR_ARG and "scratch" in str(e.value)
+    # a successful call after the rejected one leaves no stale message behind
+    n, tile = 500, 128
+    tiles = _factor(egs, n, tile, (1.0, 0.1, 0.5), seed=6)
+    z = torch.as_tensor(ei.normal(60, n)).cuda()
+    y = torch.empty_like(z)
+    egs.egs_trsv_tiles_noalloc(tiles, n, tile, z, y)
+    assert egs.egs_last_error() == ""
+
+
+def test_noalloc_rejects_host_pointers():
+    import torch
+    import paper_1708_02835_gb300 as egs
+    egs.load_library()
+    n, tile = 500, 128
+    tiles = _factor(egs, n, tile, (1.0, 0.1, 0.5), seed=6)
+    z = ei.normal(61, n)
+    y = np.empty(n)
+    with pytest.raises(egs.EgsError) as e:
+        egs.egs_trsv_tiles_noalloc(tiles, n, tile, z, y)
+    assert e.value.status == egs.EGS_ERR_ARG and "device" in str(e.value)
