@@ -174,11 +174,14 @@ size_t egs_loglik_workspace_bytes(int64_t n, int32_t tile, egs_precision p, int3
 
 /*
  * egs_matern_tiles - generate Sigma(theta) (Eq. 2; Algorithm 2, genCovMatrix)
- * into the lower-tile layout.
+ * into the lower-tile layout of precision p (egs_tiles_bytes): EGS_FP64 every
+ * tile double; the mixed precisions the band tiles (i - j < band, band <= 0
+ * meaning 2) as doubles and the other tiles rounded to float in the second
+ * array (all double when T <= band).  Every value is computed in FP64.
  *   locs   device, 2n doubles (x then y)
  *   tiles  device, egs_tiles_bytes(n, tile, p, band) bytes, written
  * Entries with r = 0 take the limit C(0) = theta1.  Asynchronous on stream.
- * Only EGS_FP64 is accepted here.
+ * EGS_ERR_ARG if locs or tiles is not device memory.
  */
 egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3], int32_t tile,
                             egs_precision p, int32_t band, void *tiles, void *stream);
@@ -263,14 +266,23 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
  * Batched evaluation (independent problems: uneven n, own theta each).
  *
  * Each problem is Eq. 1 evaluated by Algorithm 2 exactly as egs_loglik does
- * in EGS_FP64; the batch runs the tile algorithm of Section 5.2 for all
- * problems at once: every kernel launch covers one step of every problem, so
- * the whole batch is a few hundred launches, captured into a CUDA graph on the
- * first egs_batch_run and replayed afterwards.
+ * in EGS_FP64.  EGS_FP64 batches with tile <= 256 run as ONE persistent
+ * kernel launch: the tile tasks of every problem (Matern tiles, the POTRF /
+ * TRSM / SYRK-GEMM tasks of the tile Cholesky of Section 5.2 -- the DAG of
+ * its tile algorithm -- and the forward-solve tasks) form one list in a
+ * dependency order checked when the plan is made, and each CTA claims the
+ * next task and waits on per-tile device counters until its inputs are final
+ * (every wait bounded: EGS_ERR_TIMEOUT if one runs out).  Every l is bitwise
+ * equal to egs_loglik_ex's with the same tile.  Other batches (EGS_MIX_FP32,
+ * or tiles above 256) run as step-synchronous launches, each covering one
+ * step of every problem.  Either way the run is captured into a CUDA graph on
+ * the first egs_batch_run and replayed afterwards.
  *
  * egs_batch_create  plan for nprob problems of sizes n[0..nprob) with one tile
- *                   size for the batch (0 = chosen from the largest n); owns
- *                   all device memory of the batch (egs_batch_workspace_bytes).
+ *                   size for the batch (0 = the tile egs_batch_autotune found
+ *                   for this size class and precision, else 64 up to n = 2048
+ *                   and 128 above); owns all device memory of the batch
+ *                   (egs_batch_workspace_bytes).
  * egs_batch_run     locs[i] (2 n[i] doubles, x then y) and z[i] (n[i]
  *                   doubles), device or host memory; theta: nprob x 3 host
  *                   doubles.  out[i] = l_i (NaN if problem i is not positive
@@ -295,6 +307,35 @@ size_t egs_batch_workspace_bytes(const egs_batch *batch);
 egs_status egs_loglik_batched(int32_t nprob, const int64_t *n, const double *const *locs, const double *const *z,
                               const double *theta, egs_precision p, double *out, egs_status *per_status,
                               void *stream);
+
+/*
+ * egs_batch_autotune - the tile autotuner of the batched scheduler: builds a
+ * batch of these problems with each candidate tile (64, 128, 256), runs it
+ * twice on the caller's inputs (same arguments as egs_batch_run) and times
+ * the second run with CUDA events on stream; the fastest tile is stored in
+ * the library's table under (ceil(log2(largest n)), p), where
+ * egs_batch_create with tile = 0 finds it for later batches of that size
+ * class.  *best_tile (nullable) receives it, ms[0..2] (nullable) the three
+ * run times.  Allocates and synchronises; problems that are not positive
+ * definite do not stop the tuning.
+ */
+egs_status egs_batch_autotune(int32_t nprob, const int64_t *n, const double *const *locs, const double *const *z,
+                              const double *theta, egs_precision p, int32_t *best_tile, double *ms, void *stream);
+/* Tile stored by egs_batch_autotune for batches whose largest n is nmax, or 0. */
+int32_t egs_batch_tuned_tile(int64_t nmax, egs_precision p);
+
+/* Tasks in the persistent launch of a batch (0 for a step-synchronous batch). */
+int64_t egs_batch_tasks(const egs_batch *batch);
+/*
+ * egs_batch_set_wait_limit - failure detection of the persistent launch:
+ * every dependency wait gives up after limit_ns nanoseconds (default 10 s)
+ * and the run returns EGS_ERR_TIMEOUT (all per_status EGS_ERR_TIMEOUT, out
+ * NaN) with the batch still usable.  withhold_task in [0, egs_batch_tasks)
+ * makes the launch never signal that task's completion, so that the waits
+ * on it run out (for tests of this path); -1 signals every task.  Applies to
+ * the following runs.  EGS_ERR_UNIMPLEMENTED for a step-synchronous batch.
+ */
+egs_status egs_batch_set_wait_limit(egs_batch *batch, int64_t limit_ns, int64_t withhold_task);
 
 /*
  * egs_predict - kriging prediction, Eq. 5 by Algorithm 3 (Section 6.6): with

@@ -122,6 +122,11 @@ def load_library(build_if_missing: bool = True):
         "egs_loglik_batched": (c.c_int, [i32, c.POINTER(i64), c.POINTER(vp), c.POINTER(vp), pd, c.c_int, pd,
                                          c.POINTER(c.c_int), vp]),
         "egs_loglik_ind": (c.c_int, [vp, vp, pd, i64, i32, i32, pd, c.POINTER(egs_info), vp]),
+        "egs_batch_autotune": (c.c_int, [i32, c.POINTER(i64), c.POINTER(vp), c.POINTER(vp), pd, c.c_int,
+                                         c.POINTER(i32), pd, vp]),
+        "egs_batch_tuned_tile": (i32, [i64, c.c_int]),
+        "egs_batch_tasks": (i64, [vp]),
+        "egs_batch_set_wait_limit": (c.c_int, [vp, i64, i64]),
         "egs_predict": (c.c_int, [vp, vp, i64, vp, i64, pd, c.c_int, c.POINTER(egs_opts), vp, c.POINTER(egs_info),
                                   vp]),
         "egs_trace_last": (c.c_int, [c.POINTER(egs_trace_rec), i64, c.POINTER(i64)]),
@@ -339,6 +344,16 @@ class egs_batch:
     def workspace_bytes(self) -> int:
         return load_library().egs_batch_workspace_bytes(self._h)
 
+    @property
+    def tasks(self) -> int:
+        """Tasks of the persistent launch (0 for a step-synchronous batch)."""
+        return load_library().egs_batch_tasks(self._h)
+
+    def set_wait_limit(self, limit_ns: int, withhold_task: int = -1):
+        """Bound of every dependency wait of the persistent launch; a task
+        whose completion is withheld (failure tests), or -1."""
+        _check(load_library().egs_batch_set_wait_limit(self._h, int(limit_ns), int(withhold_task)))
+
     def run(self, locs, z, thetas, stream=None, raise_on_not_pd=False):
         """locs[i], z[i]: per-problem arrays (device tensors or host arrays);
         thetas: nprob x 3.  Returns (loglik array, status array)."""
@@ -367,6 +382,32 @@ class egs_batch:
             self.close()
         except Exception:
             pass
+
+
+def _batch_inputs(locs, z, thetas):
+    npb = len(locs)
+    lp = (ctypes.c_void_p * npb)(*[_ptr(a) for a in locs])
+    zp = (ctypes.c_void_p * npb)(*[_ptr(a) for a in z])
+    th = np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).reshape(npb, 3))
+    return lp, zp, th
+
+
+def egs_batch_autotune(ns, locs, z, thetas, precision="fp64", stream=None) -> tuple:
+    """Time tiles 64 / 128 / 256 on these inputs; the library keeps the best
+    for egs_batch(tile=0).  Returns (best tile, {tile: ms})."""
+    lib = load_library()
+    npb = len(ns)
+    arr = (ctypes.c_int64 * npb)(*[int(v) for v in ns])
+    lp, zp, th = _batch_inputs(locs, z, thetas)
+    best = ctypes.c_int32(0)
+    ms = (ctypes.c_double * 3)()
+    _check(lib.egs_batch_autotune(npb, arr, lp, zp, th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  _prec(precision), ctypes.byref(best), ms, _stream(stream)))
+    return best.value, {64: ms[0], 128: ms[1], 256: ms[2]}
+
+
+def egs_batch_tuned_tile(nmax: int, precision="fp64") -> int:
+    return load_library().egs_batch_tuned_tile(int(nmax), _prec(precision))
 
 
 def egs_loglik_batched(locs, z, thetas, ns, precision="fp64", stream=None):

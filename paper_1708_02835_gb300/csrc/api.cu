@@ -323,11 +323,10 @@ size_t egs_loglik_workspace_bytes(int64_t n, int32_t tile, egs_precision p, int3
 egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3], int32_t tile,
                             egs_precision p, int32_t band, void *tiles, void *stream)
 {
-    (void)band;
     g_err[0] = 0;
     if (n < 1) return set_error(EGS_ERR_ARG, "n = %lld must be >= 1", (long long)n);
     if (!tile_ok(tile)) return set_error(EGS_ERR_ARG, "tile = %d must be a multiple of 64 in [64, 1024]", tile);
-    if (p != EGS_FP64) return set_error(EGS_ERR_UNIMPLEMENTED, "egs_matern_tiles: only EGS_FP64 layout");
+    if (p != EGS_FP64 && !mixed_p(p)) return set_error(EGS_ERR_UNIMPLEMENTED, "precision %d not built", (int)p);
     if (!locs || !tiles) return set_error(EGS_ERR_ARG, "NULL pointer");
     egs_status st = check_theta(theta);
     if (st != EGS_OK) return st;
@@ -336,7 +335,17 @@ egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3]
     egs_matern_params P;
     egs_matern_params_init(theta, &P);
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
-    cudaError_t e = launch_matern_tiles_f64(locs, locs + n, g, P, (double *)tiles, (cudaStream_t)stream);
+    if (band <= 0) band = 2;
+    cudaError_t e;
+    if (p == EGS_FP64 || g.T <= band) {
+        e = launch_matern_tiles_f64(locs, locs + n, g, P, (double *)tiles, (cudaStream_t)stream);
+    } else {
+        // band tiles as doubles, then the off-band tiles as floats right after them
+        double *f64 = (double *)tiles;
+        float *f32 = (float *)(f64 + Tiles::f64_tiles(g.T, band) * g.tile_elems());
+        const Tiles tl{f64, f32, g.b, g.T, band};
+        e = launch_matern_tiles(locs, locs + n, n, tl, P, nullptr, (cudaStream_t)stream, nullptr);
+    }
     if (e != cudaSuccess) return cuda_error(e, "egs_matern_tiles launch");
     return EGS_OK;
 }

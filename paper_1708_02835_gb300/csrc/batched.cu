@@ -12,26 +12,15 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
+#include "batched.cuh"
+#include "batched_dag.cuh"
 #include "blocks.cuh"
 #include "matern.cuh"
 
 namespace egs {
-
-struct BatchProblem {
-    const double *X, *Y, *z;
-    int64_t n;
-    int T, band;       // band >= T: every tile FP64 (the FP64 batch)
-    double *tiles;     // FP64 tiles: T(T+1)/2 lower tiles, or the band tiles of a mixed problem
-    float *f32;        // mixed: off-band FP32 tiles
-    double *sig;       // mixed: dense FP64 copy of Sigma (lower tiles) for the refinement
-    double *zpad;      // T*b: Z, then the forward solution y
-    double *x, *d, *rows, *cols;  // mixed: T*b vectors
-    double *partials;  // 2T
-    DevStatus *st;
-    const egs_matern_params *P;
-};
 
 struct BatchArgs {
     const BatchProblem *probs;
@@ -434,6 +423,18 @@ struct egs_batch {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int launches_per_run = 0;
+    // persistent scheduler (FP64 batches with tile <= 256): one launch over
+    // the task list of every problem
+    bool dag = false;
+    int4 *d_tasks = nullptr;
+    long long ntasks = 0;
+    unsigned *d_cnt = nullptr;
+    size_t ncnt = 0;
+    DagCtl *d_ctl = nullptr;
+    DagCtl *h_ctl = nullptr;  // pinned: [0] written before a run, [1] read back after it
+    int grid = 0;
+    unsigned long long limit_ns = kDagWaitLimitNs;
+    long long withhold = -1;
 };
 
 namespace {
@@ -444,6 +445,24 @@ enum {
 };
 
 constexpr int kBatchBand = 2;  // FP64 band of the mixed batches (tiles)
+
+// Tile table of the autotuner: [ceil(log2(largest n))][precision], 0 = not tuned.
+std::mutex g_tune_mu;
+int32_t g_tuned[64][4] = {};
+
+int size_class(int64_t nmax)
+{
+    int c = 0;
+    while (c < 63 && ((int64_t)1 << c) < nmax) ++c;
+    return c;
+}
+
+int32_t tuned_tile(int64_t nmax, egs_precision p)
+{
+    if ((int)p < 0 || (int)p > 3) return 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tuned[size_class(nmax)][(int)p];
+}
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -517,6 +536,14 @@ void plan_launches(egs_batch *B, std::vector<int64_t> &prefix)
 
 cudaError_t enqueue_all(egs_batch *B, cudaStream_t s)
 {
+    if (B->dag) {
+        cudaError_t e = cudaMemsetAsync(B->d_cnt, 0, B->ncnt * sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_ctl, B->h_ctl, sizeof(DagCtl), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = dag_enqueue(B->d_tasks, B->ntasks, B->d_probs, B->d_ctl, B->b, B->grid, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B->h_ctl + 1, B->d_ctl, sizeof(DagCtl), cudaMemcpyDeviceToHost, s);
+        B->launches_per_run = 1;
+        return e;
+    }
     int count = 0;
     for (const auto &L : B->launches) {
         if (L.items <= 0) continue;
@@ -564,7 +591,8 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
     if (tile == 0) {
         int64_t nmax = 0;
         for (int i = 0; i < nprob; ++i) nmax = std::max(nmax, n[i]);
-        tile = nmax <= 2048 ? 64 : 128;
+        tile = tuned_tile(nmax, p);
+        if (tile == 0) tile = nmax <= 2048 ? 64 : 128;
     }
     if (tile < 64 || tile > 1024 || tile % 64) return set_error(EGS_ERR_ARG, "egs_batch_create: tile %d invalid", tile);
     egs_batch *B = new egs_batch;
@@ -609,9 +637,27 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
     const size_t inputs_off = off;
     off += a256(in_doubles * sizeof(double));
     std::vector<int64_t> prefix;
-    plan_launches(B, prefix);
+    std::vector<int4> tasks;
+    std::vector<size_t> cnt_off;
+    B->dag = !B->mixed && tile <= 256;
+    if (B->dag) {
+        egs_status sc = dag_plan(B->T, tile, tasks, cnt_off, B->ncnt);
+        if (sc != EGS_OK) {
+            delete B;
+            return sc;
+        }
+        B->ntasks = (long long)tasks.size();
+    } else {
+        plan_launches(B, prefix);
+    }
     const size_t prefix_off = off;
     off += a256(prefix.size() * sizeof(int64_t));
+    const size_t tasks_off = off;
+    off += a256(tasks.size() * sizeof(int4));
+    const size_t cnt_off_bytes = off;
+    off += a256(B->ncnt * sizeof(unsigned));
+    const size_t ctl_off = off;
+    off += a256(sizeof(DagCtl));
     B->ws_bytes = off;
     cudaError_t e = cudaMalloc((void **)&B->ws, off);
     if (e != cudaSuccess) {
@@ -626,7 +672,18 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
     if (e == cudaSuccess) e = cudaMallocHost((void **)&B->h_probs, sizeof(BatchProblem) * nprob);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&B->h_params, sizeof(egs_matern_params) * nprob);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&B->h_status, sizeof(DevStatus) * nprob);
-    if (e == cudaSuccess) e = cudaMemcpy(B->d_prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !prefix.empty())
+        e = cudaMemcpy(B->d_prefix, prefix.data(), prefix.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (B->dag) {
+        B->d_tasks = (int4 *)(B->ws + tasks_off);
+        B->d_cnt = (unsigned *)(B->ws + cnt_off_bytes);
+        B->d_ctl = (DagCtl *)(B->ws + ctl_off);
+        B->grid = dag_grid();
+        if (B->grid < 1) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&B->h_ctl, 2 * sizeof(DagCtl));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B->d_tasks, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming);
@@ -659,6 +716,7 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
         pr.partials = (double *)(B->ws + part_off[i]);
         pr.st = B->d_status + i;
         pr.P = B->d_params + i;
+        pr.cnt = B->dag ? B->d_cnt + cnt_off[i] : nullptr;
     }
     e = cudaMemcpy(B->d_probs, B->h_probs, sizeof(BatchProblem) * nprob, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -677,6 +735,11 @@ namespace {
 // (captured on first use) and the statuses back to the host; synchronises.
 cudaError_t run_staged(egs_batch *B, cudaStream_t us, cudaError_t e)
 {
+    if (B->dag) {
+        std::memset(B->h_ctl, 0, 2 * sizeof(DagCtl));
+        B->h_ctl[0].limit_ns = B->limit_ns;
+        B->h_ctl[0].withhold = B->withhold;
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(B->d_params, B->h_params, sizeof(egs_matern_params) * B->nprob, cudaMemcpyHostToDevice, B->cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->d_status, 0xFF, sizeof(DevStatus) * B->nprob, B->cs);
@@ -723,6 +786,14 @@ egs_status egs_batch_run(egs_batch *B, const double *const *locs, const double *
     }
     e = run_staged(B, us, e);
     if (e != cudaSuccess) return cuda_error(e, "egs_batch_run");
+    if (B->dag && B->h_ctl[1].timeouts > 0) {
+        for (int i = 0; i < B->nprob; ++i) {
+            if (out) out[i] = NAN;
+            if (per_status) per_status[i] = EGS_ERR_TIMEOUT;
+        }
+        return set_error(EGS_ERR_TIMEOUT, "egs_batch_run: %u dependency wait(s) of the persistent launch ran out of "
+                                          "time; the run was abandoned", B->h_ctl[1].timeouts);
+    }
     egs_status worst = EGS_OK;
     for (int i = 0; i < B->nprob; ++i) {
         const DevStatus &h = B->h_status[i];
@@ -741,7 +812,69 @@ egs_status egs_batch_run(egs_batch *B, const double *const *locs, const double *
 
 int32_t egs_batch_launches(const egs_batch *B) { return B ? B->launches_per_run : 0; }
 
+int64_t egs_batch_tasks(const egs_batch *B) { return B && B->dag ? (int64_t)B->ntasks : 0; }
+
+egs_status egs_batch_set_wait_limit(egs_batch *B, int64_t limit_ns, int64_t withhold_task)
+{
+    if (!B) return set_error(EGS_ERR_ARG, "egs_batch_set_wait_limit: NULL batch");
+    if (!B->dag) return set_error(EGS_ERR_UNIMPLEMENTED, "egs_batch_set_wait_limit: not a persistent batch");
+    if (limit_ns < 1 || withhold_task < -1 || withhold_task >= (int64_t)B->ntasks)
+        return set_error(EGS_ERR_ARG, "egs_batch_set_wait_limit: limit %lld ns or task %lld out of range",
+                         (long long)limit_ns, (long long)withhold_task);
+    B->limit_ns = (unsigned long long)limit_ns;
+    B->withhold = withhold_task;
+    return EGS_OK;
+}
+
 int32_t egs_batch_tile(const egs_batch *B) { return B ? B->b : 0; }
+
+int32_t egs_batch_tuned_tile(int64_t nmax, egs_precision p) { return nmax >= 1 ? tuned_tile(nmax, p) : 0; }
+
+egs_status egs_batch_autotune(int32_t nprob, const int64_t *n, const double *const *locs, const double *const *z,
+                              const double *theta, egs_precision p, int32_t *best_tile, double *ms, void *stream)
+{
+    if (!n || !locs || !z || !theta || nprob < 1) return set_error(EGS_ERR_ARG, "egs_batch_autotune: bad arguments");
+    static const int32_t cand[3] = {64, 128, 256};
+    cudaStream_t us = (cudaStream_t)stream;
+    int32_t best = 0;
+    double best_ms = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        egs_batch *B = nullptr;
+        egs_status st = egs_batch_create(nprob, n, cand[c], p, &B);
+        if (st != EGS_OK) return st;
+        // first run captures the graph; the second is timed
+        st = egs_batch_run(B, locs, z, theta, nullptr, nullptr, stream);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        float t = 0.f;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, us);
+        if (e == cudaSuccess && (st == EGS_OK || st == EGS_ERR_NOT_PD || st == EGS_ERR_INACCURATE))
+            st = egs_batch_run(B, locs, z, theta, nullptr, nullptr, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, us);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        egs_batch_destroy(B);
+        if (e != cudaSuccess) return cuda_error(e, "egs_batch_autotune");
+        if (st != EGS_OK && st != EGS_ERR_NOT_PD && st != EGS_ERR_INACCURATE) return st;
+        if (ms) ms[c] = t;
+        if (best == 0 || t < best_ms) {
+            best = cand[c];
+            best_ms = t;
+        }
+    }
+    int64_t nmax = 0;
+    for (int i = 0; i < nprob; ++i) nmax = std::max(nmax, n[i]);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[size_class(nmax)][(int)p] = best;
+    }
+    if (best_tile) *best_tile = best;
+    clear_error();
+    return EGS_OK;
+}
 
 size_t egs_batch_workspace_bytes(const egs_batch *B) { return B ? B->ws_bytes : 0; }
 
@@ -757,6 +890,7 @@ egs_status egs_batch_destroy(egs_batch *B)
     if (B->h_probs) cudaFreeHost(B->h_probs);
     if (B->h_params) cudaFreeHost(B->h_params);
     if (B->h_status) cudaFreeHost(B->h_status);
+    if (B->h_ctl) cudaFreeHost(B->h_ctl);
     delete B;
     return EGS_OK;
 }
@@ -813,6 +947,10 @@ egs_status egs_loglik_ind(const double *locs, const double *z, const double thet
     if (e != cudaSuccess) {
         egs_batch_destroy(B);
         return cuda_error(e, "egs_loglik_ind");
+    }
+    if (B->dag && B->h_ctl[1].timeouts > 0) {
+        egs_batch_destroy(B);
+        return set_error(EGS_ERR_TIMEOUT, "egs_loglik_ind: a dependency wait of the persistent launch ran out of time");
     }
     // fixed-order FP64 sums over the blocks
     double ll = 0.0, ld = 0.0, q = 0.0;

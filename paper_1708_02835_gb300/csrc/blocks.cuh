@@ -116,39 +116,85 @@ __device__ __forceinline__ bool potrf_block(double *A, int nb, int ld, int64_t r
 // ---------------------------------------------------------------------------
 // Cholesky of a 64 x 64 block at A (row stride ld) held in shared memory for
 // the whole factorisation (one global read and one write of the block): one
-// CTA of 256 threads, right-looking column by column.  Same failure
+// CTA of 256 threads, right-looking over four 16-column panels -- warp 0
+// factors the 16 x 16 diagonal block with warp synchronisation only, each row
+// below it is solved by one thread, and the trailing lower triangle takes a
+// rank-16 update (one 16-term dot product per entry) -- so the block needs 12
+// CTA barriers, and its FP64 work is mostly independent FMAs.  Same failure
 // reporting as potrf_block; the strict upper triangle is zeroed.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool potrf64_smem(double *A, int ld, int64_t row0, DevStatus *st)
+struct Potrf64Smem {
+    double S[64][65];
+    int fail_j;
+};
+
+__device__ __forceinline__ bool potrf64_smem_s(Potrf64Smem &sm, double *A, int ld, int64_t row0, DevStatus *st)
 {
-    __shared__ double S[64][65];
-    __shared__ int fail_j;
-    const int tid = threadIdx.x;
+    double(&S)[64][65] = sm.S;
+    int &fail_j = sm.fail_j;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) fail_j = -1;
     for (int e = tid; e < 64 * 64; e += 256) {
         const int i = e >> 6, j = e & 63;
         S[i][j] = (j <= i) ? A[(size_t)i * ld + j] : 0.0;
     }
     __syncthreads();
-    for (int j = 0; j < 64; ++j) {
-        if (tid == 0) {
-            const double d = S[j][j];
-            if (!(d > 0.0)) fail_j = j;
-            else S[j][j] = sqrt(d);
+    for (int p0 = 0; p0 < 64; p0 += kPW) {
+        // 1. the 16 x 16 diagonal block, column by column, by warp 0 (lane i < 16 owns row p0 + i)
+        if (tid < 32) {
+            for (int j = 0; j < kPW; ++j) {
+                double d = 0.0;
+                if (lane == j) {
+                    d = S[p0 + j][p0 + j];
+                    if (d > 0.0) S[p0 + j][p0 + j] = sqrt(d);
+                }
+                d = __shfl_sync(0xffffffffu, d, j);
+                if (!(d > 0.0)) {
+                    if (lane == 0) fail_j = p0 + j;
+                    break;
+                }
+                __syncwarp();
+                const double ljj = S[p0 + j][p0 + j];
+                if (lane > j && lane < kPW) S[p0 + lane][p0 + j] /= ljj;
+                __syncwarp();
+                if (lane > j && lane < kPW) {
+                    const double lij = S[p0 + lane][p0 + j];
+                    for (int l = j + 1; l <= lane; ++l) S[p0 + lane][p0 + l] -= lij * S[p0 + l][p0 + j];
+                }
+                __syncwarp();
+            }
         }
         __syncthreads();
         if (fail_j >= 0) {
             if (tid == 0) atomicMin(&st->fail_index, (unsigned long long)(row0 + fail_j));
             return false;
         }
-        const double ljj = S[j][j];
-        if (tid > j && tid < 64) S[tid][j] /= ljj;
+        const int q0 = p0 + kPW;
+        // 2. rows below the panel: x L_pp^T = row, one thread per row
+        if (tid < 64 - q0) {
+            const int i = q0 + tid;
+            double x[kPW];
+#pragma unroll
+            for (int j = 0; j < kPW; ++j) {
+                double v = S[i][p0 + j];
+#pragma unroll
+                for (int l = 0; l < j; ++l) v -= x[l] * S[p0 + j][p0 + l];
+                x[j] = v / S[p0 + j][p0 + j];
+            }
+#pragma unroll
+            for (int j = 0; j < kPW; ++j) S[i][p0 + j] = x[j];
+        }
         __syncthreads();
-        // trailing update S[i][l] -= S[i][j] S[l][j] for j < l <= i
-        const int m = 63 - j;  // trailing size
+        // 3. rank-16 update of the trailing lower triangle (rows and columns q0..63)
+        const int m = 64 - q0;
         for (int e = tid; e < m * m; e += 256) {
-            const int i = j + 1 + e / m, l = j + 1 + e % m;
-            if (l <= i) S[i][l] -= S[i][j] * S[l][j];
+            const int i = q0 + e / m, l = q0 + e % m;
+            if (l <= i) {
+                double acc = 0.0;
+#pragma unroll
+                for (int j = 0; j < kPW; ++j) acc = fma(S[i][p0 + j], S[l][p0 + j], acc);
+                S[i][l] -= acc;
+            }
         }
         __syncthreads();
     }
@@ -157,6 +203,12 @@ __device__ __forceinline__ bool potrf64_smem(double *A, int ld, int64_t row0, De
         A[(size_t)i * ld + j] = (j <= i) ? S[i][j] : 0.0;
     }
     return true;
+}
+
+__device__ __forceinline__ bool potrf64_smem(double *A, int ld, int64_t row0, DevStatus *st)
+{
+    __shared__ Potrf64Smem sm;
+    return potrf64_smem_s(sm, A, ld, row0, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -203,14 +255,23 @@ __device__ __forceinline__ void gemm_sub32(const EA *Am, int lda, const EB *An, 
 // the columns before it are zero in A, hence in X, and are skipped.  TX =
 // float: X and all arithmetic in FP32 (L rounded to FP32 as it is staged).
 // ---------------------------------------------------------------------------
+template <int RB, typename TX>
+struct TrsmSmem {
+    TX Xs[RB][kPW + 1];
+    TX Ls[32][kPW + 1];
+    TX Ab[RB][33];
+    TX Ld[32][33];
+};
+
 template <int RB, typename TX = double>
-__device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, TX *Xp, int ldx, int ncols, int cstart = 0)
+__device__ __forceinline__ void trsm_rows_s(TrsmSmem<RB, TX> &sm, const double *Lp, int ldl, TX *Xp, int ldx,
+                                            int ncols, int cstart = 0)
 {
     constexpr int RPG = RB / 8;  // rows per thread group (8 groups of 32 threads)
-    __shared__ TX Xs[RB][kPW + 1];
-    __shared__ TX Ls[32][kPW + 1];
-    __shared__ TX Ab[RB][33];
-    __shared__ TX Ld[32][33];
+    TX(&Xs)[RB][kPW + 1] = sm.Xs;
+    TX(&Ls)[32][kPW + 1] = sm.Ls;
+    TX(&Ab)[RB][33] = sm.Ab;
+    TX(&Ld)[32][33] = sm.Ld;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     for (int c0 = cstart; c0 < ncols; c0 += 32) {
         TX acc[RPG];
@@ -255,6 +316,13 @@ __device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, TX *Xp, int
     }
 }
 
+template <int RB, typename TX = double>
+__device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, TX *Xp, int ldx, int ncols, int cstart = 0)
+{
+    __shared__ TrsmSmem<RB, TX> sm;
+    trsm_rows_s<RB, TX>(sm, Lp, ldl, Xp, ldx, ncols, cstart);
+}
+
 // ---------------------------------------------------------------------------
 // C (64 x 64, row stride ldc) -= Am (64 x K) An (64 x K)^T with row strides
 // lda, ldb; the operands may be FP64 or FP32 and are converted to the
@@ -277,9 +345,9 @@ __device__ __forceinline__ GemmSmem<TC> &gemm_smem()
 }
 
 template <typename EA, typename EB, typename TC = double>
-__device__ __forceinline__ void gemm_sub64(const EA *Am, int lda, const EB *An, int ldb, int K, TC *C, int ldc)
+__device__ __forceinline__ void gemm_sub64_s(GemmSmem<TC> &sm, const EA *Am, int lda, const EB *An, int ldb, int K,
+                                             TC *C, int ldc)
 {
-    GemmSmem<TC> &sm = gemm_smem<TC>();
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     TC acc[4][4];
 #pragma unroll
@@ -311,6 +379,12 @@ __device__ __forceinline__ void gemm_sub64(const EA *Am, int lda, const EB *An, 
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) C[(size_t)(ty + 16 * i) * ldc + tx + 16 * j] -= acc[i][j];
+}
+
+template <typename EA, typename EB, typename TC = double>
+__device__ __forceinline__ void gemm_sub64(const EA *Am, int lda, const EB *An, int ldb, int K, TC *C, int ldc)
+{
+    gemm_sub64_s<EA, EB, TC>(gemm_smem<TC>(), Am, lda, An, ldb, K, C, ldc);
 }
 
 // Fixed-order tree reduction of one value per thread (any blockDim.x <= 1024).

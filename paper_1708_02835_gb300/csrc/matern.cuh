@@ -145,15 +145,51 @@ __device__ __forceinline__ double loc_dist(const egs_matern_params *__restrict__
     return 2.0 * Pp->radius * asin(sqrt(fmin(h, 1.0)));
 }
 
+// theta1 e^-x for x >= 0 by the table-driven method of P. T. P. Tang ("Table-
+// driven implementation of the exponential function in IEEE floating-point
+// arithmetic", ACM Trans. Math. Softw. 15, 1989): with k = rint(64 x / ln 2),
+// m = k >> 6, j = k & 63 and r = x - k ln2/64 (|r| <= ln2/128, Cody-Waite
+// reduction with a 36-bit high part of ln2/64, exact for k < 2^17),
+//   theta1 e^-x = 2^-m (theta1 2^(-j/64)) e^-r,
+// the table entry from the host (binary128, rounded once), e^-r - 1 by its
+// Taylor polynomial of degree 5 (truncation below 4e-17), and 2^-m applied to
+// the exponent field with integer operations.  About 10 FP64 operations,
+// within about one ulp; values below the smallest normal double give 0.
+__device__ __forceinline__ double th1_exp_neg(const egs_matern_params *__restrict__ Pp, double x)
+{
+    if (!(x < 708.0)) return x == x ? 0.0 : x;  // e^-708 is near the smallest normal; NaN stays NaN
+    constexpr double kInvLn2_64 = 92.332482616893656877;   // 64 / ln 2
+    constexpr double kShift = 6755399441055744.0;          // 1.5 * 2^52
+    constexpr double kLn2_64_hi = 0x1.62e42fefa0000p-7;    // ln2/64, 36 significant bits
+    constexpr double kLn2_64_lo = 0x1.cf79abc9e3b3ap-46;   // ln2/64 - kLn2_64_hi
+    const double t = fma(x, kInvLn2_64, kShift);           // k in the low bits of t
+    const double kd = t - kShift;
+    const int k = __double2loint(t);
+    double r = fma(-kd, kLn2_64_hi, x);
+    r = fma(-kd, kLn2_64_lo, r);
+    const double u = -r;
+    double p = fma(u, 1.0 / 120.0, 1.0 / 24.0);
+    p = fma(u, p, 1.0 / 6.0);
+    p = fma(u, p, 0.5);
+    p = fma(u, p, 1.0);
+    p *= u;                                                // e^u - 1
+    const double tj = Pp->exp_tab[k & (EGS_EXP_TAB - 1)];
+    const double v = fma(tj, p, tj);
+    const long long bits = __double_as_longlong(v);
+    const int m = k >> 6;
+    if ((int)((bits >> 52) & 0x7FF) - m <= 0) return 0.0;
+    return __longlong_as_double(bits - ((long long)m << 52));
+}
+
 // C(x * theta2) for x = r / theta2 >= 0.
 __device__ __forceinline__ double matern_eval(const egs_matern_params *__restrict__ Pp, double x)
 {
     const egs_matern_params &P = *Pp;
     if (x == 0.0) return P.th1;
     switch (P.kind) {
-    case EGS_MATERN_HALF: return P.th1 * exp(-x);
-    case EGS_MATERN_3HALF: return P.th1 * (1.0 + x) * exp(-x);
-    case EGS_MATERN_5HALF: return P.th1 * fma(x, fma(x, 1.0 / 3.0, 1.0), 1.0) * exp(-x);
+    case EGS_MATERN_HALF: return th1_exp_neg(Pp, x);
+    case EGS_MATERN_3HALF: return (1.0 + x) * th1_exp_neg(Pp, x);
+    case EGS_MATERN_5HALF: return fma(x, fma(x, 1.0 / 3.0, 1.0), 1.0) * th1_exp_neg(Pp, x);
     default: return matern_general(Pp, x);
     }
 }

@@ -16,7 +16,9 @@
  *    Temme 1975 and Thompson & Barnett, J. Comput. Phys. 64, 1986).  It needs
  *    q_k = (k + 1/2)^2 - mu^2 and C_k = prod_{j<=k} ((j - 1/2)^2 - mu^2) / j.
  *  - N upward steps of K_{m+1} = K_{m-1} + (2m/x) K_m (DLMF 10.29.1).
- * The Matern prefactor theta1 / (2^(nu-1) Gamma(nu)) is formed here as well.
+ * The Matern prefactor theta1 / (2^(nu-1) Gamma(nu)) is formed here as well,
+ * and the table theta1 2^(-j/64), j = 0..63, of the device's table-driven
+ * exponential (matern.cuh).
  */
 #define __STDC_WANT_IEC_60559_TYPES_EXT__
 #include <math.h>
@@ -90,5 +92,8 @@ int egs_matern_params_init(const double theta[3], egs_matern_params *P)
     }
     q_t g0 = 0.5f128;
     P->cf_q[0] = (double)(g0 * g0 - qmu * qmu);
+    /* theta1 2^(-j/64) for the table-driven exponential of the half-integer kinds */
+    for (int j = 0; j < EGS_EXP_TAB; ++j)
+        P->exp_tab[j] = (double)((q_t)theta[0] * exp2f128(-(q_t)j / (q_t)EGS_EXP_TAB));
     return 0;
 }

@@ -8,6 +8,7 @@
 
 #define EGS_TEMME_MAX 24 /* terms of Temme's series (x <= 1.25) */
 #define EGS_CF_MAX 140   /* depth of the backward recurrence (x > 1.25) */
+#define EGS_EXP_TAB 64   /* entries of the exponential's table (2^(j/64)) */
 
 /* distance between two locations */
 #define EGS_DIST_EUCLIDEAN 0    /* (x, y) in the plane */
@@ -41,6 +42,7 @@ typedef struct {
     double cf_q[EGS_CF_MAX + 2];    /* (k + 1/2)^2 - mu^2 */
     double cf_c[EGS_CF_MAX + 2];    /* C_k = prod_{j=1..k} ((j - 1/2)^2 - mu^2) / j, C_0 = 1 */
     double cf_ic[EGS_CF_MAX + 2];   /* 1 / C_k (unused when half_mu) */
+    double exp_tab[EGS_EXP_TAB];    /* theta1 2^(-j/64), j = 0..63: the table of theta1 e^-x */
 } egs_matern_params;
 
 #ifdef __cplusplus

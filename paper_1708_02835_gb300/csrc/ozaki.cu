@@ -10,27 +10,37 @@
 // each an integer of at most 8 bits times a power of two, so exact in BF16;
 // x = (sigma / 128) (q_1 + ... + q_5) up to 2^-36 sigma.  For a pair of rows
 //   x . y = s_x s_y sum_{i,j} q_i(x) . q_j(y)        (s = sigma / 128)
-// and the slice products are accumulated in FP32 on tcgen05 by level:
-//   acc0 = q_1 . q_1                  integers, |acc0| <= K 2^14 <= 2^23 (K <= 512)
-//   acc1 = q_1 . q_2 + q_2 . q_1      multiples of 2^-7, |acc1| <= 2^23 units
-//   acc2 = the 12 pairs with 4 <= i + j <= 6
-// so acc0 and acc1 are exact in FP32 (the tensor core adds exact BF16
+// and the slice products are accumulated in FP32 on tcgen05 by level
+// L = i + j (slices counted from 0), one accumulator per level:
+//   acc_0 = q_1 . q_1                 integers, |acc_0| <= K 2^14 <= 2^23 (K <= 512)
+//   acc_1 = q_1 . q_2 + q_2 . q_1     multiples of 2^-7, |acc_1| <= 2^23 units
+//   acc_2, acc_3, acc_4               the 12 pairs with 2 <= i + j <= 4
+// so acc_0 and acc_1 are exact in FP32 (the tensor core adds exact BF16
 // products; every partial sum is a representable integer multiple of the
-// level's unit below 2^24 units), and acc2 carries only a rounding error
-// relative to its own, 2^-14-smaller, magnitude.  The epilogue forms
-// acc0 + acc1 exactly as an FP32 pair (TwoSum), adds acc2 to the low part,
-// scales by the power of two s_x s_y on the exponents and subtracts the two
-// parts from the FP64 tile.  Dropping the pairs with i + j > 6 leaves
-// an error of about K 2^-35 s_x s_y 2^14, i.e. 35-bit products, which is the
-// accuracy the band updates need (FP32-accurate products there are not
-// enough; exact FP64 ones are).
+// level's unit below 2^24 units), and acc_2..acc_4 carry only rounding errors
+// relative to their own magnitudes, 2^-14 and less of the result.  The
+// epilogue forms acc_0 + acc_1 exactly as an FP32 pair (TwoSum), adds
+// (acc_4 + acc_3) + acc_2 to the low part, scales by the power of two
+// s_x s_y on the exponents and subtracts the two parts from the FP64 tile.
+// Dropping the pairs with i + j > 4 leaves an error of about
+// K 2^-35 s_x s_y 2^14, i.e. 35-bit products, which is the accuracy the band
+// updates need (FP32-accurate products there are not enough; exact FP64 ones
+// are).
+//
+// The 15 pair products of a K step are 5 MMAs: A slice i against the B
+// slices 0 .. 4 - i, which lie back to back in shared memory and so form one
+// operand of N = 32 (5 - i) rows; its D address is shifted by 32 i columns,
+// so that the column block of B slice j lands in the accumulator of level
+// i + j.  Each A slice is read from shared memory once per K step (instead of
+// once per pair).
 //
 // Kernel: persistent, one CTA per SM, 192 threads.  Warp 0 (one lane) loads
 // the five A slices (128 rows) and five B slices (32 rows) of a 64-element K
 // chunk with TMA (128-byte swizzle) into a 2-stage ring; warp 1 (one lane)
-// issues the 15 MMAs (M = 128, N = 32, K = 16) of every K step into three
-// 32-column TMEM accumulators, double-buffered across work items; warps 2-5
-// read the accumulators with tcgen05.ld and apply the FP64 epilogue.
+// issues the 5 MMAs (M = 128, N = 160 .. 32, K = 16) of every K step into the
+// five 32-column level accumulators, double-buffered across work items;
+// warps 2-5 read the accumulators with tcgen05.ld and apply the FP64
+// epilogue.
 #include "egs_internal.cuh"
 #include "slices.cuh"
 #include "tc_common.cuh"
@@ -48,8 +58,9 @@ constexpr int OA_SL = OBM * 128, OB_SL = OBN * 128;  // bytes of one slice box
 constexpr int OSTAGE = OS * (OA_SL + OB_SL);
 constexpr int OSMEM = OSTAGES * OSTAGE + 1024;
 constexpr int ONUM_THREADS = 192;
-constexpr uint32_t OTMEM_COLS = 256;  // 2 buffers x 3 accumulators x 32 columns, rounded up
-constexpr int NPAIRS = 15;
+constexpr int OLEV = OS;               // level accumulators (levels 0 .. 4)
+constexpr int OBUF = OLEV * OBN;       // TMEM columns of one accumulator buffer
+constexpr uint32_t OTMEM_COLS = 512;   // 2 buffers x 5 levels x 32 columns, rounded up
 
 __device__ __forceinline__ bool ofailed(const DevStatus *st)
 {
@@ -222,12 +233,10 @@ k_tc_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // slice pairs (a, b) and their accumulator: level 2, level 3, levels 4..6
-            constexpr int PA[NPAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
-            constexpr int PB[NPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
-            constexpr int PACC[NPAIRS] = {0, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2};
-            constexpr int PFIRST[NPAIRS] = {1, 1, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            constexpr uint32_t idesc = tc::idesc_f32acc(OBM, OBN, 1);
+            // A slice i against B slices 0 .. 4 - i: N = 32 (5 - i)
+            constexpr uint32_t idesc[OS] = {tc::idesc_f32acc(OBM, 5 * OBN, 1), tc::idesc_f32acc(OBM, 4 * OBN, 1),
+                                            tc::idesc_f32acc(OBM, 3 * OBN, 1), tc::idesc_f32acc(OBM, 2 * OBN, 1),
+                                            tc::idesc_f32acc(OBM, 1 * OBN, 1)};
             int g = 0, t = 0;
             for (int64_t item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
                 OzItem wi;
@@ -236,7 +245,7 @@ k_tc_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
                 const uint32_t use = (uint32_t)(t >> 1);
                 if (!tc::mbar_wait(&tempty[buf], (use & 1u) ^ 1u, &abort_flag)) break;
                 tc::tc_fence_after();
-                const uint32_t d = tbase + (uint32_t)buf * (3 * OBN);
+                const uint32_t d = tbase + (uint32_t)buf * OBUF;
                 for (int c = 0; c < kchunks; ++c, ++g) {
                     const int s = g % OSTAGES;
                     const uint32_t ph = (uint32_t)(g / OSTAGES) & 1u;
@@ -246,12 +255,13 @@ k_tc_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
                     const uint32_t b0 = a0 + OS * OA_SL;
 #pragma unroll
                     for (int j = 0; j < OKC / 16; ++j) {
+                        const uint64_t bd = tc::desc_sw128(b0 + 32 * j);
 #pragma unroll
-                        for (int p = 0; p < NPAIRS; ++p) {
-                            const uint64_t ad = tc::desc_sw128(a0 + PA[p] * OA_SL + 32 * j);
-                            const uint64_t bd = tc::desc_sw128(b0 + PB[p] * OB_SL + 32 * j);
-                            tc::mma_f16(d + (uint32_t)(PACC[p] * OBN), ad, bd, idesc,
-                                        ((c | j) != 0 || !PFIRST[p]) ? 1u : 0u);
+                        for (int i = 0; i < OS; ++i) {
+                            // the i = 0 MMA of the first K step covers all five
+                            // level blocks and so initialises them
+                            const uint64_t ad = tc::desc_sw128(a0 + i * OA_SL + 32 * j);
+                            tc::mma_f16(d + (uint32_t)(i * OBN), ad, bd, idesc[i], ((c | j) != 0 || i != 0) ? 1u : 0u);
                         }
                     }
                     tc::mma_commit(&empty[s]);
@@ -274,18 +284,24 @@ k_tc_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
             const bool ok = tc::mbar_wait(&tfull[buf], use & 1u, &abort_flag);
             tc::tc_fence_after();
             if (!__all_sync(0xffffffffu, ok && !abort_flag)) break;
-            const uint32_t d = tbase + (uint32_t)buf * (3 * OBN) + lane_base;
-            float a0v[32], a1v[32], a2v[32];
+            const uint32_t d = tbase + (uint32_t)buf * OBUF + lane_base;
+            float a0v[32], a1v[32], a2v[32], tv[32];
+            tc::tmem_ld32(d + 4 * OBN, a2v);
+            tc::tmem_ld32(d + 3 * OBN, tv);
+#pragma unroll
+            for (int c = 0; c < OBN; ++c) a2v[c] += tv[c];
+            tc::tmem_ld32(d + 2 * OBN, tv);
+#pragma unroll
+            for (int c = 0; c < OBN; ++c) a2v[c] += tv[c];
             tc::tmem_ld32(d, a0v);
             tc::tmem_ld32(d + OBN, a1v);
-            tc::tmem_ld32(d + 2 * OBN, a2v);
             tc::tc_fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&tempty[buf]);  // the accumulators are in registers now
-            // (acc0 + acc1) exactly as hi + e (Knuth's TwoSum in FP32), then
-            // lo = e + acc2 (rounded 2^-24 below acc2, itself 2^-14 below
-            // the result); the row scales are powers of two, applied to the
-            // exponents
+            // (acc_0 + acc_1) exactly as hi + e (Knuth's TwoSum in FP32), then
+            // lo = e + ((acc_4 + acc_3) + acc_2) (rounded 2^-24 below acc_2,
+            // itself 2^-14 below the result); the row scales are powers of
+            // two, applied to the exponents
             const int r = q * 32 + lane;
             const int ea = pow2_exp(scA[wi.ya + r]);
             int eb[OBN];

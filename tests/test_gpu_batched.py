@@ -1,10 +1,15 @@
 """Batched evaluation of uneven independent problems (FP64).
 
-Each problem's l must equal the single-problem egs_loglik_ex result bitwise
-(same tile size: the batch runs the same device routines in the same order)
-and the oracle within the FP64 bar 1e-10; a problem that is not positive
-definite is flagged without disturbing the others; a second run of the same
-plan replays the captured CUDA graph and gives identical values.
+FP64 batches run as one persistent launch over the tile-task graph of every
+problem.  Each problem's l must equal the single-problem egs_loglik_ex result
+bitwise (same tile size: the batch runs the same device routines in the same
+order on each tile) and the oracle within the FP64 bar 1e-10; a problem that
+is not positive definite is flagged without disturbing the others; a second
+run of the same plan replays the captured CUDA graph and gives identical
+values.  Failure detection: with a task's completion withheld, the dependency
+waits run out, the run reports EGS_ERR_TIMEOUT without hanging, and the next
+normal run of the same batch is correct.  The tile autotuner stores its choice
+where egs_batch(tile=0) finds it.
 """
 import numpy as np
 import pytest
@@ -36,11 +41,12 @@ def _problems():
     return out
 
 
-def test_batched_matches_single_and_oracle(egs):
+@pytest.mark.parametrize("tile", [64, 128, 192, 256])
+def test_batched_matches_single_and_oracle(egs, tile):
     from gpu_util import locs_dev, dev
     probs = _problems()
-    tile = 128
     B = egs.egs_batch([p[0] for p in probs], tile=tile)
+    assert B.tasks > 0                          # one persistent launch over the task graph
     dl = [locs_dev(p[2]) for p in probs]
     dz = [dev(p[3]) for p in probs]
     thetas = np.array([p[1] for p in probs])
@@ -53,7 +59,7 @@ def test_batched_matches_single_and_oracle(egs):
         assert abs(out[i] - ref) <= 1e-10 * max(1.0, abs(ref)), (i, out[i], ref)
     out2, _ = B.run(dl, dz, thetas)            # graph replay
     assert np.array_equal(out, out2)
-    assert 0 < B.launches < 2000
+    assert B.launches == 1
     # host inputs give the same values
     out3, _ = B.run([np.ascontiguousarray(p[2].reshape(-1)) for p in probs], [p[3] for p in probs], thetas)
     assert np.array_equal(out, out3)
@@ -96,4 +102,46 @@ def test_batched_fp32_mode_matches_oracle(egs):
     print("fp32 batch worst rel l %.2e" % worst)
     out2, _ = B.run(dl, dz, thetas)
     assert np.array_equal(out, out2)
+    B.close()
+
+
+def test_batched_wait_timeout_then_recovers(egs):
+    """The completion of one task (problem 0's first generated tile) is
+    withheld: the waits that need it run out after 2 ms, every CTA stops
+    claiming work, and the run returns EGS_ERR_TIMEOUT.  With the hook
+    removed, the same batch returns the values of a clean run."""
+    from gpu_util import locs_dev, dev
+    probs = _problems()
+    dl = [locs_dev(p[2]) for p in probs]
+    dz = [dev(p[3]) for p in probs]
+    thetas = np.array([p[1] for p in probs])
+    B = egs.egs_batch([p[0] for p in probs], tile=128)
+    want, _ = B.run(dl, dz, thetas)
+    B.set_wait_limit(2_000_000, withhold_task=0)
+    with pytest.raises(egs.EgsError) as e:
+        B.run(dl, dz, thetas)
+    assert e.value.status == egs.EGS_ERR_TIMEOUT
+    B.set_wait_limit(10_000_000_000, withhold_task=-1)
+    got, stat = B.run(dl, dz, thetas)
+    assert np.all(stat == 0) and np.array_equal(got, want)
+    B.close()
+
+
+def test_batch_autotuner_table(egs):
+    from gpu_util import locs_dev, dev
+    probs = _problems()
+    ns = [p[0] for p in probs]
+    dl = [locs_dev(p[2]) for p in probs]
+    dz = [dev(p[3]) for p in probs]
+    thetas = np.array([p[1] for p in probs])
+    best, ms = egs.egs_batch_autotune(ns, dl, dz, thetas, "fp64")
+    assert best in (64, 128, 256) and all(v > 0 for v in ms.values())
+    assert ms[best] == min(ms.values())
+    assert egs.egs_batch_tuned_tile(max(ns), "fp64") == best
+    B = egs.egs_batch(ns, tile=0)
+    assert B.tile == best
+    out, stat = B.run(dl, dz, thetas)
+    for i, (n, th, locs, z) in enumerate(probs):
+        ref = oracle.loglik(locs, z, th)["loglik"]
+        assert abs(out[i] - ref) <= 1e-10 * max(1.0, abs(ref))
     B.close()

@@ -77,6 +77,43 @@ def test_matern_tiles_elementwise(egs, theta):
     _lower_tiles_equal(got, want, rtol=tol)
 
 
+@pytest.mark.parametrize("prec,band", [("fp32", 2), ("tf32", 3), ("bf16", 2)])
+def test_matern_tiles_mixed_layout(egs, prec, band):
+    """The mixed-precision layout of egs_matern_tiles: band tiles (i - j <
+    band) as doubles at i * band + (i - j), the other tiles as floats at
+    (i - band)(i - band + 1) / 2 + j of the array that follows; doubles within
+    the FP64 element bar of the oracle, floats within one FP32 rounding of the
+    oracle's value (plus the same bar)."""
+    import torch
+    n, b, theta = 1000, 128, (1.0, 0.1, 1.3)
+    T = -(-n // b)
+    locs = ei.jittered_grid(n, seed=3)
+    want = oracle.tiles_lower(oracle.cov_matrix(locs, theta), b)
+    xs = _x_tiles(locs, theta[1], b)
+    nbytes = egs.egs_tiles_bytes(n, b, prec, band)
+    n64 = T * band                      # band slots per tile row (the first rows leave some unused)
+    assert nbytes == n64 * b * b * 8 + (T - band) * (T - band + 1) // 2 * b * b * 4
+    buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    from gpu_util import locs_dev
+    egs.egs_matern_tiles(locs_dev(locs), n, theta, b, buf, prec, band)
+    torch.cuda.synchronize()
+    raw = buf.cpu().numpy()
+    f64 = raw[: n64 * b * b * 8].view(np.float64).reshape(-1, b, b)
+    f32 = raw[n64 * b * b * 8:].view(np.float32).reshape(-1, b, b)
+    u = 2.0 ** -53
+    for i in range(T):
+        for j in range(i + 1):
+            t = i * (i + 1) // 2 + j
+            tol = 1e-13 + 4 * u * xs[t]
+            if i - j < band:
+                got = f64[i * band + (i - j)]
+                assert np.all(np.abs(got - want[t]) <= tol * np.abs(want[t]) + 1e-300), (i, j)
+            else:
+                r = i - band
+                got = f32[r * (r + 1) // 2 + j].astype(np.float64)
+                assert np.all(np.abs(got - want[t]) <= (2.0 ** -24 + tol) * np.abs(want[t]) + 1e-38), (i, j)
+
+
 def _spd_case(n, theta, seed=5):
     locs = ei.jittered_grid(n, seed=seed)
     S = oracle.cov_matrix(locs, theta)

@@ -56,7 +56,7 @@ def test_sizes_tiles_and_precisions():
     assert st == egs.EGS_ERR_ARG and "256" in msg
     assert _status(egs.egs_loglik_ex, LOCS, Z, GOOD, N, 9)[0] == egs.EGS_ERR_UNIMPLEMENTED
     assert _status(egs.egs_matern_tiles, LOCS, 0, GOOD, 64, np.zeros(4))[0] == egs.EGS_ERR_ARG
-    assert _status(egs.egs_matern_tiles, LOCS, N, GOOD, 64, np.zeros(4), "fp32")[0] == egs.EGS_ERR_UNIMPLEMENTED
+    assert _status(egs.egs_matern_tiles, LOCS, N, GOOD, 64, np.zeros(4), 9)[0] == egs.EGS_ERR_UNIMPLEMENTED
     assert _status(egs.egs_loglik_ind, LOCS, Z, GOOD, N, 64, 0)[0] == egs.EGS_ERR_ARG           # super_tiles = 0
     assert _status(egs.egs_loglik_ind, LOCS, Z, GOOD, N, 100, 1)[0] == egs.EGS_ERR_ARG
     z_new = np.zeros(4)
