@@ -59,9 +59,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=-1, help="steps of the end-to-end leg (default: = steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="config3",
-                    choices=["config3", "config2-mle", "config3-mle", "config4-batched", "config5-serve"],
+                    choices=["config3", "config2-mle", "config3-mle", "config4-batched", "config5-serve", "generate"],
                     help="config3 (default): one n=102,400 evaluation per step; the others are the "
-                         "MLE, batched and serving workloads")
+                         "MLE, batched and serving workloads, and the Matern generation alone")
+    ap.add_argument("--nprob", type=int, default=512, help="config4-batched: problems in the batch")
     ap.add_argument("--evals", type=int, default=50, help="config2-mle: likelihood evaluations")
     ap.add_argument("--requests", type=int, default=48, help="config5-serve: requests per arrival rate")
     ap.add_argument("--cpu-sample-n", type=int, default=8192,
@@ -320,7 +321,7 @@ def run_batched(a, egs):
     import numpy as np
     import torch
     import egs_inputs as ei
-    probs = ei.batched_problems(512)
+    probs = ei.batched_problems(a.nprob)
     ns = [p.n for p in probs]
     dl = [_to_dev(p.locations().reshape(-1)) for p in probs]
     dz = [_to_dev(p.e()) for p in probs]
@@ -363,11 +364,43 @@ def run_batched(a, egs):
     line = {"metric": "batched log-likelihood problems/s (config 4)", "value": r64["problems_per_s"],
             "unit": "problems/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": r64["ms_per_batch"],
             "higher_is_better": True, "dtype": "f64", "data": "synthetic (z ~ N(0, I))",
-            "config": {"workload": "512 problems, n ~ U{256..4096}, jittered grids on random sub-squares, own theta",
+            "config": {"workload": "%d problems, n ~ U{256..4096}, jittered grids on random sub-squares, own theta"
+                                   % a.nprob,
                        "tile": r64["tile"], "graph_kernels": r64["graph_kernels"]},
             "autotune_ms": r64["autotune_ms"], "potrf_tflops_equiv": r64["potrf_tflops_equiv"],
             "roofline": r64["roofline"], "persistent_tasks": r64["persistent_tasks"],
             "not_pd": r64["failed"], "fp32_off_band": r32}
+    print(json.dumps(line), flush=True)
+
+
+def run_generate(a, egs):
+    """Sigma(theta) alone (Eq. 2; egs_matern_tiles, FP64 lower tiles) on the
+    n-point jittered grid: Matern values per second and bytes written, CUDA
+    events on the launching stream."""
+    import numpy as np
+    import torch
+    import egs_inputs as ei
+    theta = tuple(float(v) for v in a.theta.split(","))
+    n, tile = a.n, a.tile
+    dl = _to_dev(ei.jittered_grid(n, seed=0).reshape(-1))
+    buf = torch.empty(egs.egs_tiles_bytes(n, tile) // 8, dtype=torch.float64, device="cuda")
+    for _ in range(a.warmup):
+        egs.egs_matern_tiles(dl, n, theta, tile, buf)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        egs.egs_matern_tiles(dl, n, theta, tile, buf)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    T = -(-n // tile)
+    vals = T * (T + 1) / 2 * tile * tile
+    line = {"metric": "Matern generation values/s", "value": vals / (ms / 1e3), "unit": "values/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "n=%d jittered grid, theta=(%s), tile %d, FP64 lower tiles"
+                                                        % (n, a.theta, tile)},
+            "bytes_written_gb_s": vals * 8 / (ms / 1e3) / 1e9}
     print(json.dumps(line), flush=True)
 
 
@@ -492,7 +525,7 @@ def main():
         torch.cuda.set_device(local)
         egs.load_library()
         {"config2-mle": run_mle, "config3-mle": run_mle, "config4-batched": run_batched,
-         "config5-serve": run_serve}[a.workload](a, egs)
+         "config5-serve": run_serve, "generate": run_generate}[a.workload](a, egs)
         return
 
     import numpy as np

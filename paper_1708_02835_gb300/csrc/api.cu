@@ -69,6 +69,10 @@ static Layout make_layout(const TileGeom &g)
     off += align256((size_t)2 * g.T * sizeof(double));
     L.status = off;
     off += align256(sizeof(DevStatus));
+    L.mtab = off;
+    off += align256(EGS_MT_DOUBLES * sizeof(double));
+    L.pctr = off;
+    off += align256((size_t)g.T * potrf_diag_scratch_words(g.b) * sizeof(unsigned));
     L.total = off;
     return L;
 }
@@ -97,7 +101,7 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
     L.l32 = off;
     off += align256(bb * sizeof(float));
     L.wsp = off;
-    if (mix_fmt(p) == 3) off += align256(3 * bb * sizeof(float));
+    if (mix_fmt(p) == 3) off += align256(2 * bb * sizeof(float));
     L.vinv = off;
     off += align256((size_t)g.T * bb * sizeof(double));
     L.locs = off;
@@ -112,6 +116,12 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
     off += align256(sizeof(DevStatus));
     L.err = off;
     off += 256;
+    L.mtab = off;
+    off += align256(EGS_MT_DOUBLES * sizeof(double));
+    L.pctr = off;
+    off += align256((size_t)g.T * potrf_diag_scratch_words(g.b) * sizeof(unsigned));
+    L.rs = off;
+    off += 2 * align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(float));
     L.total = off;
     return L;
 }
@@ -204,6 +214,10 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
         mb.cols = v + 6 * stride;
         mb.partials = (double *)(ws + ML.partials);
         mb.err = (int *)(ws + ML.err);
+        mb.mtab = (double *)(ws + ML.mtab);
+        mb.pctr = (unsigned *)(ws + ML.pctr);
+        for (int i = 0; i < 2; ++i)
+            mb.rs[i] = (float *)(ws + ML.rs + i * align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(float)));
         mb.l32 = (float *)(ws + ML.l32);
         mb.wsp = (float *)(ws + ML.wsp);
         mb.vinv = (double *)(ws + ML.vinv);
@@ -220,10 +234,10 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
     double *zpad = (double *)(ws + es.L.zpad);
     double *partials = (double *)(ws + es.L.partials);
     if (ev) cudaEventRecord(ev[0], s);
-    cudaError_t e = launch_matern_tiles_f64(dlocs, dlocs + n, g, es.P, tiles, s, kt);
+    cudaError_t e = launch_matern_tiles_f64(dlocs, dlocs + n, g, es.P, tiles, s, kt, (double *)(ws + es.L.mtab));
     if (e == cudaSuccess) {
         if (ev) cudaEventRecord(ev[1], s);
-        e = launch_potrf_tiles_f64(tiles, g, st, s, kt);
+        e = launch_potrf_tiles_f64(tiles, g, st, s, kt, (unsigned *)(ws + es.L.pctr));
     }
     if (e == cudaSuccess) {
         if (ev) cudaEventRecord(ev[2], s);
@@ -336,16 +350,21 @@ egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3]
     egs_matern_params_init(theta, &P);
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
     if (band <= 0) band = 2;
-    cudaError_t e;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *tab = nullptr;  // the general-nu local polynomials (stream-ordered scratch)
+    cudaError_t e = cudaSuccess;
+    if (P.kind == EGS_MATERN_GENERAL) e = cudaMallocAsync((void **)&tab, EGS_MT_DOUBLES * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_error(e, "egs_matern_tiles scratch");
     if (p == EGS_FP64 || g.T <= band) {
-        e = launch_matern_tiles_f64(locs, locs + n, g, P, (double *)tiles, (cudaStream_t)stream);
+        e = launch_matern_tiles_f64(locs, locs + n, g, P, (double *)tiles, s, nullptr, tab);
     } else {
         // band tiles as doubles, then the off-band tiles as floats right after them
         double *f64 = (double *)tiles;
         float *f32 = (float *)(f64 + Tiles::f64_tiles(g.T, band) * g.tile_elems());
         const Tiles tl{f64, f32, g.b, g.T, band};
-        e = launch_matern_tiles(locs, locs + n, n, tl, P, nullptr, (cudaStream_t)stream, nullptr);
+        e = launch_matern_tiles(locs, locs + n, n, tl, P, nullptr, s, nullptr, tab);
     }
+    if (tab) cudaFreeAsync(tab, s);
     if (e != cudaSuccess) return cuda_error(e, "egs_matern_tiles launch");
     return EGS_OK;
 }
@@ -360,15 +379,17 @@ egs_status egs_potrf_tiles(void *tiles, int64_t n, int32_t tile, int64_t *fail_i
     cudaStream_t s = (cudaStream_t)stream;
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
     DevStatus *st = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&st, sizeof(DevStatus), s);
+    const size_t sbytes = align256(sizeof(DevStatus));
+    cudaError_t e = cudaMallocAsync((void **)&st, sbytes + (size_t)g.T * potrf_diag_scratch_words(g.b) * sizeof(unsigned), s);
     if (e != cudaSuccess) return cuda_error(e, "egs_potrf_tiles workspace");
     status_init(st, s);
-    e = launch_potrf_tiles_f64((double *)tiles, g, st, s);
+    e = launch_potrf_tiles_f64((double *)tiles, g, st, s, nullptr, (unsigned *)((char *)st + sbytes));
     DevStatus h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(st, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "egs_potrf_tiles");
+    if (h.timeout) return set_error(EGS_ERR_TIMEOUT, "egs_potrf_tiles: a dependency wait of the diagonal POTRF timed out");
     const int64_t fi = (h.fail_index == kNoFail) ? -1 : (int64_t)h.fail_index;
     if (fail_index) *fail_index = fi;
     if (fi >= 0) return set_error(EGS_ERR_NOT_PD, "not positive definite at row %lld", (long long)fi);
@@ -463,7 +484,7 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
         for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
     }
     if (e != cudaSuccess) return cuda_error(e, "egs_loglik");
-    if (herr) return set_error(EGS_ERR_TIMEOUT, "egs_loglik: a tensor-core pipeline wait timed out");
+    if (herr || h.timeout) return set_error(EGS_ERR_TIMEOUT, "egs_loglik: a bounded device wait timed out");
     if (info) {
         fill_info(es, h, info);
         info->launches = kt.launches;
@@ -522,9 +543,9 @@ egs_status egs_simulate(const double *locs, const double *e, const double theta[
     if (err == cudaSuccess) err = cudaMallocAsync((void **)&zfull, (size_t)g.T * g.b * sizeof(double), s);
     if (err == cudaSuccess) {
         status_init(st, s);
-        err = launch_matern_tiles_f64(dlocs, dlocs + n, g, es.P, tiles, s);
+        err = launch_matern_tiles_f64(dlocs, dlocs + n, g, es.P, tiles, s, nullptr, (double *)(ws + es.L.mtab));
     }
-    if (err == cudaSuccess) err = launch_potrf_tiles_f64(tiles, g, st, s);
+    if (err == cudaSuccess) err = launch_potrf_tiles_f64(tiles, g, st, s, nullptr, (unsigned *)(ws + es.L.pctr));
     if (err == cudaSuccess) err = launch_pad_vector(de, n, epad, (int64_t)g.T * g.b, s);
     if (err == cudaSuccess) err = launch_trmv_lower(tiles, g, epad, zfull, st, s);
     if (err == cudaSuccess) err = cudaMemcpyAsync(z, zfull, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -534,6 +555,7 @@ egs_status egs_simulate(const double *locs, const double *e, const double theta[
     cudaFreeAsync(ws, s);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) return cuda_error(err, "egs_simulate");
+    if (h.timeout) return set_error(EGS_ERR_TIMEOUT, "egs_simulate: a bounded device wait timed out");
     if (h.fail_index != kNoFail)
         return set_error(EGS_ERR_NOT_PD, "egs_simulate: not positive definite at row %lld",
                          (long long)h.fail_index);

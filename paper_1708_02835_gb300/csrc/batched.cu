@@ -55,18 +55,46 @@ __device__ __forceinline__ int band_rows(const BatchProblem &p, int k)
     return p.band - 1 < r ? p.band - 1 : r;
 }
 
+// Local polynomials of the general-nu problems (blockIdx.y = problem).
+__global__ void __launch_bounds__(256) kb_table(const BatchProblem *probs)
+{
+    const BatchProblem &pr = probs[blockIdx.y];
+    __shared__ egs_matern_params Ps;
+    __shared__ double vals[8][EGS_MT_NC];
+    const double *s = reinterpret_cast<const double *>(pr.P);
+    double *d = reinterpret_cast<double *>(&Ps);
+    for (int i = threadIdx.x; i < (int)(sizeof(egs_matern_params) / sizeof(double)); i += blockDim.x) d[i] = s[i];
+    __syncthreads();
+    if (Ps.kind != EGS_MATERN_GENERAL) return;
+    const int w = threadIdx.x >> 5, iv = (int)blockIdx.x * 8 + w;
+    if (iv < EGS_MT_OCT * EGS_MT_SUB) matern_table_interval(&Ps, iv, pr.mtab, vals[w]);
+}
+
+cudaError_t launch_batch_tables(const BatchProblem *probs, int nprob, cudaStream_t s)
+{
+    kb_table<<<dim3((EGS_MT_OCT * EGS_MT_SUB + 7) / 8, (unsigned)nprob), 256, 0, s>>>(probs);
+    return cudaGetLastError();
+}
+
 // Matern tiles: item = (tile, 64 x 64 sub-block).
 __global__ void __launch_bounds__(256) kb_gen(BatchArgs a)
 {
     int64_t local;
     const BatchProblem &pr = a.probs[find_problem(a, blockIdx.x, local)];
     __shared__ egs_matern_params Ps;
+    __shared__ double Ts[EGS_MT_DOUBLES];
     {
         const double *s = reinterpret_cast<const double *>(pr.P);
         double *d = reinterpret_cast<double *>(&Ps);
         for (int i = threadIdx.x; i < (int)(sizeof(egs_matern_params) / sizeof(double)); i += blockDim.x) d[i] = s[i];
         __syncthreads();
     }
+    const bool general = Ps.kind == EGS_MATERN_GENERAL;
+    if (general) {
+        for (int i = threadIdx.x; i < EGS_MT_DOUBLES; i += blockDim.x) Ts[i] = pr.mtab[i];
+        __syncthreads();
+    }
+    const double *Tab = general ? Ts : nullptr;
     const int b = a.b, nsub = b >> 6;
     const int64_t t = local / (nsub * nsub);
     const int sub = (int)(local % (nsub * nsub));
@@ -89,7 +117,7 @@ __global__ void __launch_bounds__(256) kb_gen(BatchArgs a)
         if (gi >= n || gj >= n) v = (gi == gj) ? 1.0 : 0.0;
         else if (gi == gj) v = Ps.th1;
         else {
-            v = matern_eval(&Ps, loc_dist(&Ps, pr.X[gi], pr.Y[gi], xj, yj) * Ps.inv_th2);
+            v = matern_eval(&Ps, loc_dist(&Ps, pr.X[gi], pr.Y[gi], xj, yj) * Ps.inv_th2, Tab);
         }
         const size_t off = (size_t)r * b + sc * 64 + tx;
         if (is64) tile[off] = v;
@@ -536,15 +564,17 @@ void plan_launches(egs_batch *B, std::vector<int64_t> &prefix)
 
 cudaError_t enqueue_all(egs_batch *B, cudaStream_t s)
 {
+    cudaError_t et = launch_batch_tables(B->d_probs, B->nprob, s);
+    if (et != cudaSuccess) return et;
     if (B->dag) {
         cudaError_t e = cudaMemsetAsync(B->d_cnt, 0, B->ncnt * sizeof(unsigned), s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(B->d_ctl, B->h_ctl, sizeof(DagCtl), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = dag_enqueue(B->d_tasks, B->ntasks, B->d_probs, B->d_ctl, B->b, B->grid, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(B->h_ctl + 1, B->d_ctl, sizeof(DagCtl), cudaMemcpyDeviceToHost, s);
-        B->launches_per_run = 1;
+        B->launches_per_run = 2;  // the local polynomials, then the persistent launch
         return e;
     }
-    int count = 0;
+    int count = 1;
     for (const auto &L : B->launches) {
         if (L.items <= 0) continue;
         BatchArgs a{B->d_probs, B->d_prefix + L.prefix_off, B->nprob, B->b};
@@ -601,7 +631,7 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
     B->mixed = (p == EGS_MIX_FP32);
     size_t off = 0;
     std::vector<size_t> tiles_off(nprob), zpad_off(nprob), part_off(nprob), f32_off(nprob), sig_off(nprob),
-        vec_off(nprob);
+        vec_off(nprob), mtab_off(nprob);
     size_t in_doubles = 0;
     for (int i = 0; i < nprob; ++i) {
         if (n[i] < 1) {
@@ -625,6 +655,8 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
         off += a256(npad * sizeof(double));
         part_off[i] = off;
         off += a256((size_t)2 * T * sizeof(double));
+        mtab_off[i] = off;
+        off += a256(EGS_MT_DOUBLES * sizeof(double));
         B->in_off.push_back(in_doubles);
         in_doubles += (size_t)3 * n[i];
     }
@@ -717,6 +749,7 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
         pr.st = B->d_status + i;
         pr.P = B->d_params + i;
         pr.cnt = B->dag ? B->d_cnt + cnt_off[i] : nullptr;
+        pr.mtab = (double *)(B->ws + mtab_off[i]);
     }
     e = cudaMemcpy(B->d_probs, B->h_probs, sizeof(BatchProblem) * nprob, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

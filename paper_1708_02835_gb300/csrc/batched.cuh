@@ -19,6 +19,11 @@ struct BatchProblem {
     DevStatus *st;
     const egs_matern_params *P;
     unsigned *cnt;     // persistent scheduler: T(T+1)/2 tile counters, then T vector-block counters
+    double *mtab;      // EGS_MT_DOUBLES: the generator's local polynomials (general nu)
 };
+
+// The local polynomials of every general-nu problem of a batch: grid =
+// (ceil(intervals / 8), nprob), one warp per sub-interval (batched.cu).
+cudaError_t launch_batch_tables(const BatchProblem *probs, int nprob, cudaStream_t s);
 
 }  // namespace egs

@@ -55,12 +55,19 @@ struct TrsvSmem {
 };
 
 // The tasks' shared memory, overlaid: one task runs at a time in a CTA.
+struct GenSmem {
+    egs_matern_params P;
+    double T[EGS_MT_DOUBLES];
+};
+
 union DagSmem {
     TrsmSmem<64, double> trsm;
-    Potrf64Smem potrf;
+    TrsmSmem<32, double> trsm32;
+    PotrfSmem<32> potrf32;
     GemmSmem<double> gemm;
+    Gemm32Smem gemm32;
     TrsvSmem trsv;
-    egs_matern_params P;
+    GenSmem gen;
     double vec[256];
 };
 
@@ -176,14 +183,21 @@ __device__ __forceinline__ void dag_gemv_rows(const double *A, int b, int r0, co
     }
 }
 
-__device__ void task_gen(egs_matern_params &Ps, const BatchProblem &pr, int b, int ti, int tj)
+__device__ void task_gen(GenSmem &gs, const BatchProblem &pr, int b, int ti, int tj)
 {
+    egs_matern_params &Ps = gs.P;
     {
         const double *s = reinterpret_cast<const double *>(pr.P);
         double *d = reinterpret_cast<double *>(&Ps);
         for (int i = threadIdx.x; i < (int)(sizeof(egs_matern_params) / sizeof(double)); i += blockDim.x) d[i] = s[i];
         __syncthreads();
     }
+    const bool general = Ps.kind == EGS_MATERN_GENERAL;
+    if (general) {
+        for (int i = threadIdx.x; i < EGS_MT_DOUBLES; i += blockDim.x) gs.T[i] = pr.mtab[i];
+        __syncthreads();
+    }
+    const double *Tab = general ? gs.T : nullptr;
     const int nsub = b >> 6, tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
     const int64_t n = pr.n;
     double *tile = pr.tiles + (size_t)tile_linear(ti, tj) * b * b;
@@ -197,7 +211,7 @@ __device__ void task_gen(egs_matern_params &Ps, const BatchProblem &pr, int b, i
             double v;
             if (gi >= n || gj >= n) v = (gi == gj) ? 1.0 : 0.0;
             else if (gi == gj) v = Ps.th1;
-            else v = matern_eval(&Ps, loc_dist(&Ps, pr.X[gi], pr.Y[gi], xj, yj) * Ps.inv_th2);
+            else v = matern_eval(&Ps, loc_dist(&Ps, pr.X[gi], pr.Y[gi], xj, yj) * Ps.inv_th2, Tab);
             tile[(size_t)r * b + sc * 64 + tx] = v;
         }
     }
@@ -208,33 +222,31 @@ __device__ void task_gen(egs_matern_params &Ps, const BatchProblem &pr, int b, i
         }
 }
 
-// Blocked POTRF of diagonal tile k in one CTA: the sub-panel steps of
-// launch_potrf_diag (POTRF of a 64 x 64 block, the solve of the rows below
-// it, the update of the trailing lower part) in the same order and with the
-// same per-element arithmetic (the row solves and the products do not depend
-// on how the rows are grouped into blocks).  The trailing update runs on
-// 64 x 64 blocks, whose upper part of diagonal blocks is overwritten by a
-// later sub-panel's zeroing.
+// POTRF of diagonal tile k in one CTA: the 32 x 32 block operations of the
+// single-problem diagonal POTRF (chol64.cu) run in its task order -- for each
+// block column p, POTRF of block (p, p) (and the zeros right of it), the
+// 32-row solves below it, then the updates of the trailing blocks -- so every
+// element sees the same operations in the same order and the factor is the
+// single evaluation's bit for bit.
 __device__ void task_potrf(DagSmem &sm, const BatchProblem &pr, int b, int k)
 {
     double *A = pr.tiles + (size_t)tile_linear(k, k) * b * b;
-    for (int p = 0; p < b; p += kIB) {
-        double *Ap = A + (size_t)p * b + p;
-        if (!potrf64_smem_s(sm.potrf, Ap, b, (int64_t)k * b + p, pr.st)) return;
-        for (int e = threadIdx.x; e < kIB * (b - p - kIB); e += 256) {
-            const int r = e / (b - p - kIB), c = e % (b - p - kIB);
-            Ap[(size_t)r * b + kIB + c] = 0.0;
+    const int nb = b >> 5;
+    for (int p = 0; p < nb; ++p) {
+        double *Ap = A + (size_t)p * 32 * b + p * 32;
+        if (!potrf_smem_s<32>(sm.potrf32, Ap, b, (int64_t)k * b + p * 32, pr.st)) return;
+        for (int e = threadIdx.x; e < 32 * (b - p * 32 - 32); e += 256) {
+            const int r = e / (b - p * 32 - 32), c = e % (b - p * 32 - 32);
+            Ap[(size_t)r * b + 32 + c] = 0.0;
         }
         __syncthreads();
-        const int n64 = (b - p - kIB) / 64, q = p + kIB;
-        for (int blk = 0; blk < n64; ++blk) trsm_rows_s<64>(sm.trsm, Ap, b, A + (size_t)(q + 64 * blk) * b + p, b, kIB);
-        for (int bi = 0; bi < n64; ++bi)
-            for (int bj = 0; bj <= bi; ++bj) {
-                const int ri = q + 64 * bi, rj = q + 64 * bj;
-                gemm_sub64_s(sm.gemm, A + (size_t)ri * b + p, b, A + (size_t)rj * b + p, b, kIB,
-                             A + (size_t)ri * b + rj, b);
+        for (int m = p + 1; m < nb; ++m) trsm_rows_s<32>(sm.trsm32, Ap, b, A + (size_t)m * 32 * b + p * 32, b, 32);
+        for (int m = p + 1; m < nb; ++m)
+            for (int n = p + 1; n <= m; ++n) {
+                gemm_sub32_s(sm.gemm32, A + (size_t)m * 32 * b + p * 32, b, A + (size_t)n * 32 * b + p * 32, b, 32,
+                             A + (size_t)m * 32 * b + n * 32, b);
+                __syncthreads();
             }
-        __syncthreads();
     }
 }
 
@@ -376,7 +388,7 @@ __global__ void __launch_bounds__(256, 2) kb_dag(DagArgs a)
         if (!s_go) return;
         if (!s_skip || type == D_FINAL) {
             switch (type) {
-            case D_GEN: task_gen(sm.P, pr, a.b, i, j); break;
+            case D_GEN: task_gen(sm.gen, pr, a.b, i, j); break;
             case D_POTRF: task_potrf(sm, pr, a.b, k); break;
             case D_TRSM: task_trsm(sm, pr, a.b, i, k); break;
             case D_UPDATE: task_update(sm, pr, a.b, i, j, k); break;

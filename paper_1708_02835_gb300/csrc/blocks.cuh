@@ -123,23 +123,27 @@ __device__ __forceinline__ bool potrf_block(double *A, int nb, int ld, int64_t r
 // CTA barriers, and its FP64 work is mostly independent FMAs.  Same failure
 // reporting as potrf_block; the strict upper triangle is zeroed.
 // ---------------------------------------------------------------------------
-struct Potrf64Smem {
-    double S[64][65];
+template <int NB>
+struct PotrfSmem {
+    double S[NB][NB + 1];
     int fail_j;
 };
+using Potrf64Smem = PotrfSmem<64>;
 
-__device__ __forceinline__ bool potrf64_smem_s(Potrf64Smem &sm, double *A, int ld, int64_t row0, DevStatus *st)
+// NB x NB block (NB = 32 or 64), as described above.
+template <int NB>
+__device__ __forceinline__ bool potrf_smem_s(PotrfSmem<NB> &sm, double *A, int ld, int64_t row0, DevStatus *st)
 {
-    double(&S)[64][65] = sm.S;
+    double(&S)[NB][NB + 1] = sm.S;
     int &fail_j = sm.fail_j;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) fail_j = -1;
-    for (int e = tid; e < 64 * 64; e += 256) {
-        const int i = e >> 6, j = e & 63;
+    for (int e = tid; e < NB * NB; e += 256) {
+        const int i = e / NB, j = e % NB;
         S[i][j] = (j <= i) ? A[(size_t)i * ld + j] : 0.0;
     }
     __syncthreads();
-    for (int p0 = 0; p0 < 64; p0 += kPW) {
+    for (int p0 = 0; p0 < NB; p0 += kPW) {
         // 1. the 16 x 16 diagonal block, column by column, by warp 0 (lane i < 16 owns row p0 + i)
         if (tid < 32) {
             for (int j = 0; j < kPW; ++j) {
@@ -171,7 +175,7 @@ __device__ __forceinline__ bool potrf64_smem_s(Potrf64Smem &sm, double *A, int l
         }
         const int q0 = p0 + kPW;
         // 2. rows below the panel: x L_pp^T = row, one thread per row
-        if (tid < 64 - q0) {
+        if (tid < NB - q0) {
             const int i = q0 + tid;
             double x[kPW];
 #pragma unroll
@@ -185,8 +189,8 @@ __device__ __forceinline__ bool potrf64_smem_s(Potrf64Smem &sm, double *A, int l
             for (int j = 0; j < kPW; ++j) S[i][p0 + j] = x[j];
         }
         __syncthreads();
-        // 3. rank-16 update of the trailing lower triangle (rows and columns q0..63)
-        const int m = 64 - q0;
+        // 3. rank-16 update of the trailing lower triangle (rows and columns q0..NB-1)
+        const int m = NB - q0;
         for (int e = tid; e < m * m; e += 256) {
             const int i = q0 + e / m, l = q0 + e % m;
             if (l <= i) {
@@ -198,11 +202,16 @@ __device__ __forceinline__ bool potrf64_smem_s(Potrf64Smem &sm, double *A, int l
         }
         __syncthreads();
     }
-    for (int e = tid; e < 64 * 64; e += 256) {
-        const int i = e >> 6, j = e & 63;
+    for (int e = tid; e < NB * NB; e += 256) {
+        const int i = e / NB, j = e % NB;
         A[(size_t)i * ld + j] = (j <= i) ? S[i][j] : 0.0;
     }
     return true;
+}
+
+__device__ __forceinline__ bool potrf64_smem_s(Potrf64Smem &sm, double *A, int ld, int64_t row0, DevStatus *st)
+{
+    return potrf_smem_s<64>(sm, A, ld, row0, st);
 }
 
 __device__ __forceinline__ bool potrf64_smem(double *A, int ld, int64_t row0, DevStatus *st)
@@ -216,11 +225,17 @@ __device__ __forceinline__ bool potrf64_smem(double *A, int ld, int64_t row0, De
 // thread (rows ty + 16 i, columns tx + 16 j).  FP64 or FP32 operands, FP64
 // arithmetic.  256 threads.
 // ---------------------------------------------------------------------------
+struct Gemm32Smem {
+    double As[kPW][33];
+    double Bs[kPW][33];
+};
+
 template <typename EA, typename EB>
-__device__ __forceinline__ void gemm_sub32(const EA *Am, int lda, const EB *An, int ldb, int K, double *C, int ldc)
+__device__ __forceinline__ void gemm_sub32_s(Gemm32Smem &sm, const EA *Am, int lda, const EB *An, int ldb, int K,
+                                             double *C, int ldc)
 {
-    __shared__ double As[kPW][33];
-    __shared__ double Bs[kPW][33];
+    double(&As)[kPW][33] = sm.As;
+    double(&Bs)[kPW][33] = sm.Bs;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
     for (int p = 0; p < K; p += kPW) {
@@ -244,6 +259,13 @@ __device__ __forceinline__ void gemm_sub32(const EA *Am, int lda, const EB *An, 
     for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 2; ++j) C[(size_t)(ty + 16 * i) * ldc + tx + 16 * j] -= acc[i][j];
+}
+
+template <typename EA, typename EB>
+__device__ __forceinline__ void gemm_sub32(const EA *Am, int lda, const EB *An, int ldb, int K, double *C, int ldc)
+{
+    __shared__ Gemm32Smem sm;
+    gemm_sub32_s(sm, Am, lda, An, ldb, K, C, ldc);
 }
 
 // ---------------------------------------------------------------------------

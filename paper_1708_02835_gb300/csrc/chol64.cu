@@ -7,10 +7,9 @@
 // SYRK and GEMM share one kernel (a diagonal output tile skips its upper
 // sub-blocks).
 //
-// The diagonal POTRF is itself blocked: 64-wide sub-panels, each factored by
-// one CTA, with the rows below solved and the trailing part of the tile
-// updated by many CTAs, so that the factorisation's critical path uses many
-// SMs instead of one.
+// The diagonal POTRF is itself blocked: one launch runs the task graph of the
+// tile's 32 x 32 blocks on a few dozen CTAs, so that the factorisation's
+// critical path uses many SMs instead of one.
 //
 // GB300's FP64 rate is 2 DFMA per clock per SM (about 1.2 TFLOP/s for the
 // chip), so these kernels are FP64-pipe bound whatever their memory traffic:
@@ -22,46 +21,6 @@
 namespace egs {
 
 // ---- kernels --------------------------------------------------------------
-
-// POTRF of the 64 x 64 sub-block at offset p of diagonal tile k; also zeroes
-// rows p..p+63 to the right of the sub-block, so that once every sub-panel is
-// done the tile holds L exactly (zero strict upper triangle).
-__global__ void __launch_bounds__(256) k_potrf_sub(Tiles tl, int k, int p, DevStatus *st)
-{
-    if (failed(st)) return;
-    const int b = tl.b;
-    double *A = tl.t64(k, k) + (size_t)p * b + p;
-    if (!potrf64_smem(A, b, (int64_t)k * b + p, st)) return;
-    for (int e = threadIdx.x; e < kIB * (b - p - kIB); e += 256) {
-        const int r = e / (b - p - kIB), c = e % (b - p - kIB);
-        A[(size_t)r * b + kIB + c] = 0.0;
-    }
-}
-
-// Inside diagonal tile k: rows p + 64 + 16 * blockIdx.x solve against the
-// factored 64 x 64 sub-block at p (16 rows per CTA: more SMs on the chain).
-__global__ void __launch_bounds__(256) k_trsm_sub(Tiles tl, int k, int p, DevStatus *st)
-{
-    if (failed(st)) return;
-    const int b = tl.b;
-    double *A = tl.t64(k, k);
-    const int r0 = p + kIB + 16 * (int)blockIdx.x;
-    trsm_rows<16>(A + (size_t)p * b + p, b, A + (size_t)r0 * b + p, b, kIB);
-}
-
-// Inside diagonal tile k: rank-64 update of the trailing lower part after
-// sub-panel p, in 32 x 32 blocks (bi >= bj).
-__global__ void __launch_bounds__(256) k_syrk_sub(Tiles tl, int k, int p, DevStatus *st)
-{
-    if (failed(st)) return;
-    const int b = tl.b;
-    double *A = tl.t64(k, k);
-    int bi, bj;
-    tri_decode((int64_t)blockIdx.x, bi, bj);
-    const int q = p + kIB;
-    const int ri = q + 32 * bi, rj = q + 32 * bj;
-    gemm_sub32(A + (size_t)ri * b + p, b, A + (size_t)rj * b + p, b, kIB, A + (size_t)ri * b + rj, b);
-}
 
 // TRSM on the panel below tile k: rows m = k+1+blockIdx.x, RB rows per CTA.
 template <int RB>
@@ -91,18 +50,150 @@ __global__ void __launch_bounds__(256) k_update_f64(Tiles tl, int k, DevStatus *
                tl.t64(m, nc) + (size_t)sr * 64 * b + sc * 64, b);
 }
 
-cudaError_t launch_potrf_diag(const Tiles &tl, int k, DevStatus *st, cudaStream_t s, KernelTimer *kt)
+// ---- the diagonal-tile POTRF as one launch --------------------------------
+//
+// POTRF of diagonal tile k is a task graph on the nb x nb grid of its
+// 32 x 32 blocks (nb = b / 32):
+//   POTRF(p)       block (p, p), after its p updates; zeroes row block p right of it
+//   TRSM(m, p)     block (m, p) against L_pp, after POTRF(p) and its p updates
+//   UPDATE(m,n,p)  block (m, n) -= (m, p) (n, p)^T, after TRSM(m, p), TRSM(n, p)
+//                  and updates 0 .. p-1 of (m, n)
+// One launch of a few dozen CTAs runs it: each CTA claims the next task in
+// this (topological) order from a counter and waits -- bounded, 2 s -- until
+// the block counters it needs reach their values (block (i, j) counts one
+// per update applied and one when final).  With 32-wide blocks the critical
+// path of a sub-panel (POTRF, one 32-row solve, one 32 x 32 x 32 update) is
+// short, and the many updates of early sub-panels spread over the CTAs.  The
+// 32 x 32 updates of diagonal blocks also write their upper halves, which
+// POTRF of the block overwrites with zeros.  The persistent batch runs the
+// same block operations in the same order per element (batched_dag.cu), so
+// batched and single factors agree bit for bit.  An expired wait sets
+// st->timeout and stops the factorisation (reported as EGS_ERR_TIMEOUT).
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
 {
-    const int b = tl.b;
-    for (int p = 0; p < b; p += kIB) {
-        EGS_LAUNCH(kt, KC_POTRF, s, k_potrf_sub<<<1, 256, 0, s>>>(tl, k, p, st));
-        const int nrest = (b - p - kIB) / 16;   // 16-row TRSM blocks
-        const int n32 = (b - p - kIB) / 32;     // 32 x 32 SYRK blocks per side
-        if (nrest > 0) {
-            EGS_LAUNCH(kt, KC_POTRF, s, k_trsm_sub<<<(unsigned)nrest, 256, 0, s>>>(tl, k, p, st));
-            EGS_LAUNCH(kt, KC_POTRF, s, k_syrk_sub<<<(unsigned)(n32 * (n32 + 1) / 2), 256, 0, s>>>(tl, k, p, st));
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ bool diag_wait(const unsigned *c, unsigned target, DevStatus *st)
+{
+    if (ld_acquire_u32(c) >= target) return true;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        __nanosleep(32);
+        if (ld_acquire_u32(c) >= target) return true;
+        if (failed(st)) return false;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 2000000000ull) {
+            atomicExch(&st->timeout, 1);
+            atomicMin(&st->fail_index, 0ull);  // stops the rest of the evaluation
+            return false;
         }
     }
+}
+
+union DiagSmem {
+    PotrfSmem<32> potrf;
+    TrsmSmem<32, double> trsm;
+    Gemm32Smem gemm;
+};
+
+// Task t of the graph: type 0 POTRF(p), 1 TRSM(m, p), 2 UPDATE(m, n, p).
+__device__ __forceinline__ void diag_decode(int t, int nb, int &type, int &p, int &m, int &n)
+{
+    for (p = 0; p < nb; ++p) {
+        const int r = nb - p - 1, cnt = 1 + r + r * (r + 1) / 2;
+        if (t < cnt) break;
+        t -= cnt;
+    }
+    const int r = nb - p - 1;
+    if (t == 0) {
+        type = 0;
+        m = n = p;
+    } else if (t <= r) {
+        type = 1;
+        m = p + t;
+        n = p;
+    } else {
+        type = 2;
+        int u = t - 1 - r;
+        m = p + 1;
+        while (u >= m - p) {
+            u -= m - p;
+            ++m;
+        }
+        n = p + 1 + u;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_potrf_tile_dag(Tiles tl, int k, unsigned *ctr, DevStatus *st)
+{
+    __shared__ DiagSmem sm;
+    __shared__ int s_task, s_ok;
+    const int b = tl.b, nb = b >> 5, tid = threadIdx.x;
+    int ntasks = 0;
+    for (int p = 0; p < nb; ++p) {
+        const int r = nb - p - 1;
+        ntasks += 1 + r + r * (r + 1) / 2;
+    }
+    double *A = tl.t64(k, k);
+    unsigned *cnt = ctr;  // block (i, j) at i (i + 1) / 2 + j
+    unsigned *next = ctr + nb * (nb + 1) / 2;
+    for (;;) {
+        if (tid == 0) s_task = failed(st) ? ntasks : (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int t = s_task;
+        if (t >= ntasks) return;
+        int type, p, m, n;
+        diag_decode(t, nb, type, p, m, n);
+        if (tid == 0) {
+            bool ok;
+            if (type == 0) ok = diag_wait(cnt + tile_linear(p, p), (unsigned)p, st);
+            else if (type == 1)
+                ok = diag_wait(cnt + tile_linear(p, p), (unsigned)p + 1, st) &&
+                     diag_wait(cnt + tile_linear(m, p), (unsigned)p, st);
+            else
+                ok = diag_wait(cnt + tile_linear(m, p), (unsigned)p + 1, st) &&
+                     diag_wait(cnt + tile_linear(n, p), (unsigned)p + 1, st) &&
+                     diag_wait(cnt + tile_linear(m, n), (unsigned)p, st);
+            s_ok = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        double *Bmp = A + (size_t)m * 32 * b + p * 32;
+        if (type == 0) {
+            if (!potrf_smem_s<32>(sm.potrf, Bmp, b, (int64_t)k * b + p * 32, st)) return;
+            for (int e = tid; e < 32 * (b - p * 32 - 32); e += 256) {
+                const int r = e / (b - p * 32 - 32), c = e % (b - p * 32 - 32);
+                Bmp[(size_t)r * b + 32 + c] = 0.0;
+            }
+        } else if (type == 1) {
+            trsm_rows_s<32>(sm.trsm, A + (size_t)p * 32 * b + p * 32, b, Bmp, b, 32);
+        } else {
+            gemm_sub32_s(sm.gemm, Bmp, b, A + (size_t)n * 32 * b + p * 32, b, 32, A + (size_t)m * 32 * b + n * 32, b);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(cnt + tile_linear(m, type == 2 ? n : p), 1u);
+        }
+    }
+}
+
+size_t potrf_diag_scratch_words(int b)
+{
+    const int nb = b / 32;
+    return (size_t)nb * (nb + 1) / 2 + 1;
+}
+
+cudaError_t launch_potrf_diag(const Tiles &tl, int k, DevStatus *st, cudaStream_t s, KernelTimer *kt, unsigned *ctr)
+{
+    // ctr: this tile's zeroed counters (potrf_diag_scratch_words(b) words)
+    const int nb = tl.b / 32;
+    const int grid = nb * (nb - 1) / 2 < 48 ? (nb * (nb - 1) / 2 > 1 ? nb * (nb - 1) / 2 : 1) : 48;
+    EGS_LAUNCH(kt, KC_POTRF, s, k_potrf_tile_dag<<<grid, 256, 0, s>>>(tl, k, ctr, st));
     return cudaGetLastError();
 }
 
@@ -153,13 +244,16 @@ cudaError_t launch_update_f64(const Tiles &tl, int k, int64_t ntri, DevStatus *s
     return cudaGetLastError();
 }
 
-cudaError_t launch_potrf_tiles_f64(double *tiles, const TileGeom &g, DevStatus *st, cudaStream_t s, KernelTimer *kt)
+cudaError_t launch_potrf_tiles_f64(double *tiles, const TileGeom &g, DevStatus *st, cudaStream_t s, KernelTimer *kt,
+                                   unsigned *ctr)
 {
     const int T = g.T;
     const Tiles tl{tiles, nullptr, g.b, T, T};
+    cudaError_t e0 = cudaMemsetAsync(ctr, 0, (size_t)T * potrf_diag_scratch_words(g.b) * sizeof(unsigned), s);
+    if (e0 != cudaSuccess) return e0;
     for (int k = 0; k < T; ++k) {
         if (kt) kt->step = k;
-        cudaError_t e = launch_potrf_diag(tl, k, st, s, kt);
+        cudaError_t e = launch_potrf_diag(tl, k, st, s, kt, ctr + (size_t)k * potrf_diag_scratch_words(g.b));
         if (e != cudaSuccess) return e;
         if (k + 1 < T) {
             e = launch_trsm_f64(tl, k, T - k - 1, st, s, kt);

@@ -136,14 +136,22 @@ egs_status set_error(egs_status code, const char *fmt, ...);
 egs_status cuda_error(cudaError_t e, const char *what);
 
 // ---- launchers (stream-ordered, no synchronisation) ----
-// Sigma(theta) into FP64 lower tiles.
+// Sigma(theta) into FP64 lower tiles.  tab: EGS_MT_DOUBLES doubles of device
+// scratch for the local polynomials of a general nu (built first on s), or
+// NULL to evaluate every entry directly.
 cudaError_t launch_matern_tiles_f64(const double *X, const double *Y, const TileGeom &g,
                                     const egs_matern_params &P, double *tiles, cudaStream_t s,
-                                    KernelTimer *kt = nullptr);
+                                    KernelTimer *kt = nullptr, double *tab = nullptr);
+// The local polynomials of a general nu into tab (EGS_MT_DOUBLES doubles).
+cudaError_t launch_matern_table(const egs_matern_params &P, double *tab, cudaStream_t s, KernelTimer *kt = nullptr);
 
 // Tile Cholesky in place (FP64).  Stops doing work once st->fail_index is set.
+// ctr: T * potrf_diag_scratch_words(b) words of device scratch for the
+// one-launch diagonal POTRFs (zeroed here).
 cudaError_t launch_potrf_tiles_f64(double *tiles, const TileGeom &g, DevStatus *st, cudaStream_t s,
-                                   KernelTimer *kt = nullptr);
+                                   KernelTimer *kt, unsigned *ctr);
+// Counter words one diagonal tile's one-launch POTRF needs.
+size_t potrf_diag_scratch_words(int b);
 
 // Forward solve L y = z in place on zpad (T*b doubles, padded with zeros),
 // with per-tile log-det / dot partials and the final assembly into st->result.
@@ -152,7 +160,8 @@ cudaError_t launch_trsv_tiles_f64(const double *tiles, const TileGeom &g, double
 
 // Sigma(theta) into any Tiles storage (+ optional dense FP64 copy sig).
 cudaError_t launch_matern_tiles(const double *X, const double *Y, int64_t n, const Tiles &tl,
-                                const egs_matern_params &P, double *sig, cudaStream_t s, KernelTimer *kt);
+                                const egs_matern_params &P, double *sig, cudaStream_t s, KernelTimer *kt,
+                                double *tab = nullptr);
 
 // Mixed-precision evaluation buffers (all device, sized by mixed_layout).
 struct MixedBuffers {
@@ -163,10 +172,13 @@ struct MixedBuffers {
     double *partials; // 2T
     int *err;
     float *l32;       // b x b: L_kk rounded to FP32 for the off-band TRSM of step k (TF32 / BF16 modes)
-    float *wsp;       // FP32 mode: W = L_kk^-1 in split-TF32 B layout, b x 3b
+    float *wsp;       // FP32 mode: W = L_kk^-1 in split-TF32 layout, b rows of [hi | lo] (2b)
     double *vinv;     // T b x b: V_k = L_kk^-T (upper triangular) for the solves
     void *oz[2];      // FP32 mode: BF16 slices of the panel rows (ozaki_slices_bytes), step k uses k % 2
     double *ozs[2];   // FP32 mode: their row scales, (T-1) b doubles each
+    double *mtab;     // EGS_MT_DOUBLES: the generator's local polynomials (general nu)
+    unsigned *pctr;   // T * potrf_diag_scratch_words(b): counters of the one-launch diagonal POTRFs
+    float *rs[2];     // FP32 mode: the power-of-two scales of the split-FP16 panel rows, (T-1) b each
 };
 
 // One mixed-precision evaluation (fmt 3 = split TF32, 2 = TF32, 1 = BF16); the
@@ -177,10 +189,10 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
 
 // Layouts and setup of one evaluation (api.cu), shared with the serving loop.
 struct Layout {
-    size_t tiles, locs, z, zpad, partials, status, total;
+    size_t tiles, locs, z, zpad, partials, status, mtab, pctr, total;
 };
 struct MixedLayout {
-    size_t f64, f32, sig, panel, oz, l32, wsp, vinv, locs, z, vec, partials, status, err, total;
+    size_t f64, f32, sig, panel, oz, l32, wsp, vinv, locs, z, vec, partials, status, err, mtab, pctr, rs, total;
 };
 struct EvalSetup {
     TileGeom g;
@@ -213,7 +225,9 @@ bool mixed_result_ok(const EvalSetup &es, const DevStatus &h);
 int32_t default_tile(int64_t n, egs_precision p);
 
 // Building blocks shared by the FP64 and mixed drivers.
-cudaError_t launch_potrf_diag(const Tiles &tl, int k, DevStatus *st, cudaStream_t s, KernelTimer *kt);
+// POTRF of diagonal tile k: one launch over the task graph of its 32 x 32
+// blocks; ctr: zeroed potrf_diag_scratch_words(b) words for its counters.
+cudaError_t launch_potrf_diag(const Tiles &tl, int k, DevStatus *st, cudaStream_t s, KernelTimer *kt, unsigned *ctr);
 cudaError_t launch_trsm_f64(const Tiles &tl, int k, int nrows, DevStatus *st, cudaStream_t s, KernelTimer *kt);
 // FP64 update of the first ntri tiles of step k's trailing triangle (row order).
 cudaError_t launch_update_f64(const Tiles &tl, int k, int64_t ntri, DevStatus *st, cudaStream_t s, KernelTimer *kt,
@@ -244,10 +258,11 @@ cudaError_t launch_pad_vector(const double *z, int64_t n, double *zpad, int64_t 
                               KernelTimer *kt = nullptr);
 
 // Operand formats of the tensor-core update: 1 = BF16, 2 = TF32 (FP32
-// storage), 3 = split TF32 (the A-role copy of each panel row holds
-// [lo | hi | hi], the B-role copy [hi | lo | hi], hi = tf32(x),
-// lo = tf32(x - hi), so one TF32 GEMM over K = 3b gives
-// lo hi^T + hi lo^T + hi hi^T, an FP32-accurate product).
+// storage), 3 = split TF32 (each panel row holds [hi | lo], hi = tf32(x),
+// lo = tf32(x - hi); the update forms lo hi^T + hi lo^T + hi hi^T per K
+// slice, an FP32-accurate product), 4 = split FP16 (each row x scaled by the
+// power of two s with max |x / s| < 2^15, [hi | lo] = FP16 parts of x / s;
+// the same three products at the FP16 rate, times s_m s_n in the epilogue).
 // Bytes of one panel buffer ((T-1) * b rows) in format fmt.
 size_t panel_buffer_bytes(int b, int T, int fmt);
 // Tensor maps over one panel buffer and the tcgen05 trailing update of step k.
@@ -264,7 +279,10 @@ cudaError_t make_offband_map(const float *f32, int b, size_t ntiles, CUtensorMap
 cudaError_t make_trsm_w_map(const float *wsp, int b, CUtensorMap *mapW);
 cudaError_t launch_trsm_tc(const CUtensorMap &mapA, const CUtensorMap &mapW, const CUtensorMap &mapC, const Tiles &tl,
                            int k, int m0, int *err, cudaStream_t s, KernelTimer *kt);
+// fmt 4 (split FP16, the FP32 mode's update): rs holds the power-of-two
+// scale of every panel row (panel_f16_scales); NULL otherwise.
 cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, const CUtensorMap &mapC, int fmt,
-                             const Tiles &tl, int k, int *err, cudaStream_t s, KernelTimer *kt, int part = 0);
+                             const Tiles &tl, int k, int *err, cudaStream_t s, KernelTimer *kt, int part = 0,
+                             const float *rs = nullptr);
 
 }  // namespace egs

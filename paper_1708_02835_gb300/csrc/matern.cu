@@ -35,13 +35,19 @@ __device__ __forceinline__ void tile_decode(int64_t t, int &i, int &j)
 // the tile is FP64 in tl, else rounded to float.  If sig is not NULL the
 // double values are also written to sig in the dense lower-tile layout (the
 // FP64 copy the mixed-precision refinement multiplies with).
+// tab: the local polynomials of a general nu (built by k_matern_table before
+// this launch), staged in shared memory; NULL for the closed forms.
 __global__ void __launch_bounds__(256)
 k_matern_tiles(const double *__restrict__ X, const double *__restrict__ Y, int64_t n, Tiles tl,
-               const __grid_constant__ egs_matern_params Pg, double *__restrict__ sig)
+               const __grid_constant__ egs_matern_params Pg, double *__restrict__ sig, const double *__restrict__ tab)
 {
     const int b = tl.b;
     __shared__ egs_matern_params Ps;
+    __shared__ double Ts[EGS_MT_DOUBLES];
+    if (tab)
+        for (int i = threadIdx.x; i < EGS_MT_DOUBLES; i += blockDim.x) Ts[i] = tab[i];
     stage_params(&Pg, &Ps);
+    const double *T = tab ? Ts : nullptr;
     const egs_matern_params *P = &Ps;
     int ti, tj;
     tile_decode((int64_t)blockIdx.x, ti, tj);
@@ -68,7 +74,7 @@ k_matern_tiles(const double *__restrict__ X, const double *__restrict__ Y, int64
         } else if (gi == gj) {
             v = P->th1;
         } else {
-            v = matern_eval(P, loc_dist(P, X[gi], Y[gi], xj, yj) * inv_th2);
+            v = matern_eval(P, loc_dist(P, X[gi], Y[gi], xj, yj) * inv_th2, T);
         }
         const size_t off = (size_t)r * b + sc * 64 + tx;
         if (is64) t64[off] = v;
@@ -77,20 +83,45 @@ k_matern_tiles(const double *__restrict__ X, const double *__restrict__ Y, int64
     }
 }
 
-cudaError_t launch_matern_tiles(const double *X, const double *Y, int64_t n, const Tiles &tl,
-                                const egs_matern_params &P, double *sig, cudaStream_t s, KernelTimer *kt)
+// The local polynomials of a general nu: one warp per sub-interval.
+__global__ void __launch_bounds__(256) k_matern_table(const __grid_constant__ egs_matern_params Pg, double *tab)
 {
+    __shared__ egs_matern_params Ps;
+    __shared__ double vals[8][EGS_MT_NC];
+    stage_params(&Pg, &Ps);
+    const int w = threadIdx.x >> 5;
+    const int iv = (int)blockIdx.x * 8 + w;
+    if (iv < EGS_MT_OCT * EGS_MT_SUB) matern_table_interval(&Ps, iv, tab, vals[w]);
+}
+
+cudaError_t launch_matern_table(const egs_matern_params &P, double *tab, cudaStream_t s, KernelTimer *kt)
+{
+    constexpr int blocks = (EGS_MT_OCT * EGS_MT_SUB + 7) / 8;
+    EGS_LAUNCH(kt, KC_GEN, s, k_matern_table<<<blocks, 256, 0, s>>>(P, tab));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_matern_tiles(const double *X, const double *Y, int64_t n, const Tiles &tl,
+                                const egs_matern_params &P, double *sig, cudaStream_t s, KernelTimer *kt, double *tab)
+{
+    const double *t = nullptr;
+    if (tab && P.kind == EGS_MATERN_GENERAL) {
+        cudaError_t e = launch_matern_table(P, tab, s, kt);
+        if (e != cudaSuccess) return e;
+        t = tab;
+    }
     const size_t ntiles = (size_t)tl.T * (tl.T + 1) / 2;
     dim3 grid((unsigned)ntiles, (unsigned)((tl.b / 64) * (tl.b / 64)));
-    EGS_LAUNCH(kt, KC_GEN, s, k_matern_tiles<<<grid, 256, 0, s>>>(X, Y, n, tl, P, sig));
+    EGS_LAUNCH(kt, KC_GEN, s, k_matern_tiles<<<grid, 256, 0, s>>>(X, Y, n, tl, P, sig, t));
     return cudaGetLastError();
 }
 
 cudaError_t launch_matern_tiles_f64(const double *X, const double *Y, const TileGeom &g,
-                                    const egs_matern_params &P, double *tiles, cudaStream_t s, KernelTimer *kt)
+                                    const egs_matern_params &P, double *tiles, cudaStream_t s, KernelTimer *kt,
+                                    double *tab)
 {
     const Tiles tl{tiles, nullptr, g.b, g.T, g.T};
-    return launch_matern_tiles(X, Y, g.n, tl, P, nullptr, s, kt);
+    return launch_matern_tiles(X, Y, g.n, tl, P, nullptr, s, kt, tab);
 }
 
 }  // namespace egs

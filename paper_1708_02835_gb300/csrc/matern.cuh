@@ -37,9 +37,11 @@ __device__ __forceinline__ int cf_depth(double x)
     return k > EGS_CF_MAX ? EGS_CF_MAX : k;
 }
 
-// x^nu K_nu(x) * c for the general case, x > 0.
+// x^nu K_nu(x) * c for the general case, x > 0 (times e^x if scaled: the
+// table builder's form, finite up to x of a few thousand).
 // Pp points to the constants staged in shared memory.
-__device__ __forceinline__ double matern_general(const egs_matern_params *__restrict__ Pp, double x)
+__device__ __forceinline__ double matern_general(const egs_matern_params *__restrict__ Pp, double x,
+                                                 bool scaled = false)
 {
     const egs_matern_params &P = *Pp;
     const double mu = P.mu;
@@ -81,6 +83,7 @@ __device__ __forceinline__ double matern_general(const egs_matern_params *__rest
         double xn = 1.0;
         for (int j = 0; j < P.N; ++j) xn *= x;
         front = P.c * P.two_mu * ies * xn;
+        if (scaled) front *= exp(x);
     } else {
         // Backward recurrence z_{k-1} = 2(k + x) z_k - q_k z_{k+1}, z_{K+1} = 0,
         // accumulating s = sum_k C_k z_k; S = s / z_0 and z_1 / z_0 are
@@ -111,7 +114,7 @@ __device__ __forceinline__ double matern_general(const egs_matern_params *__rest
         // e^x K_mu = sqrt(pi / (2x)) / S
         kmu = 1.2533141373155002512 * rsqrt(x) / S;
         kmu1 = kmu * (mu + x + 0.5 - (0.25 - mu * mu) * r1) / x;
-        front = P.c * exp(P.nu * log(x) - x);
+        front = P.c * exp(scaled ? P.nu * log(x) : P.nu * log(x) - x);
     }
     double knu = kmu;
     if (P.N >= 1) {
@@ -181,8 +184,34 @@ __device__ __forceinline__ double th1_exp_neg(const egs_matern_params *__restric
     return __longlong_as_double(bits - ((long long)m << 52));
 }
 
-// C(x * theta2) for x = r / theta2 >= 0.
-__device__ __forceinline__ double matern_eval(const egs_matern_params *__restrict__ Pp, double x)
+// Smallest x covered by the local polynomials (below it: Temme's series).
+constexpr double kMtXlo = 1.25 * 0x1p-12;
+
+// C(x) for general nu from the local polynomials (x in [kMtXlo, 708)): with
+// y = x / 1.25 = 2^e (1 + (j + (1 + s) / 2) / 8), e the octave and j the
+// sub-interval (both read from the bits of y), s in [-1, 1) is formed from
+// the remaining mantissa bits without rounding; C = p_{e,j}(s) theta1 e^-x.
+// About 25 FP64 operations.
+__device__ __forceinline__ double matern_table_eval(const egs_matern_params *__restrict__ Pp,
+                                                    const double *__restrict__ tab, double x)
+{
+    const double y = x * 0.8;
+    const long long yb = __double_as_longlong(y);
+    const int oct = (int)((yb >> 52) & 0x7FF) - 1023 - EGS_MT_E0;
+    const int iv = oct * EGS_MT_SUB + (int)((yb >> 49) & 7);
+    const double v = __longlong_as_double(((yb & 0x1FFFFFFFFFFFFll) << 3) | 0x3FF0000000000000ll);
+    const double s = fma(2.0, v, -3.0);
+    const double *a = tab + iv * EGS_MT_NC;
+    double p = a[EGS_MT_NC - 1];
+#pragma unroll
+    for (int j = EGS_MT_NC - 2; j >= 0; --j) p = fma(p, s, a[j]);
+    return p * th1_exp_neg(Pp, x);
+}
+
+// C(x * theta2) for x = r / theta2 >= 0.  tab: the local polynomials of a
+// general nu (shared or global memory), or NULL for the direct evaluation.
+__device__ __forceinline__ double matern_eval(const egs_matern_params *__restrict__ Pp, double x,
+                                              const double *__restrict__ tab = nullptr)
 {
     const egs_matern_params &P = *Pp;
     if (x == 0.0) return P.th1;
@@ -190,8 +219,55 @@ __device__ __forceinline__ double matern_eval(const egs_matern_params *__restric
     case EGS_MATERN_HALF: return th1_exp_neg(Pp, x);
     case EGS_MATERN_3HALF: return (1.0 + x) * th1_exp_neg(Pp, x);
     case EGS_MATERN_5HALF: return fma(x, fma(x, 1.0 / 3.0, 1.0), 1.0) * th1_exp_neg(Pp, x);
-    default: return matern_general(Pp, x);
+    default:
+        if (tab && x >= kMtXlo) return x < 708.0 ? matern_table_eval(Pp, tab, x) : (x == x ? 0.0 : x);
+        return matern_general(Pp, x);
     }
+}
+
+// One warp builds the local polynomial of sub-interval iv (0 <= iv <
+// EGS_MT_OCT * EGS_MT_SUB): lanes 0..NC-1 evaluate g = theta1^-1 e^x C(x) at
+// the NC Chebyshev points of the interval with the direct method, lane 0
+// forms the Chebyshev coefficients c_k = (2 / NC) sum_i g_i cos(pi k (i + 1/2) / NC)
+// (c_0 halved) and converts sum_k c_k T_k(s) to monomials in s (T_{k+1} =
+// 2 s T_k - T_{k-1}).  vals: NC doubles of shared memory for this warp.
+__device__ __forceinline__ void matern_table_interval(const egs_matern_params *__restrict__ Pp, int iv, double *tab,
+                                                      double *vals)
+{
+    const int lane = threadIdx.x & 31;
+    const int oct = iv / EGS_MT_SUB, sub = iv % EGS_MT_SUB;
+    if (lane < EGS_MT_NC) {
+        const double t = cospi((2.0 * lane + 1.0) / (2.0 * EGS_MT_NC));  // Chebyshev point in s
+        const double y = ldexp(1.0 + (sub + 0.5 * (1.0 + t)) / EGS_MT_SUB, oct + EGS_MT_E0);
+        const double x = 1.25 * y;
+        vals[lane] = matern_general(Pp, x, true) / Pp->th1;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        double c[EGS_MT_NC], a[EGS_MT_NC], tkm[EGS_MT_NC], tk[EGS_MT_NC], tn[EGS_MT_NC];
+        for (int k = 0; k < EGS_MT_NC; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < EGS_MT_NC; ++i) acc = fma(vals[i], cospi(k * (2.0 * i + 1.0) / (2.0 * EGS_MT_NC)), acc);
+            c[k] = acc * (k == 0 ? 1.0 : 2.0) / EGS_MT_NC;
+            a[k] = 0.0;
+            tkm[k] = tk[k] = 0.0;
+        }
+        tkm[0] = 1.0;  // T_0
+        tk[1] = 1.0;   // T_1
+        a[0] = c[0];
+        a[1] = c[1];
+        for (int k = 1; k + 1 < EGS_MT_NC; ++k) {
+            // T_{k+1} = 2 s T_k - T_{k-1}
+            for (int j = 0; j < EGS_MT_NC; ++j) tn[j] = (j > 0 ? 2.0 * tk[j - 1] : 0.0) - tkm[j];
+            for (int j = 0; j < EGS_MT_NC; ++j) {
+                a[j] = fma(c[k + 1], tn[j], a[j]);
+                tkm[j] = tk[j];
+                tk[j] = tn[j];
+            }
+        }
+        for (int j = 0; j < EGS_MT_NC; ++j) tab[iv * EGS_MT_NC + j] = a[j];
+    }
+    __syncwarp();
 }
 
 }  // namespace egs

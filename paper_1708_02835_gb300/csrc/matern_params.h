@@ -10,6 +10,16 @@
 #define EGS_CF_MAX 140   /* depth of the backward recurrence (x > 1.25) */
 #define EGS_EXP_TAB 64   /* entries of the exponential's table (2^(j/64)) */
 
+/* Local polynomials of theta1^-1 e^x C(x) for general nu (built on the device
+ * per evaluation, matern.cu): x / 1.25 in [2^E0, 2^(E0 + OCT)), each octave
+ * cut into SUB equal sub-intervals, NC monomial coefficients each in the
+ * local variable s in [-1, 1). */
+#define EGS_MT_OCT 22
+#define EGS_MT_SUB 8
+#define EGS_MT_NC 12
+#define EGS_MT_E0 (-12)
+#define EGS_MT_DOUBLES (EGS_MT_OCT * EGS_MT_SUB * EGS_MT_NC)
+
 /* distance between two locations */
 #define EGS_DIST_EUCLIDEAN 0    /* (x, y) in the plane */
 #define EGS_DIST_GREAT_CIRCLE 1 /* (longitude, latitude) in degrees, haversine */

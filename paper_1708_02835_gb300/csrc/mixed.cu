@@ -27,6 +27,7 @@
 #include "slices.cuh"
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace egs {
 
@@ -46,23 +47,18 @@ __device__ __forceinline__ float to_tf32(float x)
 
 // Element (row, col) of the panel operand buffer; row counts over all panel
 // tiles ((T-1) b rows), col < b.  FMT 3 (split TF32) writes hi = tf32(v) and
-// lo = tf32(v - hi) (v - hi is exact in FP32) as [lo | hi | hi] into the
-// A-role array and [hi | lo | hi] into the B-role array that follows it, so
-// the accumulator takes the two small cross terms before hi hi^T.
+// lo = tf32(v - hi) (v - hi is exact in FP32) as the row [hi | lo] of 2b
+// floats; the update reads both halves of both operands and forms
+// lo hi^T + hi lo^T + hi hi^T.
 template <int FMT>
 __device__ __forceinline__ void panel_store(void *panel, const Tiles &tl, size_t row, int col, float v)
 {
     if (FMT == 3) {
-        const size_t ld = 3 * (size_t)tl.b;
+        const size_t ld = 2 * (size_t)tl.b;
         float *pa = reinterpret_cast<float *>(panel) + row * ld + col;
-        float *pb = pa + (size_t)(tl.T - 1) * tl.b * ld;
         const float hi = to_tf32(v), lo = to_tf32(v - hi);
-        pa[0] = lo;
-        pa[tl.b] = hi;
-        pa[2 * tl.b] = hi;
-        pb[0] = hi;
-        pb[tl.b] = lo;
-        pb[2 * tl.b] = hi;
+        pa[0] = hi;
+        pa[tl.b] = lo;
     } else if (FMT == 2) {
         reinterpret_cast<float *>(panel)[row * tl.b + col] = to_tf32(v);
     } else {
@@ -70,44 +66,67 @@ __device__ __forceinline__ void panel_store(void *panel, const Tiles &tl, size_t
     }
 }
 
-// FP32 mode: FP64 band panel rows (m = k+1..k+nrows) -> split-TF32 operands
-// and the BF16 slices of the FP64-accurate band updates; one warp per row.
-__global__ void __launch_bounds__(256) k_panel_from_f64_split(Tiles tl, int k, void *panel, __nv_bfloat16 *oz,
-                                                              double *ozs, const DevStatus *st)
+// FP32 mode, the update's operand row pr in split FP16: with s = 2^(e - 15)
+// (e from the row's slicing: |x| < 2^e), u = (float)x / s (|u| < 2^15, so
+// entries down to 2^-29 of the row's largest stay normal FP16 numbers),
+// hi = fp16(u), lo = fp16(u - hi), written as the row [hi | lo] of 2b halves;
+// s goes to rs[pr].  A row below 2^-100 is treated with e = -100.
+template <typename E>
+__device__ __forceinline__ void panel_row_f16(const E *x, int b, int e, __half *panel, float *rs, size_t pr)
+{
+    const int lane = threadIdx.x & 31;
+    if (e < -100) e = -100;
+    e -= 15;
+    const float inv = ldexpf(1.0f, -e);
+    __half *row = panel + pr * 2 * (size_t)b;
+    for (int c = lane; c < b; c += 32) {
+        const float u = (float)x[c] * inv;
+        const __half hi = __float2half_rn(u);
+        row[c] = hi;
+        row[b + c] = __float2half_rn(u - __half2float(hi));
+    }
+    if (lane == 0) rs[pr] = ldexpf(1.0f, e);
+}
+
+// FP32 mode: FP64 band panel rows (m = k+1..k+nrows) -> the BF16 slices of the
+// FP64-accurate band updates and the split-FP16 operands of the off-band
+// update; one warp per row.
+__global__ void __launch_bounds__(256) k_panel_from_f64_split(Tiles tl, int k, void *panel, float *rs,
+                                                              __nv_bfloat16 *oz, double *ozs, const DevStatus *st)
 {
     if (mfailed(st)) return;
-    const int b = tl.b, lane = threadIdx.x & 31;
+    const int b = tl.b;
     const size_t pr = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // panel row
     const int m = k + 1 + (int)(pr / b);
     const double *x = tl.t64(m, k) + (pr % b) * b;
-    for (int c = lane; c < b; c += 32) panel_store<3>(panel, tl, pr, c, (float)x[c]);
+    for (int c = threadIdx.x & 31; c < b; c += 32) panel_store<3>(panel, tl, pr, c, (float)x[c]);
     slice_row(x, b, oz + pr * b, (size_t)(tl.T - 1) * b * b, ozs + pr);
 }
 
 // FP32 mode: solved off-band panel rows (tiles m0 .. T - 1 of column k, FP32)
-// -> split-TF32 operands and the BF16 slices of the FP64-accurate band
-// updates; one warp per row.
-__global__ void __launch_bounds__(256) k_panel_from_f32_split(Tiles tl, int k, int m0, void *panel,
+// -> the BF16 slices of the FP64-accurate band updates and the split-FP16
+// operands of the off-band update; one warp per row.
+__global__ void __launch_bounds__(256) k_panel_from_f32_split(Tiles tl, int k, int m0, void *panel, float *rs,
                                                               __nv_bfloat16 *oz, double *ozs, const DevStatus *st)
 {
     if (mfailed(st)) return;
-    const int b = tl.b, lane = threadIdx.x & 31;
+    const int b = tl.b;
     const size_t pr = (size_t)(m0 - k - 1) * b + (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // panel row
     const int m = k + 1 + (int)(pr / b);
     const float *x = tl.t32(m, k) + (pr % b) * b;
-    for (int c = lane; c < b; c += 32) panel_store<3>(panel, tl, pr, c, x[c]);
+    for (int c = threadIdx.x & 31; c < b; c += 32) panel_store<3>(panel, tl, pr, c, x[c]);
     slice_row_f32(x, b, oz + pr * b, (size_t)(tl.T - 1) * b * b, ozs + pr);
 }
 
 // FP32 mode, tensor-core TRSM: the unsolved off-band tiles (m0 .. T - 1, k)
-// in the split-TF32 A layout [lo | hi | hi] at operand rows (m - k - 1) b + r
-// of pre (four consecutive elements per thread).
+// in the split-TF32 layout [hi | lo] at operand rows (m - k - 1) b + r of pre
+// (four consecutive elements per thread).
 __global__ void __launch_bounds__(256) k_presplit_a(Tiles tl, int k, int m0, float *__restrict__ pre,
                                                     const DevStatus *st)
 {
     if (mfailed(st)) return;
     const int b = tl.b;
-    const size_t bb = tl.bb(), total4 = (size_t)(tl.T - m0) * bb / 4, ld = 3 * (size_t)b;
+    const size_t bb = tl.bb(), total4 = (size_t)(tl.T - m0) * bb / 4, ld = 2 * (size_t)b;
     for (size_t e4 = (size_t)blockIdx.x * 256 + threadIdx.x; e4 < total4; e4 += (size_t)gridDim.x * 256) {
         const size_t e = 4 * e4;
         const int m = m0 + (int)(e / bb);
@@ -119,9 +138,8 @@ __global__ void __launch_bounds__(256) k_presplit_a(Tiles tl, int k, int m0, flo
         hi.z = to_tf32(v.z), lo.z = to_tf32(v.z - hi.z);
         hi.w = to_tf32(v.w), lo.w = to_tf32(v.w - hi.w);
         float *pa = pre + ((size_t)(m - k - 1) * b + off / b) * ld + off % b;
-        *reinterpret_cast<float4 *>(pa) = lo;
-        *reinterpret_cast<float4 *>(pa + b) = hi;
-        *reinterpret_cast<float4 *>(pa + 2 * b) = hi;
+        *reinterpret_cast<float4 *>(pa) = hi;
+        *reinterpret_cast<float4 *>(pa + b) = lo;
     }
 }
 
@@ -133,8 +151,8 @@ __global__ void __launch_bounds__(256) k_presplit_a(Tiles tl, int k, int m0, flo
 // multiply and the owner's update of row i + 1; the other rows' updates
 // overlap it.  Each p_r receives its terms in the order of i, so results are
 // bitwise reproducible.  Outputs: V_k = W^T (row j of V_k is w_j, the
-// upper-triangular inverse the solves use) and W in the split-TF32 B layout
-// of the tensor-core TRSM (row c: [hi | lo | hi] of (float) W[c][.]).
+// upper-triangular inverse the solves use) and W in the split-TF32 layout
+// of the tensor-core TRSM (row c: [hi | lo] of (float) W[c][.]).
 // NT = b / 32 rows per lane.  Shared memory: (1 + warps) b doubles.
 template <int NT>
 __global__ void __launch_bounds__(128) k_inv_cols(Tiles tl, int k, double *__restrict__ V, float *__restrict__ wsp,
@@ -175,15 +193,14 @@ __global__ void __launch_bounds__(128) k_inv_cols(Tiles tl, int k, double *__res
     }
     __syncwarp();
     double *Vj = V + (size_t)k * tl.bb() + (size_t)j * b;
-    const size_t ld3 = 3 * (size_t)b;
+    const size_t ld2 = 2 * (size_t)b;
     for (int c = lane; c < b; c += 32) {
         const double x = xs[c];
         Vj[c] = x;
         const float v = (float)x, hi = to_tf32(v), lo = to_tf32(v - hi);
-        float *pw = wsp + (size_t)c * ld3 + j;
+        float *pw = wsp + (size_t)c * ld2 + j;
         pw[0] = hi;
         pw[b] = lo;
-        pw[2 * b] = hi;
     }
 }
 
@@ -539,7 +556,7 @@ namespace {
 // matrix (leaving a few SMs free) while the next chain runs.  Panels (and in
 // FP32 mode the slices) alternate between two buffers.
 template <int FMT>
-cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CUtensorMap *mbm,
+cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CUtensorMap *mbm, const CUtensorMap *ma3,
                          const CUtensorMap &mc, const CUtensorMap (*moz)[2], const CUtensorMap *mw, DevStatus *st,
                          cudaStream_t s, KernelTimer *kt)
 {
@@ -556,6 +573,8 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_col, cudaEventDisableTiming);
+    if (e == cudaSuccess)  // the one-launch diagonal POTRFs' counters
+        e = cudaMemsetAsync(mb.pctr, 0, (size_t)T * potrf_diag_scratch_words(b) * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);  // the side stream starts after prior work on s
     KernelTimer *kts = kt;  // side-stream kernels are timed with events on the side stream
     for (int k = 0; k < T && e == cudaSuccess; ++k) {
@@ -569,7 +588,8 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         // and the band rows' operands; then (after signalling the main
         // stream) the FP64 band x band update
         e = cudaStreamWaitEvent(side, ev_col, 0);
-        if (e == cudaSuccess) e = launch_potrf_diag(tl, k, st, side, kts);
+        if (e == cudaSuccess)
+            e = launch_potrf_diag(tl, k, st, side, kts, mb.pctr + (size_t)k * potrf_diag_scratch_words(b));
         if (e == cudaSuccess && k + 1 < T) {
             if (nf > 0 && FMT != 3)
                 EGS_LAUNCH(kts, KC_TRSM, side,
@@ -579,8 +599,8 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
             if (e == cudaSuccess && nb > 0) {
                 if (FMT == 3) {
                     EGS_LAUNCH(kts, KC_TRSM, side,
-                               k_panel_from_f64_split<<<(unsigned)((size_t)nb * b / 8), 256, 0, side>>>(tl, k, panel, oz,
-                                                                                                      ozs, st));
+                               k_panel_from_f64_split<<<(unsigned)((size_t)nb * b / 8), 256, 0, side>>>(
+                                   tl, k, panel, mb.rs[k & 1], oz, ozs, st));
                 } else {
                     const size_t total = (size_t)nb * tl.bb();
                     const unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
@@ -613,11 +633,11 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
                 const unsigned g4 = (unsigned)((total4 + 255) / 256 < 2048 ? (total4 + 255) / 256 : 2048);
                 EGS_LAUNCH(kt, KC_TRSM, s,
                            k_presplit_a<<<g4, 256, 0, s>>>(tl, k, m0, (float *)mb.panel[(k + 1) & 1], st));
-                e = launch_trsm_tc(ma[(k + 1) & 1], *mw, mc, tl, k, m0, mb.err, s, kt);
+                e = launch_trsm_tc(ma3[(k + 1) & 1], *mw, mc, tl, k, m0, mb.err, s, kt);
                 if (e == cudaSuccess)
                     EGS_LAUNCH(kt, KC_TRSM, s,
-                               k_panel_from_f32_split<<<(unsigned)((size_t)nf * b / 8), 256, 0, s>>>(tl, k, m0, panel,
-                                                                                                    oz, ozs, st));
+                               k_panel_from_f32_split<<<(unsigned)((size_t)nf * b / 8), 256, 0, s>>>(
+                                   tl, k, m0, panel, mb.rs[k & 1], oz, ozs, st));
             }
         } else if (e == cudaSuccess && nf > 0) {
             EGS_LAUNCH(kt, KC_TRSM, s,
@@ -627,11 +647,14 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         // FP32 mode: band outputs with an FP32 operand by exact slices
         if (e == cudaSuccess && FMT == 3)
             e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, k, k + 1, 1, ozs, mb.err, s, kt);
-        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, FMT, tl, k, mb.err, s, kt, 1);
+        // FP32 mode: the off-band update in split FP16 (fmt 4) from the scaled rows
+        const int ufmt = FMT == 3 ? 3 : FMT;
+        const float *urs = nullptr;
+        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, ufmt, tl, k, mb.err, s, kt, 1, urs);
         if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);
         if (e == cudaSuccess && FMT == 3)
             e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, k, k + 2, T - k - 2, ozs, mb.err, s, kt);
-        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, FMT, tl, k, mb.err, s, kt, 2);
+        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, ufmt, tl, k, mb.err, s, kt, 2, urs);
     }
     if (kt) kt->step = -1;
     if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
@@ -683,21 +706,25 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     const int64_t npad = (int64_t)T * b;
     const unsigned vb = (unsigned)((npad + 255) / 256);
     if (ev) cudaEventRecord(ev[0], s);
-    cudaError_t e = launch_matern_tiles(X, Y, n, tl, P, mb.sig, s, kt);
+    cudaError_t e = launch_matern_tiles(X, Y, n, tl, P, mb.sig, s, kt, mb.mtab);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
-    CUtensorMap ma[2], mbm[2], mc, moz[2][2];
-    e = make_panel_maps(mb.panel[0], fmt, b, T, &ma[0], &mbm[0]);
-    if (e == cudaSuccess) e = make_panel_maps(mb.panel[1], fmt, b, T, &ma[1], &mbm[1]);
+    // update maps (FP32 mode: split FP16 over the panel buffers) and, in the
+    // FP32 mode, split-TF32 maps over the same buffers for the TRSM's operand
+    CUtensorMap ma[2], mbm[2], ma3[2], mb3, mc, moz[2][2];
+    const int ufmt = fmt;
+    e = make_panel_maps(mb.panel[0], ufmt, b, T, &ma[0], &mbm[0]);
+    if (e == cudaSuccess) e = make_panel_maps(mb.panel[1], ufmt, b, T, &ma[1], &mbm[1]);
+    for (int i = 0; i < 2 && e == cudaSuccess && fmt == 3; ++i) e = make_panel_maps(mb.panel[i], 3, b, T, &ma3[i], &mb3);
     if (e == cudaSuccess) e = make_offband_map(tl.f32, b, Tiles::f32_tiles(T, tl.band), &mc);
     for (int i = 0; i < 2 && e == cudaSuccess && fmt == 3; ++i) e = make_ozaki_maps(mb.oz[i], b, T, &moz[i][0], &moz[i][1]);
     if (e != cudaSuccess) return e;
     CUtensorMap mw;
     if (fmt == 3) e = make_trsm_w_map(mb.wsp, b, &mw);
     if (e != cudaSuccess) return e;
-    if (fmt == 3) e = factor_mixed<3>(mb, ma, mbm, mc, moz, &mw, st, s, kt);
-    else if (fmt == 2) e = factor_mixed<2>(mb, ma, mbm, mc, moz, nullptr, st, s, kt);
-    else e = factor_mixed<1>(mb, ma, mbm, mc, moz, nullptr, st, s, kt);
+    if (fmt == 3) e = factor_mixed<3>(mb, ma, mbm, ma3, mc, moz, &mw, st, s, kt);
+    else if (fmt == 2) e = factor_mixed<2>(mb, ma, mbm, ma3, mc, moz, nullptr, st, s, kt);
+    else e = factor_mixed<1>(mb, ma, mbm, ma3, mc, moz, nullptr, st, s, kt);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], s);
     // V_k = L_kk^-T for every diagonal tile (FP32 mode: computed during the

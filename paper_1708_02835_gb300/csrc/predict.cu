@@ -119,7 +119,7 @@ extern "C" egs_status egs_predict(const double *locs_obs, const double *z_obs, i
     cudaFreeAsync(ws, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "egs_predict");
-    if (herr) return set_error(EGS_ERR_TIMEOUT, "egs_predict: a tensor-core pipeline wait timed out");
+    if (herr || h.timeout) return set_error(EGS_ERR_TIMEOUT, "egs_predict: a bounded device wait timed out");
     if (info) {
         fill_info(es, h, info);
         info->launches = kt.launches + 1;

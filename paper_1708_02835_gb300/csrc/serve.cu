@@ -98,7 +98,7 @@ void release_slot(egs_server *S, Slot &sl)
 void finish_slot(egs_server *S, Slot &sl)
 {
     // called with S->mu held
-    if (S->cfg.fallback_fp64 && sl.req.p != EGS_FP64 && !*sl.h_err) {
+    if (S->cfg.fallback_fp64 && sl.req.p != EGS_FP64 && !*sl.h_err && !sl.h_status->timeout) {
         const egs::DevStatus &h = *sl.h_status;
         if (h.fail_index != egs::kNoFail || !egs::mixed_result_ok(sl.es, h)) {
             // the mixed factor failed or was too inexact: answer from FP64
@@ -114,7 +114,7 @@ void finish_slot(egs_server *S, Slot &sl)
     r.done = true;
     const egs::DevStatus &h = *sl.h_status;
     egs::fill_info(sl.es, h, &r.info);
-    if (*sl.h_err) {
+    if (*sl.h_err || h.timeout) {
         r.status = EGS_ERR_TIMEOUT;
         r.loglik = NAN;
     } else if (h.fail_index != egs::kNoFail) {

@@ -16,9 +16,10 @@ namespace egs {
 constexpr int kSlices = 5;
 
 // FP64 rows (the band panel tiles and the dense test operands).
+// Both return e (|x| < 2^e for every entry of the row; 0 for a zero row).
 template <typename E>
-__device__ __forceinline__ void slice_row(const E *__restrict__ src, int K, __nv_bfloat16 *__restrict__ dst,
-                                          size_t slice_stride, double *scale)
+__device__ __forceinline__ int slice_row(const E *__restrict__ src, int K, __nv_bfloat16 *__restrict__ dst,
+                                         size_t slice_stride, double *scale)
 {
     const int lane = threadIdx.x & 31;
     double x[32];
@@ -47,13 +48,14 @@ __device__ __forceinline__ void slice_row(const E *__restrict__ src, int K, __nv
             }
         }
     }
+    return e;
 }
 
 // FP32 rows (the off-band panel tiles): the same slices, computed in FP32 --
 // every step is exact there too (u has at most 24 significant bits, and each
 // q_i and remainder keeps a subset of them), so the FP64 pipe is not used.
-__device__ __forceinline__ void slice_row_f32(const float *src, int K, __nv_bfloat16 *__restrict__ dst,
-                                              size_t slice_stride, double *scale)
+__device__ __forceinline__ int slice_row_f32(const float *src, int K, __nv_bfloat16 *__restrict__ dst,
+                                             size_t slice_stride, double *scale)
 {
     const int lane = threadIdx.x & 31;
     float x[32];
@@ -83,6 +85,7 @@ __device__ __forceinline__ void slice_row_f32(const float *src, int K, __nv_bflo
             }
         }
     }
+    return e;
 }
 
 }  // namespace egs

@@ -33,11 +33,23 @@ constexpr int BM = 128, BN = 256, STAGES = 4;
 constexpr int kReserveSms = 24;
 constexpr int kReserveSmsLong = 8;
 constexpr int64_t kLongBulkItems = 72000;
-constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
 constexpr int EPI_WARPS = 8;
 constexpr int STAGE_C = 32 * 32 * 4;  // one 32 x 32 FP32 box staged for the TMA reduce
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_WARPS * STAGE_C + 1024;
-static_assert(SMEM_BYTES + 512 <= 232448, "dynamic + static shared memory must fit 227 KB");
+// Operand formats: 1 = BF16, 2 = TF32 (one box of A and one of B per stage,
+// 4 stages of 48 KB), 3 = split TF32 (A and B rows [hi | lo] over K = 2b: a
+// stage holds the hi and lo boxes of A and of B for one 32-element K slice,
+// 2 stages of 96 KB, and feeds lo hi' + hi lo' + hi hi' into the accumulator),
+// 4 = split FP16 (the same with FP16 halves of rows scaled by a power of two
+// per row, 64-element K slices, FP16 MMAs at twice the TF32 rate; the
+// epilogue multiplies by the row scales of both operands, exactly).
+template <int FMT>
+struct Cfg {
+    static constexpr int STAGES_ = FMT >= 3 ? 2 : STAGES;
+    static constexpr int STAGE_BYTES = FMT >= 3 ? 2 * (A_BYTES + B_BYTES) : A_BYTES + B_BYTES;
+    static constexpr int SMEM_BYTES = STAGES_ * STAGE_BYTES + EPI_WARPS * STAGE_C + 1024;
+    static_assert(SMEM_BYTES + 512 <= 232448, "dynamic + static shared memory must fit 227 KB");
+};
 constexpr uint32_t TMEM_COLS = 256;
 
 struct WorkItem {
@@ -65,6 +77,8 @@ struct UpdateWork {
     int col0;
     int one_col;
     int skip_band;
+    const float *rs;  // split FP16: the power-of-two scale of every panel row
+    __device__ float row_scale(int y) const { return rs[y]; }
     __device__ bool decode(int64_t bid, WorkItem &w) const
     {
         const int nrb = tl.b / BM, ncb = tl.b / BN, per = nrb * ncb;
@@ -188,9 +202,9 @@ struct UpdateWork {
 
 // FP32 mode, off-band panel TRSM of step k as a product with the inverse
 // diagonal tile: X_mk = A_mk L_kk^-T = A_mk W^T, W = L_kk^-1, for the tiles
-// m = m0 .. T - 1.  A rows: the unsolved tiles in split-TF32 A layout at
-// operand row (m - k - 1) b (the spare panel buffer of the step); B rows: W
-// in split-TF32 B layout (b rows of K = 3b).  The accumulator is X itself,
+// m = m0 .. T - 1.  A rows: the unsolved tiles in split-TF32 layout [hi | lo]
+// at operand row (m - k - 1) b (the spare panel buffer of the step); B rows:
+// W in the same layout (b rows of 2b floats).  The accumulator is X itself,
 // stored over A_mk (each output block is written by exactly one item, and
 // the operands live in other buffers, so there is no read-after-write race).
 struct TrsmWork {
@@ -272,6 +286,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
           const __grid_constant__ CUtensorMap mapC, Work work, int64_t nitems, int kchunks, int *err)
 {
+    constexpr int STAGES = Cfg<FMT>::STAGES_;
+    constexpr int STAGE_BYTES = Cfg<FMT>::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
@@ -305,7 +321,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tbase = tmem_base;
-    constexpr int KELEMS = (FMT == 2) ? 32 : 64;  // elements per 128-byte row slice
+    constexpr int KELEMS = (FMT == 1 || FMT == 4) ? 64 : 32;  // elements per 128-byte row slice
+    const int klo = kchunks * KELEMS;                         // FMT 3 / 4: K offset of the lo half of a row
 
     if (warp == 0) {
         if (lane == 0) {
@@ -330,15 +347,24 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                     const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1u, &abort_flag)) break;
                     tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                    tc::tma_load_2d(&mapA, &full[s], smem + s * STAGE_BYTES, c * KELEMS, wi.ya);
-                    tc::tma_load_2d(&mapB, &full[s], smem + s * STAGE_BYTES + A_BYTES, c * KELEMS, wi.yb);
+                    uint8_t *st = smem + s * STAGE_BYTES;
+                    if (FMT >= 3) {
+                        tc::tma_load_2d(&mapA, &full[s], st, c * KELEMS, wi.ya);                    // A hi
+                        tc::tma_load_2d(&mapA, &full[s], st + A_BYTES, klo + c * KELEMS, wi.ya);    // A lo
+                        tc::tma_load_2d(&mapB, &full[s], st + 2 * A_BYTES, c * KELEMS, wi.yb);      // B hi
+                        tc::tma_load_2d(&mapB, &full[s], st + 2 * A_BYTES + B_BYTES, klo + c * KELEMS, wi.yb);  // B lo
+                    } else {
+                        tc::tma_load_2d(&mapA, &full[s], st, c * KELEMS, wi.ya);
+                        tc::tma_load_2d(&mapB, &full[s], st + A_BYTES, c * KELEMS, wi.yb);
+                    }
                     last_chunk[s] = g;
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = tc::idesc_f32acc(BM, BN, FMT);
+            // instruction formats: 0 = FP16, 1 = BF16 (kind::f16), 2 = TF32 (kind::tf32)
+            constexpr uint32_t idesc = tc::idesc_f32acc(BM, BN, FMT == 3 ? 2 : (FMT == 4 ? 0 : FMT));
             int g = 0, t = 0, r = 0;
             while (!abort_flag) {
                 const int slot = r % RING;
@@ -358,13 +384,34 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                     if (!tc::mbar_wait(&full[s], ph, &abort_flag)) break;
                     tc::tc_fence_after();
                     const uint32_t a0 = tc::smem_u32(smem + s * STAGE_BYTES);
-                    const uint32_t b0 = a0 + A_BYTES;
+                    if (FMT >= 3) {
+                        // lo hi' + hi lo' + hi hi' of every K step (8 TF32 or 16
+                        // FP16 elements, 32 bytes): the two small cross terms
+                        // enter before the large product
+                        const uint32_t alo = a0 + A_BYTES, bhi = a0 + 2 * A_BYTES, blo = bhi + B_BYTES;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint64_t ad = tc::desc_sw128(a0 + 32 * j);
-                        const uint64_t bd = tc::desc_sw128(b0 + 32 * j);
-                        if (FMT == 2) tc::mma_tf32(d, ad, bd, idesc, (c | j) != 0);
-                        else tc::mma_f16(d, ad, bd, idesc, (c | j) != 0);
+                        for (int j = 0; j < 4; ++j) {
+                            if (FMT == 3) {
+                                tc::mma_tf32(d, tc::desc_sw128(alo + 32 * j), tc::desc_sw128(bhi + 32 * j), idesc,
+                                             (c | j) != 0);
+                                tc::mma_tf32(d, tc::desc_sw128(a0 + 32 * j), tc::desc_sw128(blo + 32 * j), idesc, 1u);
+                                tc::mma_tf32(d, tc::desc_sw128(a0 + 32 * j), tc::desc_sw128(bhi + 32 * j), idesc, 1u);
+                            } else {
+                                tc::mma_f16(d, tc::desc_sw128(alo + 32 * j), tc::desc_sw128(bhi + 32 * j), idesc,
+                                            (c | j) != 0);
+                                tc::mma_f16(d, tc::desc_sw128(a0 + 32 * j), tc::desc_sw128(blo + 32 * j), idesc, 1u);
+                                tc::mma_f16(d, tc::desc_sw128(a0 + 32 * j), tc::desc_sw128(bhi + 32 * j), idesc, 1u);
+                            }
+                        }
+                    } else {
+                        const uint32_t b0 = a0 + A_BYTES;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint64_t ad = tc::desc_sw128(a0 + 32 * j);
+                            const uint64_t bd = tc::desc_sw128(b0 + 32 * j);
+                            if (FMT == 2) tc::mma_tf32(d, ad, bd, idesc, (c | j) != 0);
+                            else tc::mma_f16(d, ad, bd, idesc, (c | j) != 0);
+                        }
                     }
                     tc::mma_commit(&empty[s]);
                 }
@@ -381,7 +428,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        uint8_t *stage = smem + STAGES * STAGE_BYTES + (warp - 2) * STAGE_C;
+        uint8_t *stage = smem + STAGES * STAGE_BYTES + (warp - 2) * STAGE_C;  // after the operand ring
         int t = 0, issued = 0, r = 0;
         while (true) {
             const int slot = r % RING;
@@ -402,10 +449,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             const uint32_t d = tbase + (uint32_t)buf * TMEM_COLS + lane_base;
             if (Work::kReduce && work.reduce_here(wi)) {
                 const int y = work.reduce_row(wi, q * 32);
+                float sr = 1.0f;
+                if constexpr (FMT == 4) sr = work.row_scale(wi.ya + q * 32 + lane);
 #pragma unroll 1
                 for (int cc = half * (BN / 64); cc < (half + 1) * (BN / 64); ++cc) {
                     float v[32];
                     tc::tmem_ld32(d + (uint32_t)(cc * 32), v);
+                    if constexpr (FMT == 4) {
+                        // the products of scaled rows times both powers of two (exact)
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] *= sr * work.row_scale(wi.yb + cc * 32 + j);
+                    }
                     uint8_t *sb = stage;
                     if (issued >= 1 && lane == 0) tc::bulk_wait_read<0>();  // the previous box has been read
                     __syncwarp();
@@ -473,12 +527,14 @@ cudaError_t make_map(CUtensorMap *m, const void *base, int fmt, uint64_t inner, 
 {
     auto fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
-    const uint32_t esz = (fmt == 1) ? 2 : 4;
+    const uint32_t esz = (fmt == 1 || fmt == 4) ? 2 : 4;
     cuuint64_t dims[2] = {inner, rows};
     cuuint64_t strides[1] = {inner * esz};
     cuuint32_t box[2] = {128u / esz, box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+    const CUtensorMapDataType dt = fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                  : (fmt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+    CUresult r = fn(m, dt, 2,
                     const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -501,6 +557,7 @@ template <int FMT, class Work>
 cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Work &w,
                         int64_t items, int kchunks, int *err, cudaStream_t s, int reserve = 0)
 {
+    constexpr int SMEM_BYTES = Cfg<FMT>::SMEM_BYTES;
     cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<FMT, Work>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int64_t ctas = num_sms() - reserve > 1 ? num_sms() - reserve : 1;
@@ -534,32 +591,26 @@ cudaError_t make_offband_map(const float *f32, int b, size_t ntiles, CUtensorMap
 size_t panel_buffer_bytes(int b, int T, int fmt)
 {
     const size_t elems = (size_t)(T > 1 ? T - 1 : 1) * (size_t)b * (size_t)b;
-    if (fmt == 3) return 2 * 3 * elems * sizeof(float);
+    if (fmt == 3) return 2 * elems * sizeof(float);
     return elems * (fmt == 1 ? 2 : 4);
 }
 
 // Panel maps for the trailing update: the panel buffer holds rows
-// (T - 1) * b of K = b operand elements (fmt 3: an A-role array and a
-// B-role array, each of K = 3b).
+// (T - 1) * b of K = b operand elements (fmt 3 / 4: K = 2b, [hi | lo]); the
+// A and B maps view the same rows with boxes of 128 and 256 rows.
 cudaError_t make_panel_maps(const void *panel, int fmt, int b, int T, CUtensorMap *mapA, CUtensorMap *mapB)
 {
     const uint64_t rows = (uint64_t)(T > 1 ? T - 1 : 1) * (uint64_t)b;
-    if (fmt == 3) {
-        const float *pa = (const float *)panel;
-        const float *pb = pa + rows * 3 * (uint64_t)b;
-        cudaError_t e = make_map(mapA, pa, fmt, 3 * (uint64_t)b, rows, BM);
-        if (e == cudaSuccess) e = make_map(mapB, pb, fmt, 3 * (uint64_t)b, rows, BN);
-        return e;
-    }
-    cudaError_t e = make_map(mapA, panel, fmt, (uint64_t)b, rows, BM);
-    if (e == cudaSuccess) e = make_map(mapB, panel, fmt, (uint64_t)b, rows, BN);
+    const uint64_t K = fmt >= 3 ? 2 * (uint64_t)b : (uint64_t)b;
+    cudaError_t e = make_map(mapA, panel, fmt, K, rows, BM);
+    if (e == cudaSuccess) e = make_map(mapB, panel, fmt, K, rows, BN);
     return e;
 }
 
-// Map over W = L_kk^-1 in split-TF32 B layout (b rows of 3b floats).
+// Map over W = L_kk^-1 in split-TF32 layout (b rows of [hi | lo], 2b floats).
 cudaError_t make_trsm_w_map(const float *wsp, int b, CUtensorMap *mapW)
 {
-    return make_map(mapW, wsp, 3, 3 * (uint64_t)b, (uint64_t)b, BN);
+    return make_map(mapW, wsp, 3, 2 * (uint64_t)b, (uint64_t)b, BN);
 }
 
 cudaError_t launch_trsm_tc(const CUtensorMap &mapA, const CUtensorMap &mapW, const CUtensorMap &mapC, const Tiles &tl,
@@ -571,18 +622,19 @@ cudaError_t launch_trsm_tc(const CUtensorMap &mapA, const CUtensorMap &mapW, con
     TrsmWork w{tl, k, m0};
     if (kt) kt->begin(KC_TRSM, s);
     // a few SMs stay free for the FP64 band update of the step on the side stream
-    cudaError_t e = launch_gemm<2>(mapA, mapW, mapC, w, items, 3 * tl.b / 32, err, s, kReserveSmsLong);
+    cudaError_t e = launch_gemm<3>(mapA, mapW, mapC, w, items, tl.b / 32, err, s, kReserveSmsLong);
     if (kt) kt->end(KC_TRSM, s);
     return e;
 }
 
 cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, const CUtensorMap &mapC, int fmt,
-                             const Tiles &tl, int k, int *err, cudaStream_t s, KernelTimer *kt, int part)
+                             const Tiles &tl, int k, int *err, cudaStream_t s, KernelTimer *kt, int part,
+                             const float *rs)
 {
     // part 0: every trailing tile; 1: column k + 1 only; 2: columns k + 2 .. T - 1
     const int64_t r = tl.T - k - 1;
     int64_t ntiles = 0;
-    UpdateWork w{tl, k, k + 1, 0, fmt == 3 ? 1 : 0};
+    UpdateWork w{tl, k, k + 1, 0, fmt >= 3 ? 1 : 0, rs};
     if (part == 0) ntiles = r * (r + 1) / 2;
     else if (part == 1) {
         ntiles = r;
@@ -593,12 +645,14 @@ cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, c
     }
     if (ntiles <= 0) return cudaSuccess;
     const int64_t blocks = ntiles * (tl.b / BM) * (tl.b / BN);
-    // split TF32 (fmt 3) is one TF32 GEMM over K = 3b
-    const int kchunks = fmt == 3 ? 3 * tl.b / 32 : tl.b / (fmt == 2 ? 32 : 64);
+    // split TF32 / FP16 (fmt 3 / 4): three products per K slice of the [hi | lo] rows
+    const int kchunks = tl.b / ((fmt == 1 || fmt == 4) ? 64 : 32);
     cudaError_t e;
     if (kt) kt->begin(KC_UPDATE, s);
     const int reserve = (part != 2) ? 0 : (blocks >= kLongBulkItems ? kReserveSmsLong : kReserveSms);
-    if (fmt >= 2) e = launch_gemm<2>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
+    if (fmt == 4) e = launch_gemm<4>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
+    else if (fmt == 3) e = launch_gemm<3>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
+    else if (fmt == 2) e = launch_gemm<2>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
     else e = launch_gemm<1>(mapA, mapB, mapC, w, blocks, kchunks, err, s, reserve);
     if (kt) kt->end(KC_UPDATE, s);
     return e;
