@@ -54,7 +54,10 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--n", type=int, default=102400, help="development override; the workload is n=102400")
     ap.add_argument("--tile", type=int, default=512)
-    ap.add_argument("--band", type=int, default=3)
+    ap.add_argument("--band", type=int, default=2)
+    ap.add_argument("--xband", type=int, default=3,
+                    help="FP32 mode: tiles with i - j < xband get FP64-accurate updates (those beyond the band stay "
+                         "FP32 in storage); 0 = band")
     ap.add_argument("--theta", default="1.0,0.1,0.5")
     ap.add_argument("--e2e-steps", type=int, default=-1, help="steps of the end-to-end leg (default: = steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -116,8 +119,11 @@ def whole_job_rate(units_per_rank: int, world: int, seconds_max: float) -> float
 def workload_name(a) -> str:
     m = int(round(math.sqrt(a.n)))
     grid = "%dx%d jittered grid" % (m, m) if m * m == a.n else "jittered grid"
-    return "n=%d (%s over [0,1]^2), theta=(%s), tile %d, %s, FP64 band %d" % (
-        a.n, grid, a.theta, a.tile, a.precision, a.band)
+    extra = ""
+    if a.precision == "fp32" and a.xband > a.band:
+        extra = " (FP64-accurate updates up to %d tiles from the diagonal)" % (a.xband - 1)
+    return "n=%d (%s over [0,1]^2), theta=(%s), tile %d, %s, FP64 band %d%s" % (
+        a.n, grid, a.theta, a.tile, a.precision, a.band, extra)
 
 
 def flop_counts(n: int, b: int) -> dict:
@@ -141,14 +147,16 @@ def band_band_flops(n: int, b: int, band: int) -> float:
     return tot
 
 
-def band_out_flops(n: int, b: int, band: int) -> float:
-    """Updates whose output is a band tile (m - n < band) but whose operands
-    are not both band tiles: FP64 in the FP32 (split-TF32) mode."""
+def band_out_flops(n: int, b: int, band: int, xband: int = 0) -> float:
+    """Updates whose output lies within xband (>= band) of the diagonal
+    (m - n < xband) but whose operands are not both FP64 band tiles: the
+    FP64-accurate slice products of the FP32 mode."""
     T = -(-n // b)
+    xband = max(xband, band)
     tot = 0.0
     for k in range(T - 1):
         for c in range(k + 1, T):
-            for d in range(band):
+            for d in range(xband):
                 m = c + d
                 if m < T and m - k >= band:
                     tot += b ** 3 if d == 0 else 2 * b ** 3
@@ -169,8 +177,12 @@ def tensor_peak(precision: str, sustained: bool = False) -> dict:
     except Exception:
         bf16 = 1700.0 if sustained else 1900.0
         src = "fallback bf16 %s PFLOP/s" % ("1.7 sustained" if sustained else "1.9 burst")
-    if precision in ("tf32", "fp32"):
+    if precision == "tf32":
         return {"tflops": bf16 * 0.5, "source": src + " x 1/2 (nominal tf32:bf16 dense ratio 1.1:2.25)"}
+    if precision == "fp32":
+        # the FP32 mode's off-band update runs FP16 MMAs (split FP16); the
+        # dense FP16 and BF16 rates are the same
+        return {"tflops": bf16, "source": src + " (FP16 products; nominal dense fp16 = bf16 rate)"}
     return {"tflops": bf16, "source": src}
 
 
@@ -416,7 +428,7 @@ def serve_rates(a, egs, rhos, requests: int, burst: int = 16) -> dict:
     mixed = a.precision if a.precision != "fp64" else "fp32"
 
     def server():
-        srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=a.band, fallback_fp64=True)
+        srv = egs.egs_server(150 << 30, max_inflight=8, tile=0, band=a.band, fallback_fp64=True, xband=a.xband)
         return srv, [srv.add_field(np.ascontiguousarray(f.locations().reshape(-1)), f.e(), f.n) for f in fields]
 
     def request(fids, i):
@@ -462,8 +474,8 @@ def serve_rates(a, egs, rhos, requests: int, burst: int = 16) -> dict:
         srv.close()
     return {"capacity_per_s": cap, "burst": burst, "mixed": mixed, "rates": results,
             "workload": "64 fields, n log-uniform [1000, 40000], nu ~ U(0.3, 2), Poisson arrivals, 50/50 FP64 and "
-                        "%s (band %d; a mixed request the accuracy guard rejects is re-run in FP64 by the server), "
-                        "150 GB budget, 8 slots" % (mixed, a.band)}
+                        "%s (band %d, xband %d; a mixed request the accuracy guard rejects is re-run in FP64 by the "
+                        "server), 150 GB budget, 8 slots" % (mixed, a.band, a.xband)}
 
 
 def run_serve(a, egs):
@@ -549,9 +561,11 @@ def main():
     ws_bytes = egs.egs_loglik_workspace_bytes(n, tile, a.precision, a.band)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
 
+    xband = a.xband if a.precision == "fp32" else 0
+
     def step(timing):
         return egs.egs_loglik_ex(dlocs, dz, theta, n, a.precision, tile=tile, band=a.band, timing=timing,
-                                 workspace=ws, stream=stream)
+                                 workspace=ws, stream=stream, xband=xband)
 
     for _ in range(a.warmup):
         step(0)
@@ -594,7 +608,8 @@ def main():
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            egs.egs_loglik_ex(hl, hz, theta, n, a.precision, tile=tile, band=a.band, workspace=ws, stream=stream)
+            egs.egs_loglik_ex(hl, hz, theta, n, a.precision, tile=tile, band=a.band, workspace=ws, stream=stream,
+                              xband=xband)
         barrier()
         te = max_over_ranks(time.perf_counter() - t0, world, "cuda")
         e2e = {"value": whole_job_rate(e2e_steps, world, te), "unit": "evals/s",
@@ -638,7 +653,7 @@ def main():
             tc_flops = fc["update"] - f64_flops
             products = 1
             if a.precision == "fp32":
-                bo = band_out_flops(n, tile, a.band)
+                bo = band_out_flops(n, tile, a.band, xband)
                 tc_flops -= bo
                 f64_flops += bo
                 products = 3
@@ -662,8 +677,10 @@ def main():
                     "products_per_update": products,
                     "note": "achieved = algorithmic flops of the off-band trailing updates (2 b^3 per tile GEMM, the "
                             "n^3/3 convention) over the tcgen05 launches' event time (two launches per step: column "
-                            "k+1, then the rest); executed_* count the %d TF32/BF16 MMA product(s) per update that "
-                            "the kernel issues" % products}
+                            "k+1, then the rest); executed_* count the %d MMA product(s) per update that the kernel "
+                            "issues (%s)" % (products, {"fp32": "split FP16: lo hi' + hi lo' + hi hi' of row-scaled "
+                                                                "FP16 halves", "tf32": "one TF32 product",
+                                                        "bf16": "one BF16 product"}[a.precision])}
             upd64 = info2["ms_update_f64"]
             if upd64 > 0:
                 a64 = f64_flops / (upd64 / 1e3) / 1e12

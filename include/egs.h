@@ -127,7 +127,10 @@ typedef struct {
                               (longitude, latitude) in degrees by the haversine
                               formula (Section 7.4) on a sphere of 6371 km, so
                               theta2 is in km */
-    int32_t reserved;      /* 0 */
+    int32_t xband;         /* EGS_MIX_FP32 only: tiles with i - j < xband receive
+                              FP64-accurate updates (exact BF16 slice products)
+                              although those with i - j >= band are stored in
+                              FP32; 0 = band (must be >= band otherwise) */
 } egs_opts;
 
 /* One kernel launch of a traced evaluation (egs_opts.timing >= 3). */
@@ -411,6 +414,7 @@ typedef struct {
                               EGS_ERR_INACCURATE is run again in EGS_FP64
                               (ahead of the queue) and answered from that run;
                               its latency covers both */
+    int32_t xband;         /* EGS_MIX_FP32 requests: egs_opts.xband (0 = band) */
 } egs_serve_config;
 typedef struct {
     double p50_ms, p99_ms, mean_ms, evals_per_s;

@@ -52,7 +52,7 @@ class egs_info(ctypes.Structure):
 class egs_opts(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("band", ctypes.c_int32), ("refine", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
-                ("distance", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("distance", ctypes.c_int32), ("xband", ctypes.c_int32)]
 
 
 class egs_trace_rec(ctypes.Structure):
@@ -65,7 +65,7 @@ TRACE_CLASSES = ("generate", "potrf", "trsm", "update", "solve", "other", "updat
 
 class egs_serve_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("band", ctypes.c_int32), ("fallback_fp64", ctypes.c_int32)]
+                ("band", ctypes.c_int32), ("fallback_fp64", ctypes.c_int32), ("xband", ctypes.c_int32)]
 
 
 class egs_serve_stats(ctypes.Structure):
@@ -254,14 +254,15 @@ DISTANCES = {"euclidean": 0, "great_circle": 1}
 
 
 def egs_loglik_ex(locs, z, theta, n: int, precision="fp64", tile: int = 0, band: int = 0, refine: int = 0,
-                  timing: int = 0, workspace=None, stream=None, distance="euclidean") -> tuple:
+                  timing: int = 0, workspace=None, stream=None, distance="euclidean", xband: int = 0) -> tuple:
     """One evaluation of Eq. 1; returns (loglik, info dict).  distance
-    "great_circle": locations are (longitude, latitude) in degrees."""
+    "great_circle": locations are (longitude, latitude) in degrees.  xband
+    (FP32 mode): FP64-accurate updates for tiles with i - j < xband."""
     tp, _keep = _theta(theta)
     opts = egs_opts(tile=tile, band=band, refine=refine, timing=int(timing),
                     workspace=_ptr(workspace) if workspace is not None else None,
                     workspace_bytes=(workspace.numel() * workspace.element_size()) if workspace is not None else 0,
-                    distance=DISTANCES[distance])
+                    distance=DISTANCES[distance], xband=int(xband))
     out = ctypes.c_double()
     info = egs_info()
     st = load_library().egs_loglik_ex(_ptr(locs), _ptr(z), tp, n, _prec(precision), ctypes.byref(opts),
@@ -423,9 +424,10 @@ class egs_server:
     """Serving loop (C ABI egs_serve_*): resident fields, budgeted admission."""
 
     def __init__(self, hbm_budget_bytes: int, max_inflight: int = 4, tile: int = 0, band: int = 0,
-                 fallback_fp64: bool = False):
+                 fallback_fp64: bool = False, xband: int = 0):
         cfg = egs_serve_config(hbm_budget_bytes=int(hbm_budget_bytes), max_inflight=int(max_inflight),
-                               tile=int(tile), band=int(band), fallback_fp64=int(bool(fallback_fp64)))
+                               tile=int(tile), band=int(band), fallback_fp64=int(bool(fallback_fp64)),
+                               xband=int(xband))
         h = ctypes.c_void_p()
         _check(load_library().egs_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

@@ -151,6 +151,9 @@ egs_status eval_setup(int64_t n, const double *theta, egs_precision p, const egs
     int32_t tile = (opts && opts->tile) ? opts->tile : default_tile(n, p);
     if (!tile_ok(tile)) return set_error(EGS_ERR_ARG, "tile = %d must be a multiple of 64 in [64, 1024]", tile);
     es->band = (opts && opts->band > 0) ? opts->band : 2;
+    es->xband = (opts && opts->xband > 0) ? opts->xband : es->band;
+    if (es->xband < es->band)
+        return set_error(EGS_ERR_ARG, "xband = %d must be >= band = %d (or 0)", es->xband, es->band);
     es->refine = (opts && opts->refine) ? (opts->refine < 0 ? 0 : opts->refine) : 1;
     if (mixed_p(p) && tile % 256 != 0)
         return set_error(EGS_ERR_ARG, "mixed precision needs tile %% 256 == 0 (got %d)", tile);
@@ -216,6 +219,7 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
         mb.err = (int *)(ws + ML.err);
         mb.mtab = (double *)(ws + ML.mtab);
         mb.pctr = (unsigned *)(ws + ML.pctr);
+        mb.xband = es.xband;
         for (int i = 0; i < 2; ++i)
             mb.rs[i] = (float *)(ws + ML.rs + i * align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(float)));
         mb.l32 = (float *)(ws + ML.l32);

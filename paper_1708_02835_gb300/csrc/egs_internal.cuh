@@ -179,6 +179,7 @@ struct MixedBuffers {
     double *mtab;     // EGS_MT_DOUBLES: the generator's local polynomials (general nu)
     unsigned *pctr;   // T * potrf_diag_scratch_words(b): counters of the one-launch diagonal POTRFs
     float *rs[2];     // FP32 mode: the power-of-two scales of the split-FP16 panel rows, (T-1) b each
+    int xband;        // FP32 mode: tiles with i - j < xband get FP64-accurate updates (>= tl.band)
 };
 
 // One mixed-precision evaluation (fmt 3 = split TF32, 2 = TF32, 1 = BF16); the
@@ -196,7 +197,7 @@ struct MixedLayout {
 };
 struct EvalSetup {
     TileGeom g;
-    int band, refine;
+    int band, refine, xband;
     bool mixed;
     egs_precision p;
     Layout L;
@@ -238,8 +239,10 @@ cudaError_t launch_update_f64(const Tiles &tl, int k, int64_t ntri, DevStatus *s
 size_t ozaki_slices_bytes(int b, int T);
 cudaError_t make_ozaki_maps(const void *oz, int b, int T, CUtensorMap *mapA, CUtensorMap *mapB);
 // Band tiles of columns col0 .. col0 + ncols - 1 at step k.
-cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &mapB, const Tiles &tl, int k, int col0,
-                                  int ncols, const double *scale, int *err, cudaStream_t s, KernelTimer *kt);
+// xband >= tl.band: outputs m = n .. n + xband - 1 (those with m - n >= band
+// are FP32 tiles, updated in FP64 and rounded once).
+cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &mapB, const Tiles &tl, int xband, int k,
+                                  int col0, int ncols, const double *scale, int *err, cudaStream_t s, KernelTimer *kt);
 cudaError_t launch_forward_solve(const Tiles &tl, double *zpad, double *partials, DevStatus *st, cudaStream_t s,
                                  KernelTimer *kt);
 // z_m -= L_mk y_k for m > k, y_k read from ysrc (may equal zpad).
@@ -281,8 +284,9 @@ cudaError_t launch_trsm_tc(const CUtensorMap &mapA, const CUtensorMap &mapW, con
                            int k, int m0, int *err, cudaStream_t s, KernelTimer *kt);
 // fmt 4 (split FP16, the FP32 mode's update): rs holds the power-of-two
 // scale of every panel row (panel_f16_scales); NULL otherwise.
+// xband (fmt >= 3): outputs with m - n < xband are left to the FP64-accurate kernels.
 cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, const CUtensorMap &mapC, int fmt,
                              const Tiles &tl, int k, int *err, cudaStream_t s, KernelTimer *kt, int part = 0,
-                             const float *rs = nullptr);
+                             const float *rs = nullptr, int xband = 0);
 
 }  // namespace egs

@@ -99,8 +99,8 @@ __global__ void __launch_bounds__(256) k_panel_from_f64_split(Tiles tl, int k, v
     const size_t pr = (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // panel row
     const int m = k + 1 + (int)(pr / b);
     const double *x = tl.t64(m, k) + (pr % b) * b;
-    for (int c = threadIdx.x & 31; c < b; c += 32) panel_store<3>(panel, tl, pr, c, (float)x[c]);
-    slice_row(x, b, oz + pr * b, (size_t)(tl.T - 1) * b * b, ozs + pr);
+    const int e = slice_row(x, b, oz + pr * b, (size_t)(tl.T - 1) * b * b, ozs + pr);
+    panel_row_f16(x, b, e, reinterpret_cast<__half *>(panel), rs, pr);
 }
 
 // FP32 mode: solved off-band panel rows (tiles m0 .. T - 1 of column k, FP32)
@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(256) k_panel_from_f32_split(Tiles tl, int k, i
     const size_t pr = (size_t)(m0 - k - 1) * b + (size_t)blockIdx.x * 8 + (threadIdx.x >> 5);  // panel row
     const int m = k + 1 + (int)(pr / b);
     const float *x = tl.t32(m, k) + (pr % b) * b;
-    for (int c = threadIdx.x & 31; c < b; c += 32) panel_store<3>(panel, tl, pr, c, x[c]);
-    slice_row_f32(x, b, oz + pr * b, (size_t)(tl.T - 1) * b * b, ozs + pr);
+    const int e = slice_row_f32(x, b, oz + pr * b, (size_t)(tl.T - 1) * b * b, ozs + pr);
+    panel_row_f16(x, b, e, reinterpret_cast<__half *>(panel), rs, pr);
 }
 
 // FP32 mode, tensor-core TRSM: the unsolved off-band tiles (m0 .. T - 1, k)
@@ -646,15 +646,18 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         }
         // FP32 mode: band outputs with an FP32 operand by exact slices
         if (e == cudaSuccess && FMT == 3)
-            e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, k, k + 1, 1, ozs, mb.err, s, kt);
+            e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, mb.xband, k, k + 1, 1, ozs, mb.err, s, kt);
         // FP32 mode: the off-band update in split FP16 (fmt 4) from the scaled rows
-        const int ufmt = FMT == 3 ? 3 : FMT;
-        const float *urs = nullptr;
-        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, ufmt, tl, k, mb.err, s, kt, 1, urs);
+        const int ufmt = FMT == 3 ? 4 : FMT;
+        const float *urs = FMT == 3 ? mb.rs[k & 1] : nullptr;
+        if (e == cudaSuccess)
+            e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, ufmt, tl, k, mb.err, s, kt, 1, urs, mb.xband);
         if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);
         if (e == cudaSuccess && FMT == 3)
-            e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, k, k + 2, T - k - 2, ozs, mb.err, s, kt);
-        if (e == cudaSuccess) e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, ufmt, tl, k, mb.err, s, kt, 2, urs);
+            e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, mb.xband, k, k + 2, T - k - 2, ozs, mb.err, s,
+                                      kt);
+        if (e == cudaSuccess)
+            e = launch_update_tc(ma[k & 1], mbm[k & 1], mc, ufmt, tl, k, mb.err, s, kt, 2, urs, mb.xband);
     }
     if (kt) kt->step = -1;
     if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
@@ -712,7 +715,7 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     // update maps (FP32 mode: split FP16 over the panel buffers) and, in the
     // FP32 mode, split-TF32 maps over the same buffers for the TRSM's operand
     CUtensorMap ma[2], mbm[2], ma3[2], mb3, mc, moz[2][2];
-    const int ufmt = fmt;
+    const int ufmt = fmt == 3 ? 4 : fmt;
     e = make_panel_maps(mb.panel[0], ufmt, b, T, &ma[0], &mbm[0]);
     if (e == cudaSuccess) e = make_panel_maps(mb.panel[1], ufmt, b, T, &ma[1], &mbm[1]);
     for (int i = 0; i < 2 && e == cudaSuccess && fmt == 3; ++i) e = make_panel_maps(mb.panel[i], 3, b, T, &ma3[i], &mb3);

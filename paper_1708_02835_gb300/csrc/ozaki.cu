@@ -105,19 +105,21 @@ struct OzItem {
     int ya, yb;  // operand rows (within one slice) of the A and B boxes
 };
 
-// Band outputs of step k not covered by the FP64 band x band update: tiles
-// (m, n), n = col0 .. col0 + ncols - 1, m = n .. n + band - 1 < T, with
-// m - k >= band.  C_mn -= P_m P_n^T in FP64.
+// FP64-accurate outputs of step k not covered by the FP64 band x band
+// update: tiles (m, n), n = col0 .. col0 + ncols - 1, m = n .. n + xband - 1
+// < T, with m - k >= band (an FP32 panel operand).  C_mn -= P_m P_n^T in
+// FP64; tiles with m - n >= band are FP32 and take the FP64 result rounded
+// once.
 struct OzBandWork {
     Tiles tl;
-    int k, col0;
+    int k, col0, xband;
     __device__ bool decode(int64_t item, OzItem &w) const
     {
         const int nrb = tl.b / OBM, ncb = tl.b / OBN, per = nrb * ncb;
         const int64_t t = item / per;
         const int blk = (int)(item % per);
-        w.n = col0 + (int)(t / tl.band);
-        w.m = w.n + (int)(t % tl.band);
+        w.n = col0 + (int)(t / xband);
+        w.m = w.n + (int)(t % xband);
         w.rb = blk / ncb;
         w.cb = blk % ncb;
         if (w.m >= tl.T || w.m - k < tl.band) return false;
@@ -130,6 +132,21 @@ struct OzBandWork {
     __device__ void apply(const OzItem &w, int r, int ea, const int (&eb)[OBN], const float (&hi)[OBN],
                           const float (&lo)[OBN]) const
     {
+        if (!tl.is64(w.m, w.n)) {
+            float *C = tl.t32(w.m, w.n) + (size_t)(w.rb * OBM + r) * tl.b + w.cb * OBN;
+            float4 c[OBN / 4];
+#pragma unroll
+            for (int i = 0; i < OBN / 4; ++i) c[i] = *reinterpret_cast<const float4 *>(C + 4 * i);
+            float *cf = reinterpret_cast<float *>(c);
+#pragma unroll
+            for (int i = 0; i < OBN; ++i) {
+                const int e = ea + eb[i];
+                cf[i] = (float)(((double)cf[i] - f32_scaled(hi[i], e)) - f32_scaled(lo[i], e));
+            }
+#pragma unroll
+            for (int i = 0; i < OBN / 4; ++i) *reinterpret_cast<float4 *>(C + 4 * i) = c[i];
+            return;
+        }
         double *C = tl.t64(w.m, w.n) + (size_t)(w.rb * OBM + r) * tl.b + w.cb * OBN;
         double2 c[OBN / 2];
 #pragma unroll
@@ -400,14 +417,15 @@ cudaError_t make_ozaki_maps(const void *oz, int b, int T, CUtensorMap *mapA, CUt
     return e;
 }
 
-cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &mapB, const Tiles &tl, int k, int col0,
-                                  int ncols, const double *scale, int *err, cudaStream_t s, KernelTimer *kt)
+cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &mapB, const Tiles &tl, int xband, int k,
+                                  int col0, int ncols, const double *scale, int *err, cudaStream_t s, KernelTimer *kt)
 {
     if (ncols <= 0) return cudaSuccess;
+    if (xband < tl.band) xband = tl.band;
     const int64_t per = (int64_t)(tl.b / OBM) * (tl.b / OBN);
-    const int64_t items = (int64_t)ncols * tl.band * per;
+    const int64_t items = (int64_t)ncols * xband * per;
     const int R = (tl.T - 1) * tl.b;
-    OzBandWork w{tl, k, col0};
+    OzBandWork w{tl, k, col0, xband};
     cudaError_t e;
     if (kt) kt->begin(KC_UPDATE64, s);
     e = launch_ozaki(mapA, mapB, w, scale, scale, R, R, items, tl.b / OKC, err, s);

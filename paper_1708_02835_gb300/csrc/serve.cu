@@ -153,6 +153,7 @@ bool admit_one(egs_server *S, std::unique_lock<std::mutex> &lk)
     egs_opts o{};
     o.tile = S->cfg.tile;
     o.band = S->cfg.band;
+    if (rq.p == EGS_MIX_FP32 && S->cfg.xband > S->cfg.band) o.xband = S->cfg.xband;
     egs::EvalSetup es;
     if (egs::eval_setup(f.n, rq.theta, rq.p, &o, &es) != EGS_OK) {
         Result &r = S->results[rq.ticket];

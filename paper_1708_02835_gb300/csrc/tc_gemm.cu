@@ -78,6 +78,7 @@ struct UpdateWork {
     int one_col;
     int skip_band;
     const float *rs;  // split FP16: the power-of-two scale of every panel row
+    int xband;        // skip_band: outputs with m - n < xband are done by the FP64-accurate kernels
     __device__ float row_scale(int y) const { return rs[y]; }
     __device__ bool decode(int64_t bid, WorkItem &w) const
     {
@@ -117,7 +118,7 @@ struct UpdateWork {
         w.rb = blk / ncb;
         w.cb = blk % ncb;
         if (w.m - k < tl.band && w.n - k < tl.band) return false;         // FP64 band x band: done in FP64
-        if (skip_band && w.m - w.n < tl.band) return false;              // band output: done in FP64
+        if (skip_band && w.m - w.n < xband) return false;                // FP64-accurate output: done elsewhere
         if (w.m == w.n && w.cb * BN > w.rb * BM + BM - 1) return false;  // strictly above the diagonal
         w.ya = (w.m - k - 1) * tl.b + w.rb * BM;
         w.yb = (w.n - k - 1) * tl.b + w.cb * BN;
@@ -629,12 +630,12 @@ cudaError_t launch_trsm_tc(const CUtensorMap &mapA, const CUtensorMap &mapW, con
 
 cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, const CUtensorMap &mapC, int fmt,
                              const Tiles &tl, int k, int *err, cudaStream_t s, KernelTimer *kt, int part,
-                             const float *rs)
+                             const float *rs, int xband)
 {
     // part 0: every trailing tile; 1: column k + 1 only; 2: columns k + 2 .. T - 1
     const int64_t r = tl.T - k - 1;
     int64_t ntiles = 0;
-    UpdateWork w{tl, k, k + 1, 0, fmt >= 3 ? 1 : 0, rs};
+    UpdateWork w{tl, k, k + 1, 0, fmt >= 3 ? 1 : 0, rs, xband > tl.band ? xband : tl.band};
     if (part == 0) ntiles = r * (r + 1) / 2;
     else if (part == 1) {
         ntiles = r;

@@ -6,9 +6,10 @@
   the elementwise bar of the smaller tests), for nu = 1/2 and a general nu;
 * the IND approximation over the whole field (100 blocks of 1,024 points, the
   batched scheduler) against the oracle's per-block log-likelihoods, 1e-10;
-* the FP32-mode evaluation in the bench's launch configuration (band 3):
-  finite, bitwise reproducible, l assembled exactly from its log-det and
-  quadratic form, and a refinement step below the guard's 1e-5.
+* the FP32-mode evaluation in the bench's launch configuration (FP64 band of
+  2 tiles, FP64-accurate updates up to 2 tiles from the diagonal): finite,
+  bitwise reproducible, l assembled exactly from its log-det and quadratic
+  form, and a refinement step below the guard's 1e-5.
 """
 import math
 
@@ -73,8 +74,8 @@ def test_fp32_mode_bench_configuration(egs, field):
     from gpu_util import locs_dev, dev
     theta = (1.0, 0.1, 0.5)
     dl, dz = locs_dev(field), dev(ei.normal(0, N))
-    a, ia = egs.egs_loglik_ex(dl, dz, theta, N, "fp32", tile=B, band=3)
-    b, _ = egs.egs_loglik_ex(dl, dz, theta, N, "fp32", tile=B, band=3)
+    a, ia = egs.egs_loglik_ex(dl, dz, theta, N, "fp32", tile=B, band=2, xband=3)
+    b, _ = egs.egs_loglik_ex(dl, dz, theta, N, "fp32", tile=B, band=2, xband=3)
     assert math.isfinite(a) and a == b
     assembled = -0.5 * ia["quad"] - 0.5 * ia["logdet"] - 0.5 * N * math.log(2.0 * math.pi)
     assert abs(a - assembled) <= 1e-12 * abs(a)

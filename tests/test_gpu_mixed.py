@@ -138,3 +138,46 @@ def test_mixed_never_returns_a_gross_error(egs, prec, theta):
     rel = abs(ll - ref["loglik"]) / abs(ref["loglik"])
     print("%s theta=%s: rel l %.2e" % (prec, theta, rel))
     assert rel <= (5e-5 if prec == "fp32" else 1e-3), rel
+
+
+@pytest.mark.parametrize("n,theta,tile", [(4096, (1.0, 0.1, 0.5), 256), (4600, (1.5, 0.05, 0.6), 512)])
+def test_fp32_mode_extended_band(egs, n, theta, tile):
+    """FP64 band of 2 tiles with FP64-accurate (slice-product) updates of the
+    tiles one further from the diagonal (xband = 3), which stay FP32 in
+    storage: l within the FP32-mode bar of the oracle, and not worse than the
+    plain band-2 evaluation by more than rounding."""
+    from gpu_util import locs_dev, dev
+    locs, z, ref = _case(n, theta, 3)
+    l2, _ = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "fp32", tile=tile, band=2)
+    lx, ix = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "fp32", tile=tile, band=2, xband=3)
+    r2 = abs(l2 - ref["loglik"]) / abs(ref["loglik"])
+    rx = abs(lx - ref["loglik"]) / abs(ref["loglik"])
+    print("fp32 n=%d band 2: rel l %.2e; band 2 + xband 3: %.2e" % (n, r2, rx))
+    assert ix["band"] == 2
+    assert rx <= TOL["fp32"], rx
+    assert rx <= 2 * r2 + 1e-12
+
+
+def test_fp32_mode_extended_band_tracks_fp64_at_n16384(egs):
+    """As test_fp32_mode_tracks_fp64_at_n16384 with xband = 3 (band 2 storage)."""
+    from gpu_util import locs_dev, dev
+    import torch
+    n, theta = 16384, (1.0, 0.1, 0.5)
+    p = ei.Problem(n=n, theta=theta, seed=11)
+    locs = p.locations()
+    dl = locs_dev(locs)
+    z = torch.empty(n, dtype=torch.float64, device="cuda")
+    egs.egs_simulate(dl, dev(p.e()), theta, n, z, tile=512)
+    ll64, i64 = egs.egs_loglik_ex(dl, z, theta, n, "fp64", tile=512)
+    llx, ix = egs.egs_loglik_ex(dl, z, theta, n, "fp32", tile=512, band=2, xband=3)
+    rel = abs(llx - ll64) / abs(ll64)
+    print("fp32 n=16384 band 2 + xband 3: rel l %.2e  dlogdet %.3e" % (rel, ix["logdet"] - i64["logdet"]))
+    assert rel <= TOL["fp32"], rel
+
+
+def test_xband_below_band_is_rejected(egs):
+    from gpu_util import locs_dev, dev
+    locs = ei.jittered_grid(1000)
+    with pytest.raises(egs.EgsError) as e:
+        egs.egs_loglik_ex(locs_dev(locs), dev(np.ones(1000)), (1, 0.1, 0.5), 1000, "fp32", tile=256, band=3, xband=2)
+    assert e.value.status == egs.EGS_ERR_ARG

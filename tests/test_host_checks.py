@@ -70,6 +70,10 @@ def test_options_are_checked(lib):
     st = lib.egs_loglik_ex(LOCS.ctypes.data, Z.ctypes.data, th, N, 0, ctypes.byref(opts), ctypes.byref(out), None,
                            None)
     assert st == egs.EGS_ERR_ARG and "distance" in egs.egs_last_error()
+    opts = egs.egs_opts(band=3, xband=2)
+    st = lib.egs_loglik_ex(LOCS.ctypes.data, Z.ctypes.data, th, N, 1, ctypes.byref(opts), ctypes.byref(out), None,
+                           None)
+    assert st == egs.EGS_ERR_ARG and "xband" in egs.egs_last_error()
     need = egs.egs_loglik_workspace_bytes(N, 64, "fp64", 2)
     assert need > 0
     small = np.zeros(16, dtype=np.uint8)
