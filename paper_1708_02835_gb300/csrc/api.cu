@@ -98,8 +98,8 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
     if (mix_fmt(p) == 3)
         off += 2 * (align256(ozaki_slices_bytes(g.b, g.T)) +
                     align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(double)));
-    L.l32 = off;
-    off += align256(bb * sizeof(float));
+    L.l32 = off;  // TF32 / BF16: L_kk in FP32; FP32 mode: L_kk^T in FP64
+    off += align256(bb * sizeof(double));
     L.wsp = off;
     if (mix_fmt(p) == 3) off += align256(2 * bb * sizeof(float));
     L.vinv = off;
@@ -223,6 +223,7 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
         for (int i = 0; i < 2; ++i)
             mb.rs[i] = (float *)(ws + ML.rs + i * align256((size_t)(g.T > 1 ? g.T - 1 : 1) * g.b * sizeof(float)));
         mb.l32 = (float *)(ws + ML.l32);
+        mb.lt = (double *)(ws + ML.l32);
         mb.wsp = (float *)(ws + ML.wsp);
         mb.vinv = (double *)(ws + ML.vinv);
         const size_t ozb = align256(ozaki_slices_bytes(g.b, g.T));

@@ -172,6 +172,7 @@ struct MixedBuffers {
     double *partials; // 2T
     int *err;
     float *l32;       // b x b: L_kk rounded to FP32 for the off-band TRSM of step k (TF32 / BF16 modes)
+    double *lt;       // b x b, the same region: L_kk^T of step k (FP32 mode, for the inversion)
     float *wsp;       // FP32 mode: W = L_kk^-1 in split-TF32 layout, b rows of [hi | lo] (2b)
     double *vinv;     // T b x b: V_k = L_kk^-T (upper triangular) for the solves
     void *oz[2];      // FP32 mode: BF16 slices of the panel rows (ozaki_slices_bytes), step k uses k % 2
@@ -243,6 +244,10 @@ cudaError_t make_ozaki_maps(const void *oz, int b, int T, CUtensorMap *mapA, CUt
 // are FP32 tiles, updated in FP64 and rounded once).
 cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &mapB, const Tiles &tl, int xband, int k,
                                   int col0, int ncols, const double *scale, int *err, cudaStream_t s, KernelTimer *kt);
+// The band x band update of step k (tiles (m, n), k < n <= m <= k + nb) from
+// the slices of the FP64 band rows.
+cudaError_t launch_band_band_ozaki(const CUtensorMap &mapA, const CUtensorMap &mapB, const Tiles &tl, int k, int nb,
+                                   const double *scale, int *err, cudaStream_t s, KernelTimer *kt);
 cudaError_t launch_forward_solve(const Tiles &tl, double *zpad, double *partials, DevStatus *st, cudaStream_t s,
                                  KernelTimer *kt);
 // z_m -= L_mk y_k for m > k, y_k read from ysrc (may equal zpad).

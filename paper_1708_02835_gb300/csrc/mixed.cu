@@ -149,14 +149,16 @@ __global__ void __launch_bounds__(256) k_presplit_a(Tiles tl, int k, int m0, flo
 // every r > i.  Lane l keeps p_r of the rows r = l + 32 t in registers, so a
 // step's critical chain is one shuffle (w_i from its owner lane), one
 // multiply and the owner's update of row i + 1; the other rows' updates
-// overlap it.  Each p_r receives its terms in the order of i, so results are
+// overlap it.  Column i of L_kk is read as row i of LT = L_kk^T, one
+// contiguous 256-byte load per 32 rows (reading L_kk itself by columns cost
+// 32 cache lines per load).  Each p_r receives its terms in the order of i, so results are
 // bitwise reproducible.  Outputs: V_k = W^T (row j of V_k is w_j, the
 // upper-triangular inverse the solves use) and W in the split-TF32 layout
 // of the tensor-core TRSM (row c: [hi | lo] of (float) W[c][.]).
 // NT = b / 32 rows per lane.  Shared memory: (1 + warps) b doubles.
 template <int NT>
-__global__ void __launch_bounds__(128) k_inv_cols(Tiles tl, int k, double *__restrict__ V, float *__restrict__ wsp,
-                                                  const DevStatus *st)
+__global__ void __launch_bounds__(128) k_inv_cols(Tiles tl, int k, const double *__restrict__ LT,
+                                                  double *__restrict__ V, float *__restrict__ wsp, const DevStatus *st)
 {
     if (mfailed(st)) return;
     extern __shared__ double inv_sm[];
@@ -176,12 +178,12 @@ __global__ void __launch_bounds__(128) k_inv_cols(Tiles tl, int k, double *__res
         const int ii0 = j > 32 * s ? j - 32 * s : 0;
         double lc[NT];  // L[r][i] of the current step for the slots t >= s
 #pragma unroll
-        for (int t = s; t < NT; ++t) lc[t] = L[(size_t)(lane + 32 * t) * b + 32 * s + ii0];
+        for (int t = s; t < NT; ++t) lc[t] = LT[(size_t)(32 * s + ii0) * b + lane + 32 * t];
         for (int ii = ii0; ii < 32; ++ii) {
             const int i = 32 * s + ii;
             double ln[NT];  // the next step's column, loaded ahead
 #pragma unroll
-            for (int t = s; t < NT; ++t) ln[t] = (i + 1 < b) ? L[(size_t)(lane + 32 * t) * b + i + 1] : 0.0;
+            for (int t = s; t < NT; ++t) ln[t] = (i + 1 < b) ? LT[(size_t)(i + 1) * b + lane + 32 * t] : 0.0;
             const double wi = __shfl_sync(0xffffffffu, p[s], ii) * rinv[i];
             if (lane == 0) xs[i] = wi;
 #pragma unroll
@@ -204,17 +206,33 @@ __global__ void __launch_bounds__(128) k_inv_cols(Tiles tl, int k, double *__res
     }
 }
 
-cudaError_t launch_inv_cols(const Tiles &tl, int k, double *V, float *wsp, const DevStatus *st, cudaStream_t s,
-                            KernelTimer *kt)
+// LT = L_kk^T (32 x 32 blocks through shared memory), so that the inversion
+// reads a column of L_kk as one contiguous row.
+__global__ void __launch_bounds__(256) k_transpose_diag(Tiles tl, int k, double *__restrict__ LT, const DevStatus *st)
+{
+    __shared__ double blk[32][33];
+    if (mfailed(st)) return;
+    const int b = tl.b, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int r0 = 32 * (int)blockIdx.y, c0 = 32 * (int)blockIdx.x;
+    const double *L = tl.t64(k, k);
+    for (int r = ty; r < 32; r += 8) blk[r][tx] = L[(size_t)(r0 + r) * b + c0 + tx];
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) LT[(size_t)(c0 + r) * b + r0 + tx] = blk[tx][r];
+}
+
+cudaError_t launch_inv_cols(const Tiles &tl, int k, double *LT, double *V, float *wsp, const DevStatus *st,
+                            cudaStream_t s, KernelTimer *kt)
 {
     const int b = tl.b;
+    EGS_LAUNCH(kt, KC_TRSM, s,
+               k_transpose_diag<<<dim3((unsigned)(b / 32), (unsigned)(b / 32)), 256, 0, s>>>(tl, k, LT, st));
     const unsigned grid = (unsigned)(b / 4);
     const size_t sm = (size_t)5 * b * sizeof(double);
     switch (b / 32) {
-    case 8: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<8><<<grid, 128, sm, s>>>(tl, k, V, wsp, st)); break;
-    case 16: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<16><<<grid, 128, sm, s>>>(tl, k, V, wsp, st)); break;
-    case 24: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<24><<<grid, 128, sm, s>>>(tl, k, V, wsp, st)); break;
-    case 32: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<32><<<grid, 128, sm, s>>>(tl, k, V, wsp, st)); break;
+    case 8: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<8><<<grid, 128, sm, s>>>(tl, k, LT, V, wsp, st)); break;
+    case 16: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<16><<<grid, 128, sm, s>>>(tl, k, LT, V, wsp, st)); break;
+    case 24: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<24><<<grid, 128, sm, s>>>(tl, k, LT, V, wsp, st)); break;
+    case 32: EGS_LAUNCH(kt, KC_TRSM, s, k_inv_cols<32><<<grid, 128, sm, s>>>(tl, k, LT, V, wsp, st)); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -234,6 +252,89 @@ __global__ void __launch_bounds__(256) k_panel_from_f64(Tiles tl, int k, int nro
         panel_store<FMT>(panel, tl, (size_t)(m - k - 1) * tl.b + off / tl.b, (int)(off % tl.b),
                          (float)tl.t64(m, k)[off]);
     }
+}
+
+// FP64 TRSM of the band rows of step k (tiles (k+1 .. k+nb, k)): X L_kk^T = A,
+// solved in place.  A CTA keeps kTbR rows of one tile in shared memory and
+// sweeps the 32-column blocks of L_kk: block j first subtracts the solved
+// columns, X[:, 0:32j] L[32j:32j+32, 0:32j]^T, one 32 x 32 chunk of L at a
+// time (staged transposed in shared memory while the next chunk is loaded
+// into registers; two warps per row, each over half of a chunk), then one
+// warp per row solves the 32 x 32 diagonal block by column-oriented
+// substitution (one division and one shuffle per column).  b / kTbR CTAs per
+// tile spread the b^3 / 2 FMA of a tile over the GPU; the chain of the FP64
+// band is latency-bound, and this solve sits on it once per step.
+constexpr int kTbR = 4;
+static_assert(kTbR * 64 == 256, "two warps per row of the CTA");
+__global__ void __launch_bounds__(256) k_trsm_band_f64(Tiles tl, int k, const DevStatus *st)
+{
+    extern __shared__ double tb_xs[];  // kTbR x b: the CTA's rows
+    __shared__ double LcT[2][32][33];  // chunk (j, i) transposed: LcT[cc][cr] = L[32j + cr][32i + cc]
+    __shared__ double part[2][kTbR][32];
+    if (mfailed(st)) return;
+    const int b = tl.b, nblk = b >> 5, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r = tid >> 6, h = (tid >> 5) & 1;  // row of the CTA, half of a chunk
+    double *X = tl.t64(k + 1 + (int)blockIdx.y, k) + (size_t)blockIdx.x * kTbR * b;
+    const double *L = tl.t64(k, k);
+    for (int e = tid; e < kTbR * b; e += 256) tb_xs[e] = X[e];
+    double reg[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) reg[q] = L[(size_t)((tid >> 5) + 8 * q) * b + lane];  // chunk (0, 0)
+    double acc = 0.0;
+    int j = 0, i = 0, buf = 0;
+    for (;;) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) LcT[buf][lane][(tid >> 5) + 8 * q] = reg[q];
+        int jn = j, in = i + 1;
+        if (in > jn) {
+            ++jn;
+            in = 0;
+        }
+        if (jn < nblk) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) reg[q] = L[(size_t)(32 * jn + (tid >> 5) + 8 * q) * b + 32 * in + lane];
+        }
+        __syncthreads();
+        if (i < j) {
+            const double *xr = tb_xs + (size_t)r * b + 32 * i + 16 * h;
+#pragma unroll
+            for (int l = 0; l < 16; ++l) acc = fma(xr[l], LcT[buf][16 * h + l][lane], acc);
+        } else {
+            part[h][r][lane] = acc;
+            acc = 0.0;
+            __syncthreads();
+            if (warp < kTbR) {
+                double *xj = tb_xs + (size_t)warp * b + 32 * j;
+                double v = xj[lane] - (part[0][warp][lane] + part[1][warp][lane]);
+                for (int l = 0; l < 32; ++l) {
+                    double x = 0.0;
+                    if (lane == l) x = v / LcT[buf][l][l];
+                    x = __shfl_sync(0xffffffffu, x, l);
+                    if (lane > l) v = fma(-x, LcT[buf][l][lane], v);
+                    if (lane == l) v = x;
+                }
+                xj[lane] = v;
+            }
+        }
+        j = jn;
+        i = in;
+        buf ^= 1;
+        if (j >= nblk) break;
+    }
+    __syncthreads();
+    for (int e = tid; e < kTbR * b; e += 256) X[e] = tb_xs[e];
+}
+
+cudaError_t launch_trsm_band_f64(const Tiles &tl, int k, int nb, const DevStatus *st, cudaStream_t s, KernelTimer *kt)
+{
+    if (nb <= 0) return cudaSuccess;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_trsm_band_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, kTbR * 1024 * (int)sizeof(double));
+    if (e != cudaSuccess) return e;
+    EGS_LAUNCH(kt, KC_TRSM, s,
+               k_trsm_band_f64<<<dim3((unsigned)(tl.b / kTbR), (unsigned)nb), 256, (size_t)kTbR * tl.b * sizeof(double),
+                                 s>>>(tl, k, st));
+    return cudaGetLastError();
 }
 
 // L_kk rounded to FP32 once per step for the FP32 TRSM of the TF32 / BF16
@@ -551,10 +652,15 @@ namespace {
 // (POTRF, the band TRSM, the band rows' operands, then the FP64 band x band
 // update) runs on a side stream; the main stream runs the TRSM of the
 // off-band panel on the whole GPU and the tensor-core update of column k + 1,
-// signals the side stream (whose chain for step k + 1 needs only that column
-// and its own band x band update), and updates the rest of the trailing
-// matrix (leaving a few SMs free) while the next chain runs.  Panels (and in
-// FP32 mode the slices) alternate between two buffers.
+// signals the side stream, and updates the rest of the trailing matrix
+// (leaving a few SMs free) while the next chain runs.  Diagonal tile k + 1
+// is final once the chain's own band x band update of step k is done (every
+// other update of column k + 1 writes tiles below it), so POTRF(k + 1) does
+// not wait for the main stream: only the band TRSM of step k + 1, whose rows
+// column k + 1's other updates write, waits for its signal.  In the FP32 mode
+// the main stream's off-band TRSM (through L_kk^-1) starts once POTRF(k) is
+// done, beside the chain's band TRSM.  Panels (and in FP32 mode the slices)
+// alternate between two buffers.
 template <int FMT>
 cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CUtensorMap *mbm, const CUtensorMap *ma3,
                          const CUtensorMap &mc, const CUtensorMap (*moz)[2], const CUtensorMap *mw, DevStatus *st,
@@ -563,7 +669,7 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
     const Tiles &tl = mb.tl;
     const int T = tl.T, b = tl.b;
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_panel = nullptr, ev_col = nullptr;
+    cudaEvent_t ev_panel = nullptr, ev_col = nullptr, ev_potrf = nullptr;
     // The chain gates the next step, so its kernels take the SMs that the
     // main stream's kernels free first: the side stream runs at the highest
     // priority (otherwise each step's POTRF waits for the whole slice-product
@@ -573,6 +679,7 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_col, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_potrf, cudaEventDisableTiming);
     if (e == cudaSuccess)  // the one-launch diagonal POTRFs' counters
         e = cudaMemsetAsync(mb.pctr, 0, (size_t)T * potrf_diag_scratch_words(b) * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);  // the side stream starts after prior work on s
@@ -584,18 +691,23 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         void *panel = mb.panel[k & 1];
         __nv_bfloat16 *oz = (__nv_bfloat16 *)mb.oz[k & 1];
         double *ozs = mb.ozs[k & 1];
-        // ---- chain of step k on the side stream: POTRF, the FP64 band TRSM
-        // and the band rows' operands; then (after signalling the main
-        // stream) the FP64 band x band update
-        e = cudaStreamWaitEvent(side, ev_col, 0);
+        // ---- chain of step k on the side stream: POTRF (tile k was final
+        // after the chain's band x band update of step k - 1), then, once
+        // the main stream has updated column k, the FP64 band TRSM and the
+        // band rows' operands; then (after signalling the main stream) the
+        // FP64 band x band update.  At k = 0 ev_col marks the work on s
+        // before the call (Sigma generation).
+        if (k == 0) e = cudaStreamWaitEvent(side, ev_col, 0);
         if (e == cudaSuccess)
             e = launch_potrf_diag(tl, k, st, side, kts, mb.pctr + (size_t)k * potrf_diag_scratch_words(b));
+        if (e == cudaSuccess) e = cudaEventRecord(ev_potrf, side);
+        if (e == cudaSuccess && k > 0) e = cudaStreamWaitEvent(side, ev_col, 0);
         if (e == cudaSuccess && k + 1 < T) {
             if (nf > 0 && FMT != 3)
                 EGS_LAUNCH(kts, KC_TRSM, side,
                            k_l32_from_f64<<<(unsigned)((tl.bb() + 255) / 256 < 1024 ? (tl.bb() + 255) / 256 : 1024), 256,
                                             0, side>>>(tl, k, mb.l32, st));
-            e = launch_trsm_f64(tl, k, nb, st, side, kts);
+            e = launch_trsm_band_f64(tl, k, nb, st, side, kts);
             if (e == cudaSuccess && nb > 0) {
                 if (FMT == 3) {
                     EGS_LAUNCH(kts, KC_TRSM, side,
@@ -611,23 +723,28 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
             if (e == cudaSuccess) e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
-        // updates whose two operands are FP64 band tiles stay in FP64 (they
-        // carry the nearest-neighbour entries that set the diagonal pivots);
+        // updates whose two operands are FP64 band tiles stay FP64-accurate
+        // (they carry the nearest-neighbour entries that set the diagonal
+        // pivots): on DFMA, or in the FP32 mode as exact slice products;
         // their outputs are read by nothing else at this step
-        if (e == cudaSuccess && k + 1 < T)
-            e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, side, kts, KC_UPDATE64);
+        if (e == cudaSuccess && k + 1 < T) {
+            if (FMT == 3)  // FP32 mode: from the band rows' exact slices on tcgen05
+                e = launch_band_band_ozaki(moz[k & 1][0], moz[k & 1][1], tl, k, nb, ozs, mb.err, side, kts);
+            else
+                e = launch_update_f64(tl, k, (int64_t)nb * (nb + 1) / 2, st, side, kts, KC_UPDATE64);
+        }
         if (k + 1 == T || e != cudaSuccess) break;
         // ---- step k on the main stream: the off-band TRSM (whole GPU),
         // column k + 1, signal, then the rest
-        e = cudaStreamWaitEvent(s, ev_panel, 0);
+        e = cudaStreamWaitEvent(s, FMT == 3 ? ev_potrf : ev_panel, 0);
         if (FMT == 3) {
             // W = L_kk^-1 (and V_k = W^T for the solves), then X = A W^T on the
             // tensor cores: the unsolved tiles are split into the spare panel
-            // buffer (free until the next step's chain, which starts after
-            // column k + 1 below), the product overwrites them, and the solved
+            // buffer (free until the next step's chain writes its band rows,
+            // after column k + 1 below), the product overwrites them, and the solved
             // rows are split into this step's panel and slices
             const int m0 = k + 1 + nb;
-            if (e == cudaSuccess) e = launch_inv_cols(tl, k, mb.vinv, mb.wsp, st, s, kt);
+            if (e == cudaSuccess) e = launch_inv_cols(tl, k, mb.lt, mb.vinv, mb.wsp, st, s, kt);
             if (e == cudaSuccess && nf > 0) {
                 const size_t total4 = (size_t)nf * tl.bb() / 4;
                 const unsigned g4 = (unsigned)((total4 + 255) / 256 < 2048 ? (total4 + 255) / 256 : 2048);
@@ -644,6 +761,8 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
                        k_trsm_panel_f32<FMT><<<dim3((unsigned)nf, (unsigned)(b / 64)), 256, 0, s>>>(
                            tl, k, k + 1 + nb, mb.l32, panel, oz, ozs, st));
         }
+        // the band rows' operands (and slices) come from the chain
+        if (e == cudaSuccess && FMT == 3) e = cudaStreamWaitEvent(s, ev_panel, 0);
         // FP32 mode: band outputs with an FP32 operand by exact slices
         if (e == cudaSuccess && FMT == 3)
             e = launch_band_out_ozaki(moz[k & 1][0], moz[k & 1][1], tl, mb.xband, k, k + 1, 1, ozs, mb.err, s, kt);
@@ -663,13 +782,14 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
     if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_panel, 0);  // join the side stream
     // FP32 mode: V_k of the last diagonal tile (the others came with their TRSM)
-    if (e == cudaSuccess && FMT == 3) e = launch_inv_cols(tl, T - 1, mb.vinv, mb.wsp, st, s, kt);
+    if (e == cudaSuccess && FMT == 3) e = launch_inv_cols(tl, T - 1, mb.lt, mb.vinv, mb.wsp, st, s, kt);
     // destroying a stream or event with work still pending is legal: the
     // resources are released once that work completes, and s already waits
     // for it through ev_panel
     if (side) cudaStreamDestroy(side);
     if (ev_panel) cudaEventDestroy(ev_panel);
     if (ev_col) cudaEventDestroy(ev_col);
+    if (ev_potrf) cudaEventDestroy(ev_potrf);
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
 

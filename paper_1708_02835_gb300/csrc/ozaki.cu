@@ -109,10 +109,11 @@ struct OzItem {
 // update: tiles (m, n), n = col0 .. col0 + ncols - 1, m = n .. n + xband - 1
 // < T, with m - k >= band (an FP32 panel operand).  C_mn -= P_m P_n^T in
 // FP64; tiles with m - n >= band are FP32 and take the FP64 result rounded
-// once.
+// once.  With band_band set, the items are instead the band x band update
+// itself (m - k < band: both operands FP64 band tiles).
 struct OzBandWork {
     Tiles tl;
-    int k, col0, xband;
+    int k, col0, xband, band_band;
     __device__ bool decode(int64_t item, OzItem &w) const
     {
         const int nrb = tl.b / OBM, ncb = tl.b / OBN, per = nrb * ncb;
@@ -122,7 +123,7 @@ struct OzBandWork {
         w.m = w.n + (int)(t % xband);
         w.rb = blk / ncb;
         w.cb = blk % ncb;
-        if (w.m >= tl.T || w.m - k < tl.band) return false;
+        if (w.m >= tl.T || (w.m - k < tl.band) != (band_band != 0)) return false;
         if (w.m == w.n && w.cb * OBN > w.rb * OBM + OBM - 1) return false;  // strictly above the diagonal
         w.ya = (w.m - k - 1) * tl.b + w.rb * OBM;
         w.yb = (w.n - k - 1) * tl.b + w.cb * OBN;
@@ -425,7 +426,22 @@ cudaError_t launch_band_out_ozaki(const CUtensorMap &mapA, const CUtensorMap &ma
     const int64_t per = (int64_t)(tl.b / OBM) * (tl.b / OBN);
     const int64_t items = (int64_t)ncols * xband * per;
     const int R = (tl.T - 1) * tl.b;
-    OzBandWork w{tl, k, col0, xband};
+    OzBandWork w{tl, k, col0, xband, 0};
+    cudaError_t e;
+    if (kt) kt->begin(KC_UPDATE64, s);
+    e = launch_ozaki(mapA, mapB, w, scale, scale, R, R, items, tl.b / OKC, err, s);
+    if (kt) kt->end(KC_UPDATE64, s);
+    return e;
+}
+
+cudaError_t launch_band_band_ozaki(const CUtensorMap &mapA, const CUtensorMap &mapB, const Tiles &tl, int k, int nb,
+                                   const double *scale, int *err, cudaStream_t s, KernelTimer *kt)
+{
+    if (nb <= 0) return cudaSuccess;
+    const int64_t per = (int64_t)(tl.b / OBM) * (tl.b / OBN);
+    const int64_t items = (int64_t)nb * nb * per;
+    const int R = (tl.T - 1) * tl.b;
+    OzBandWork w{tl, k, k + 1, nb, 1};
     cudaError_t e;
     if (kt) kt->begin(KC_UPDATE64, s);
     e = launch_ozaki(mapA, mapB, w, scale, scale, R, R, items, tl.b / OKC, err, s);
