@@ -101,7 +101,7 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
     L.l32 = off;  // TF32 / BF16: L_kk in FP32; FP32 mode: L_kk^T in FP64
     off += align256(bb * sizeof(double));
     L.wsp = off;
-    if (mix_fmt(p) == 3) off += align256(2 * bb * sizeof(float));
+    if (mix_fmt(p) == 3) off += 2 * align256(2 * bb * sizeof(float));
     L.vinv = off;
     off += align256((size_t)g.T * bb * sizeof(double));
     L.locs = off;

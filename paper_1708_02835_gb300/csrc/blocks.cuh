@@ -482,15 +482,24 @@ template <typename E>
 __device__ __forceinline__ void gemv_rows(const E *__restrict__ A, int b, int r0, const double *ys,
                                           double *__restrict__ out)
 {
+    // the warp's 8 rows are swept together (8 loads in flight per lane); each
+    // row's sum keeps its order, so results equal a row-by-row sweep
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rr = 0; rr < 8; ++rr) {
-        const int r = r0 + warp * 8 + rr;
-        const E *row = A + (size_t)r * b;
-        double s = 0.0;
-        for (int c = lane; c < b; c += 32) s = fma((double)row[c], ys[c], s);
+    const E *rows = A + (size_t)(r0 + warp * 8) * b;
+    double s[8];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) out[r] -= s;
+    for (int rr = 0; rr < 8; ++rr) s[rr] = 0.0;
+    for (int c = lane; c < b; c += 32) {
+        const double y = ys[c];
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) s[rr] = fma((double)rows[(size_t)rr * b + c], y, s[rr]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) {
+        double v = s[rr];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) out[r0 + warp * 8 + rr] -= v;
     }
 }
 
@@ -531,9 +540,14 @@ __device__ __forceinline__ void trsv_bwd_tile(const double *__restrict__ L, int 
 __device__ __forceinline__ double col_dot(const double *__restrict__ A, int b, int c, int g, const double *xs,
                                           const float *)
 {
-    double s = 0.0;
-    for (int r = g; r < b; r += 4) s = fma(A[(size_t)r * b + c], xs[r], s);
-    return s;
+    // four independent partial sums (rows g + 4 u mod 16) keep four loads in
+    // flight; they are combined in a fixed order
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int r = g; r < b; r += 16) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] = fma(A[(size_t)(r + 4 * u) * b + c], xs[r + 4 * u], s[u]);
+    }
+    return (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 // Off-band (FP32) tiles: products and the partial sum in FP32 (the tile is
@@ -541,9 +555,12 @@ __device__ __forceinline__ double col_dot(const double *__restrict__ A, int b, i
 __device__ __forceinline__ double col_dot(const float *__restrict__ A, int b, int c, int g, const double *,
                                           const float *xs32)
 {
-    float s = 0.0f;
-    for (int r = g; r < b; r += 4) s = fmaf(A[(size_t)r * b + c], xs32[r], s);
-    return (double)s;
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int r = g; r < b; r += 16) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] = fmaf(A[(size_t)(r + 4 * u) * b + c], xs32[r + 4 * u], s[u]);
+    }
+    return (double)((s[0] + s[1]) + (s[2] + s[3]));
 }
 
 // vj[c0 .. c0+63] -= (L_kj^T xk)[c0 .. c0+63] for one tile (FP64 or FP32):
@@ -575,14 +592,21 @@ __device__ __forceinline__ void gemv_rows_f32(const float *__restrict__ A, int b
                                               double *__restrict__ out)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rr = 0; rr < 8; ++rr) {
-        const int r = r0 + warp * 8 + rr;
-        const float *row = A + (size_t)r * b;
-        float s = 0.0f;
-        for (int c = lane; c < b; c += 32) s = fmaf(row[c], ys32[c], s);
+    const float *rows = A + (size_t)(r0 + warp * 8) * b;
+    float s[8];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) out[r] -= (double)s;
+    for (int rr = 0; rr < 8; ++rr) s[rr] = 0.0f;
+    for (int c = lane; c < b; c += 32) {
+        const float y = ys32[c];
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) s[rr] = fmaf(rows[(size_t)rr * b + c], y, s[rr]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) {
+        float v = s[rr];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) out[r0 + warp * 8 + rr] -= (double)v;
     }
 }
 

@@ -173,7 +173,8 @@ struct MixedBuffers {
     int *err;
     float *l32;       // b x b: L_kk rounded to FP32 for the off-band TRSM of step k (TF32 / BF16 modes)
     double *lt;       // b x b, the same region: L_kk^T of step k (FP32 mode, for the inversion)
-    float *wsp;       // FP32 mode: W = L_kk^-1 in split-TF32 layout, b rows of [hi | lo] (2b)
+    float *wsp;       // FP32 mode: W = L_kk^-1 in split-TF32 layout, b rows of [hi | lo] (2b); two such
+                      // buffers of 2 b^2 floats, step k uses k % 2
     double *vinv;     // T b x b: V_k = L_kk^-T (upper triangular) for the solves
     void *oz[2];      // FP32 mode: BF16 slices of the panel rows (ozaki_slices_bytes), step k uses k % 2
     double *ozs[2];   // FP32 mode: their row scales, (T-1) b doubles each

@@ -172,25 +172,34 @@ __global__ void __launch_bounds__(128) k_inv_cols(Tiles tl, int k, const double 
     double p[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) p[t] = (lane + 32 * t == j) ? 1.0 : 0.0;
+    // rows i .. i + D - 1 of LT in registers: a row is loaded D steps before
+    // its use, which hides the L2 latency behind D steps of FMAs
+    constexpr int D = NT <= 16 ? 4 : (NT <= 24 ? 2 : 1);
+    double ring[D][NT];
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int t = 0; t < NT; ++t) ring[d][t] = (j + d < b) ? LT[(size_t)(j + d) * b + lane + 32 * t] : 0.0;
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
         if (32 * s + 31 < j) continue;  // rows of this slot lie above j: w = 0 there
         const int ii0 = j > 32 * s ? j - 32 * s : 0;
-        double lc[NT];  // L[r][i] of the current step for the slots t >= s
-#pragma unroll
-        for (int t = s; t < NT; ++t) lc[t] = LT[(size_t)(32 * s + ii0) * b + lane + 32 * t];
         for (int ii = ii0; ii < 32; ++ii) {
             const int i = 32 * s + ii;
-            double ln[NT];  // the next step's column, loaded ahead
+            double nx[NT];  // row i + D
 #pragma unroll
-            for (int t = s; t < NT; ++t) ln[t] = (i + 1 < b) ? LT[(size_t)(i + 1) * b + lane + 32 * t] : 0.0;
+            for (int t = s; t < NT; ++t) nx[t] = (i + D < b) ? LT[(size_t)(i + D) * b + lane + 32 * t] : 0.0;
             const double wi = __shfl_sync(0xffffffffu, p[s], ii) * rinv[i];
             if (lane == 0) xs[i] = wi;
 #pragma unroll
             for (int t = s; t < NT; ++t)
-                if (lane + 32 * t > i) p[t] = fma(-lc[t], wi, p[t]);
+                if (lane + 32 * t > i) p[t] = fma(-ring[0][t], wi, p[t]);
 #pragma unroll
-            for (int t = s; t < NT; ++t) lc[t] = ln[t];
+            for (int t = s; t < NT; ++t) {
+#pragma unroll
+                for (int d = 0; d + 1 < D; ++d) ring[d][t] = ring[d + 1][t];
+                ring[D - 1][t] = nx[t];
+            }
         }
     }
     __syncwarp();
@@ -261,9 +270,10 @@ __global__ void __launch_bounds__(256) k_panel_from_f64(Tiles tl, int k, int nro
 // time (staged transposed in shared memory while the next chunk is loaded
 // into registers; two warps per row, each over half of a chunk), then one
 // warp per row solves the 32 x 32 diagonal block by column-oriented
-// substitution (one division and one shuffle per column).  b / kTbR CTAs per
-// tile spread the b^3 / 2 FMA of a tile over the GPU; the chain of the FP64
-// band is latency-bound, and this solve sits on it once per step.
+// substitution (a shuffle, a multiplication by 1 / L_ii and an FMA per
+// column).  b / kTbR CTAs per tile spread the b^3 / 2 FMA of a tile over the
+// GPU; the chain of the FP64 band is latency-bound, and this solve sits on it
+// once per step.
 constexpr int kTbR = 4;
 static_assert(kTbR * 64 == 256, "two warps per row of the CTA");
 __global__ void __launch_bounds__(256) k_trsm_band_f64(Tiles tl, int k, const DevStatus *st)
@@ -271,12 +281,14 @@ __global__ void __launch_bounds__(256) k_trsm_band_f64(Tiles tl, int k, const De
     extern __shared__ double tb_xs[];  // kTbR x b: the CTA's rows
     __shared__ double LcT[2][32][33];  // chunk (j, i) transposed: LcT[cc][cr] = L[32j + cr][32i + cc]
     __shared__ double part[2][kTbR][32];
+    __shared__ double rdg[1024];  // 1 / L_ii
     if (mfailed(st)) return;
     const int b = tl.b, nblk = b >> 5, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int r = tid >> 6, h = (tid >> 5) & 1;  // row of the CTA, half of a chunk
     double *X = tl.t64(k + 1 + (int)blockIdx.y, k) + (size_t)blockIdx.x * kTbR * b;
     const double *L = tl.t64(k, k);
     for (int e = tid; e < kTbR * b; e += 256) tb_xs[e] = X[e];
+    for (int e = tid; e < b; e += 256) rdg[e] = 1.0 / L[(size_t)e * b + e];
     double reg[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) reg[q] = L[(size_t)((tid >> 5) + 8 * q) * b + lane];  // chunk (0, 0)
@@ -307,11 +319,11 @@ __global__ void __launch_bounds__(256) k_trsm_band_f64(Tiles tl, int k, const De
                 double *xj = tb_xs + (size_t)warp * b + 32 * j;
                 double v = xj[lane] - (part[0][warp][lane] + part[1][warp][lane]);
                 for (int l = 0; l < 32; ++l) {
-                    double x = 0.0;
-                    if (lane == l) x = v / LcT[buf][l][l];
-                    x = __shfl_sync(0xffffffffu, x, l);
-                    if (lane > l) v = fma(-x, LcT[buf][l][lane], v);
-                    if (lane == l) v = x;
+                    // every lane forms x_l (a warp-wide FP64 instruction costs
+                    // the same with one lane active or all 32)
+                    const double x = __shfl_sync(0xffffffffu, v, l) * rdg[32 * j + l];
+                    const double u = fma(-x, LcT[buf][l][lane], v);
+                    v = lane > l ? u : (lane == l ? x : v);
                 }
                 xj[lane] = v;
             }
@@ -482,7 +494,8 @@ __global__ void __launch_bounds__(256) k_logdet_tiles(Tiles tl, double *__restri
     if (threadIdx.x == 0) partials[k] = tot;
 }
 
-// out_k = V_k^T rhs_k (= L_kk^-1 rhs_k): 64 columns x 4 row groups per CTA,
+// out_k = V_k^T rhs_k (= L_kk^-1 rhs_k): 16 columns x 16 row groups per CTA
+// (b / 16 CTAs: the product is FP64-bound, so it is spread over many SMs),
 // rows r <= c only (V_k is upper triangular), fixed-order reduction.
 __global__ void __launch_bounds__(256) k_fwd_inv(const double *__restrict__ V, int b, int k,
                                                  const double *__restrict__ rhs, double *__restrict__ out,
@@ -490,21 +503,26 @@ __global__ void __launch_bounds__(256) k_fwd_inv(const double *__restrict__ V, i
 {
     if (mfailed(st)) return;
     __shared__ double xs[1024];
-    __shared__ double red[4][64];
+    __shared__ double red[16][17];
     const double *Vk = V + (size_t)k * b * b;
-    const int c0 = (int)blockIdx.x * 64, tx = threadIdx.x & 63, g = threadIdx.x >> 6;
-    for (int r = threadIdx.x; r < b; r += 256) xs[r] = rhs[(size_t)k * b + r];
+    const int c0 = (int)blockIdx.x * 16, tx = threadIdx.x & 15, g = threadIdx.x >> 4;
+    for (int r = threadIdx.x; r < c0 + 16; r += 256) xs[r] = rhs[(size_t)k * b + r];
     __syncthreads();
     const int c = c0 + tx;
     double sacc = 0.0;
-    for (int r = g; r < c0 + 64; r += 4) sacc = fma(Vk[(size_t)r * b + c], xs[r], sacc);
+#pragma unroll 4
+    for (int r = g; r < c0 + 16; r += 16) sacc = fma(Vk[(size_t)r * b + c], xs[r], sacc);
     red[g][tx] = sacc;
     __syncthreads();
-    if (g == 0) out[(size_t)k * b + c] = ((red[0][tx] + red[1][tx]) + red[2][tx]) + red[3][tx];
+    if (g == 0) {
+        double t = red[0][tx];
+#pragma unroll
+        for (int q = 1; q < 16; ++q) t += red[q][tx];
+        out[(size_t)k * b + c] = t;
+    }
 }
-
-// out_k = V_k rhs_k (= L_kk^-T rhs_k): one warp per 8 rows, columns c >= r,
-// fixed shuffle tree.
+// out_k = V_k rhs_k (= L_kk^-T rhs_k): one row per warp (b / 8 CTAs), columns
+// c >= r, fixed shuffle tree.
 __global__ void __launch_bounds__(256) k_bwd_inv(const double *__restrict__ V, int b, int k,
                                                  const double *__restrict__ rhs, double *__restrict__ out,
                                                  const DevStatus *st)
@@ -515,15 +533,13 @@ __global__ void __launch_bounds__(256) k_bwd_inv(const double *__restrict__ V, i
     for (int c = threadIdx.x; c < b; c += 256) xs[c] = rhs[(size_t)k * b + c];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int rr = 0; rr < 8; ++rr) {
-        const int r = (int)blockIdx.x * 64 + warp * 8 + rr;
-        const double *row = Vk + (size_t)r * b;
-        double sacc = 0.0;
-        for (int c = (r & ~31) + lane; c < b; c += 32) sacc = fma(row[c], xs[c], sacc);  // row[c] = 0 for c < r
+    const int r = (int)blockIdx.x * 8 + warp;
+    const double *row = Vk + (size_t)r * b;
+    double sacc = 0.0;
+    for (int c = (r & ~31) + lane; c < b; c += 32) sacc = fma(row[c], xs[c], sacc);  // row[c] = 0 for c < r
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
-        if (lane == 0) out[(size_t)k * b + r] = sacc;
-    }
+    for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+    if (lane == 0) out[(size_t)k * b + r] = sacc;
 }
 
 // Sigma x, row part: rows[i*b + r] = sum_{j <= i} Sigma_ij[r][:] . x_j over the
@@ -658,9 +674,10 @@ namespace {
 // other update of column k + 1 writes tiles below it), so POTRF(k + 1) does
 // not wait for the main stream: only the band TRSM of step k + 1, whose rows
 // column k + 1's other updates write, waits for its signal.  In the FP32 mode
-// the main stream's off-band TRSM (through L_kk^-1) starts once POTRF(k) is
-// done, beside the chain's band TRSM.  Panels (and in FP32 mode the slices)
-// alternate between two buffers.
+// the chain also inverts L_kk right after POTRF(k) (a latency-bound kernel
+// kept off the main stream), and the main stream's off-band TRSM through
+// L_kk^-1 starts once that is done, beside the chain's band TRSM.  Panels,
+// W (and in FP32 mode the slices) alternate between two buffers.
 template <int FMT>
 cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CUtensorMap *mbm, const CUtensorMap *ma3,
                          const CUtensorMap &mc, const CUtensorMap (*moz)[2], const CUtensorMap *mw, DevStatus *st,
@@ -669,7 +686,7 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
     const Tiles &tl = mb.tl;
     const int T = tl.T, b = tl.b;
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_panel = nullptr, ev_col = nullptr, ev_potrf = nullptr;
+    cudaEvent_t ev_panel = nullptr, ev_col = nullptr, ev_diag = nullptr;
     // The chain gates the next step, so its kernels take the SMs that the
     // main stream's kernels free first: the side stream runs at the highest
     // priority (otherwise each step's POTRF waits for the whole slice-product
@@ -679,7 +696,7 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, prio_greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_panel, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_col, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_potrf, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_diag, cudaEventDisableTiming);
     if (e == cudaSuccess)  // the one-launch diagonal POTRFs' counters
         e = cudaMemsetAsync(mb.pctr, 0, (size_t)T * potrf_diag_scratch_words(b) * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaEventRecord(ev_col, s);  // the side stream starts after prior work on s
@@ -700,7 +717,11 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         if (k == 0) e = cudaStreamWaitEvent(side, ev_col, 0);
         if (e == cudaSuccess)
             e = launch_potrf_diag(tl, k, st, side, kts, mb.pctr + (size_t)k * potrf_diag_scratch_words(b));
-        if (e == cudaSuccess) e = cudaEventRecord(ev_potrf, side);
+        // FP32 mode: W = L_kk^-1 (and V_k = W^T for the solves) for the main
+        // stream's off-band TRSM, off the main stream
+        float *wsp = mb.wsp + (size_t)(k & 1) * 2 * tl.bb();
+        if (e == cudaSuccess && FMT == 3) e = launch_inv_cols(tl, k, mb.lt, mb.vinv, wsp, st, side, kts);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_diag, side);
         if (e == cudaSuccess && k > 0) e = cudaStreamWaitEvent(side, ev_col, 0);
         if (e == cudaSuccess && k + 1 < T) {
             if (nf > 0 && FMT != 3)
@@ -736,21 +757,20 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
         if (k + 1 == T || e != cudaSuccess) break;
         // ---- step k on the main stream: the off-band TRSM (whole GPU),
         // column k + 1, signal, then the rest
-        e = cudaStreamWaitEvent(s, FMT == 3 ? ev_potrf : ev_panel, 0);
+        e = cudaStreamWaitEvent(s, FMT == 3 ? ev_diag : ev_panel, 0);
         if (FMT == 3) {
-            // W = L_kk^-1 (and V_k = W^T for the solves), then X = A W^T on the
-            // tensor cores: the unsolved tiles are split into the spare panel
+            // X = A W^T on the tensor cores with W = L_kk^-1 from the chain
+            // stream: the unsolved tiles are split into the spare panel
             // buffer (free until the next step's chain writes its band rows,
             // after column k + 1 below), the product overwrites them, and the solved
             // rows are split into this step's panel and slices
             const int m0 = k + 1 + nb;
-            if (e == cudaSuccess) e = launch_inv_cols(tl, k, mb.lt, mb.vinv, mb.wsp, st, s, kt);
             if (e == cudaSuccess && nf > 0) {
                 const size_t total4 = (size_t)nf * tl.bb() / 4;
                 const unsigned g4 = (unsigned)((total4 + 255) / 256 < 2048 ? (total4 + 255) / 256 : 2048);
                 EGS_LAUNCH(kt, KC_TRSM, s,
                            k_presplit_a<<<g4, 256, 0, s>>>(tl, k, m0, (float *)mb.panel[(k + 1) & 1], st));
-                e = launch_trsm_tc(ma3[(k + 1) & 1], *mw, mc, tl, k, m0, mb.err, s, kt);
+                e = launch_trsm_tc(ma3[(k + 1) & 1], mw[k & 1], mc, tl, k, m0, mb.err, s, kt);
                 if (e == cudaSuccess)
                     EGS_LAUNCH(kt, KC_TRSM, s,
                                k_panel_from_f32_split<<<(unsigned)((size_t)nf * b / 8), 256, 0, s>>>(
@@ -781,15 +801,13 @@ cudaError_t factor_mixed(const MixedBuffers &mb, const CUtensorMap *ma, const CU
     if (kt) kt->step = -1;
     if (e == cudaSuccess) e = cudaEventRecord(ev_panel, side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_panel, 0);  // join the side stream
-    // FP32 mode: V_k of the last diagonal tile (the others came with their TRSM)
-    if (e == cudaSuccess && FMT == 3) e = launch_inv_cols(tl, T - 1, mb.lt, mb.vinv, mb.wsp, st, s, kt);
     // destroying a stream or event with work still pending is legal: the
     // resources are released once that work completes, and s already waits
     // for it through ev_panel
     if (side) cudaStreamDestroy(side);
     if (ev_panel) cudaEventDestroy(ev_panel);
     if (ev_col) cudaEventDestroy(ev_col);
-    if (ev_potrf) cudaEventDestroy(ev_potrf);
+    if (ev_diag) cudaEventDestroy(ev_diag);
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
@@ -798,7 +816,7 @@ cudaError_t forward_solve_inv(const Tiles &tl, const double *V, double *rhs, dou
                               cudaStream_t s, KernelTimer *kt)
 {
     for (int k = 0; k < tl.T; ++k) {
-        EGS_LAUNCH(kt, KC_TRSV, s, k_fwd_inv<<<(unsigned)(tl.b / 64), 256, 0, s>>>(V, tl.b, k, rhs, out, st));
+        EGS_LAUNCH(kt, KC_TRSV, s, k_fwd_inv<<<(unsigned)(tl.b / 16), 256, 0, s>>>(V, tl.b, k, rhs, out, st));
         cudaError_t e = launch_gemv_panel(tl, k, out, rhs, st, s, kt);
         if (e != cudaSuccess) return e;
     }
@@ -810,7 +828,7 @@ cudaError_t backward_solve_inv(const Tiles &tl, const double *V, double *rhs, do
                                cudaStream_t s, KernelTimer *kt)
 {
     for (int k = tl.T - 1; k >= 0; --k) {
-        EGS_LAUNCH(kt, KC_TRSV, s, k_bwd_inv<<<(unsigned)(tl.b / 64), 256, 0, s>>>(V, tl.b, k, rhs, out, st));
+        EGS_LAUNCH(kt, KC_TRSV, s, k_bwd_inv<<<(unsigned)(tl.b / 8), 256, 0, s>>>(V, tl.b, k, rhs, out, st));
         if (k > 0)
             EGS_LAUNCH(kt, KC_TRSV, s,
                        k_gemv_T<<<dim3((unsigned)k, (unsigned)(tl.b / 64)), 256, 0, s>>>(tl, k, out, rhs, st));
@@ -842,10 +860,11 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     if (e == cudaSuccess) e = make_offband_map(tl.f32, b, Tiles::f32_tiles(T, tl.band), &mc);
     for (int i = 0; i < 2 && e == cudaSuccess && fmt == 3; ++i) e = make_ozaki_maps(mb.oz[i], b, T, &moz[i][0], &moz[i][1]);
     if (e != cudaSuccess) return e;
-    CUtensorMap mw;
-    if (fmt == 3) e = make_trsm_w_map(mb.wsp, b, &mw);
+    CUtensorMap mw[2];
+    for (int i = 0; i < 2 && e == cudaSuccess && fmt == 3; ++i)
+        e = make_trsm_w_map(mb.wsp + (size_t)i * 2 * tl.bb(), b, &mw[i]);
     if (e != cudaSuccess) return e;
-    if (fmt == 3) e = factor_mixed<3>(mb, ma, mbm, ma3, mc, moz, &mw, st, s, kt);
+    if (fmt == 3) e = factor_mixed<3>(mb, ma, mbm, ma3, mc, moz, mw, st, s, kt);
     else if (fmt == 2) e = factor_mixed<2>(mb, ma, mbm, ma3, mc, moz, nullptr, st, s, kt);
     else e = factor_mixed<1>(mb, ma, mbm, ma3, mc, moz, nullptr, st, s, kt);
     if (e != cudaSuccess) return e;
