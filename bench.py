@@ -41,8 +41,9 @@ if ROOT not in sys.path:
 
 METRIC = "loglik evals/s & POTRF TFLOP/s at n=102400 FP64 vs mixed; serve p50/p99 ms"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x flop/FMA x max clock
-# k_tc_gemm, split TF32: 5.30 GB of DRAM traffic for 1.425e12 flop in one launch (ncu)
-SPLIT_TF32_DRAM_BYTES_PER_FLOP = 5.297e9 / 1.425e12
+# k_tc_gemm, split FP16 update: 3.559 GB of DRAM traffic (1.888 read + 1.671 written) for 1.331e12
+# executed flop in one launch (ncu; n = 32,768, tile 512, the bulk update of step 2: 1,653 output tiles)
+SPLIT_F16_DRAM_BYTES_PER_FLOP = 3.559e9 / 1.3312e12
 
 
 def parse():
@@ -506,8 +507,8 @@ def fp64_leg(a, egs, dlocs, dz, theta, stream) -> dict:
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     upd = info["ms_update"]
-    achieved = fc["update"] / (upd / 1e3) / 1e12
-    nlaunch = fc["T"] - 1
+    achieved = fc["update"] / (upd / 1e3) / 1e12 if upd > 0 else 0.0  # one tile: no trailing update
+    nlaunch = max(fc["T"] - 1, 1)
     return {"evals_per_s": 1e3 / ms, "ms_per_eval": ms, "loglik": ll, "logdet": info["logdet"], "quad": info["quad"],
             "potrf_tflops": fc["total_n3"] / (info["ms_factor"] / 1e3) / 1e12,
             "phase_ms": {"generate": info["ms_generate"], "factor": info["ms_factor"], "solve": info["ms_solve"]},
@@ -634,12 +635,12 @@ def main():
         ms_step = ms_max / a.steps
         ms_factor = statistics.mean(i["ms_factor"] for i in infos)
         upd_ms = info2["ms_update"]
-        launches_update = fc["T"] - 1
+        launches_update = max(fc["T"] - 1, 1)
         classes = {k: info2["ms_" + k] for k in ("update", "update_f64", "potrf", "trsm", "trsv", "generate")}
         classes["note"] = ("one extra untimed step with CUDA events around every launch; classes on the side "
                            "stream include time spent waiting for SMs")
         if a.precision == "fp64":
-            achieved = fc["update"] / (upd_ms / 1e3) / 1e12
+            achieved = fc["update"] / (upd_ms / 1e3) / 1e12 if upd_ms > 0 else 0.0
             roof = {"bound": "alu", "kernel": "k_update_f64 (SYRK/GEMM trailing update)", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe, no tensor path)",
@@ -657,13 +658,15 @@ def main():
                 tc_flops -= bo
                 f64_flops += bo
                 products = 3
-            executed = products * tc_flops / (upd_ms / 1e3) / 1e12
-            achieved = tc_flops / (upd_ms / 1e3) / 1e12
+            upd_s = upd_ms / 1e3 if upd_ms > 0 else float("inf")  # one tile: no trailing update
+            executed = products * tc_flops / upd_s / 1e12
+            achieved = tc_flops / upd_s / 1e12
             peak = tensor_peak(a.precision, sustained=True)
             peak_burst = tensor_peak(a.precision, sustained=False)
-            # DRAM bytes per executed flop of the split-TF32 update from an ncu
+            # DRAM bytes per executed flop of the split-FP16 update from an ncu
             # capture at n = 32,768, scaled to this launch size by its flops
-            traffic = SPLIT_TF32_DRAM_BYTES_PER_FLOP * products * tc_flops / (2 * launches_update) \
+            # (the output tiles' reduce-adds dominate and grow with the flops)
+            traffic = SPLIT_F16_DRAM_BYTES_PER_FLOP * products * tc_flops / (2 * launches_update) \
                 if a.precision == "fp32" else None
             roof = {"bound": "tensor", "kernel": "k_tc_gemm (tcgen05 trailing update, %s)" % a.precision,
                     "achieved": achieved, "peak": peak["tflops"], "unit": "TFLOP/s", "frac": achieved / peak["tflops"],

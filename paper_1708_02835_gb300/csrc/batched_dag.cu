@@ -62,7 +62,7 @@ struct GenSmem {
 
 union DagSmem {
     TrsmSmem<64, double> trsm;
-    TrsmSmem<32, double> trsm32;
+    Trsm32Smem trsm32;
     PotrfSmem<32> potrf32;
     GemmSmem<double> gemm;
     Gemm32Smem gemm32;
@@ -240,7 +240,7 @@ __device__ void task_potrf(DagSmem &sm, const BatchProblem &pr, int b, int k)
             Ap[(size_t)r * b + 32 + c] = 0.0;
         }
         __syncthreads();
-        for (int m = p + 1; m < nb; ++m) trsm_rows_s<32>(sm.trsm32, Ap, b, A + (size_t)m * 32 * b + p * 32, b, 32);
+        for (int m = p + 1; m < nb; ++m) trsm32_s(sm.trsm32, Ap, b, A + (size_t)m * 32 * b + p * 32, b);
         for (int m = p + 1; m < nb; ++m)
             for (int n = p + 1; n <= m; ++n) {
                 gemm_sub32_s(sm.gemm32, A + (size_t)m * 32 * b + p * 32, b, A + (size_t)n * 32 * b + p * 32, b, 32,

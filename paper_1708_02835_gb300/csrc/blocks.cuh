@@ -25,107 +25,22 @@ __device__ __forceinline__ void tri_decode(int64_t t, int &i, int &j)
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky of an nb x nb block at A (row stride ld) by one CTA of 256 threads,
-// right-looking over 16-column panels: one warp factors the 16 x 16 diagonal
-// block in shared memory, the rows below solve against it, then a rank-16
-// update of the trailing lower triangle.  pan: nb x 17 doubles of shared
-// memory.  A pivot that is not positive records row0 + its row in
-// st->fail_index and returns false.  The strict upper triangle is zeroed.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool potrf_block(double *A, int nb, int ld, int64_t row0, DevStatus *st, double *pan)
-{
-    __shared__ double dblk[kPW][kPW + 1];
-    __shared__ int fail_j;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) fail_j = -1;
-    __syncthreads();
-    for (int p0 = 0; p0 < nb; p0 += kPW) {
-        for (int e = tid; e < kPW * kPW; e += 256) {
-            const int i = e / kPW, j = e % kPW;
-            if (j <= i) dblk[i][j] = A[(size_t)(p0 + i) * ld + p0 + j];
-        }
-        __syncthreads();
-        if (warp == 0) {
-            for (int j = 0; j < kPW; ++j) {
-                if (lane == 0) {
-                    const double d = dblk[j][j];
-                    if (!(d > 0.0)) fail_j = p0 + j;
-                    else dblk[j][j] = sqrt(d);
-                }
-                __syncwarp();
-                if (fail_j >= 0) break;
-                const double ljj = dblk[j][j];
-                if (lane > j && lane < kPW) dblk[lane][j] /= ljj;
-                __syncwarp();
-                if (lane > j && lane < kPW) {
-                    const double lij = dblk[lane][j];
-                    for (int l = j + 1; l <= lane; ++l) dblk[lane][l] -= lij * dblk[l][j];
-                }
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        if (fail_j >= 0) {
-            if (tid == 0) atomicMin(&st->fail_index, (unsigned long long)(row0 + fail_j));
-            return false;
-        }
-        for (int e = tid; e < kPW * kPW; e += 256) {
-            const int i = e / kPW, j = e % kPW;
-            if (j <= i) A[(size_t)(p0 + i) * ld + p0 + j] = dblk[i][j];
-        }
-        for (int i = p0 + kPW + tid; i < nb; i += 256) {
-            double x[kPW];
-            double *row = A + (size_t)i * ld + p0;
-#pragma unroll
-            for (int j = 0; j < kPW; ++j) x[j] = row[j];
-#pragma unroll
-            for (int j = 0; j < kPW; ++j) {
-                double s = x[j];
-#pragma unroll
-                for (int l = 0; l < j; ++l) s -= x[l] * dblk[j][l];
-                x[j] = s / dblk[j][j];
-            }
-#pragma unroll
-            for (int j = 0; j < kPW; ++j) {
-                row[j] = x[j];
-                pan[(size_t)i * (kPW + 1) + j] = x[j];
-            }
-        }
-        __syncthreads();
-        const int q0 = p0 + kPW;
-        for (int i = q0 + warp; i < nb; i += 8) {
-            double li[kPW];
-#pragma unroll
-            for (int l = 0; l < kPW; ++l) li[l] = pan[(size_t)i * (kPW + 1) + l];
-            double *row = A + (size_t)i * ld;
-            for (int j = q0 + lane; j <= i; j += 32) {
-                const double *lj = pan + (size_t)j * (kPW + 1);
-                double acc = 0.0;
-#pragma unroll
-                for (int l = 0; l < kPW; ++l) acc = fma(li[l], lj[l], acc);
-                row[j] -= acc;
-            }
-        }
-        __syncthreads();
-    }
-    for (int i = warp; i < nb; i += 8)
-        for (int j = i + 1 + lane; j < nb; j += 32) A[(size_t)i * ld + j] = 0.0;
-    return true;
-}
-
-// ---------------------------------------------------------------------------
 // Cholesky of a 64 x 64 block at A (row stride ld) held in shared memory for
 // the whole factorisation (one global read and one write of the block): one
 // CTA of 256 threads, right-looking over four 16-column panels -- warp 0
 // factors the 16 x 16 diagonal block with warp synchronisation only, each row
 // below it is solved by one thread, and the trailing lower triangle takes a
 // rank-16 update (one 16-term dot product per entry) -- so the block needs 12
-// CTA barriers, and its FP64 work is mostly independent FMAs.  Same failure
-// reporting as potrf_block; the strict upper triangle is zeroed.
+// CTA barriers, and its FP64 work is mostly independent FMAs.  Pivots are
+// applied through 1 / sqrt(d) (one reciprocal square root per column, then
+// multiplications).  A pivot that is not positive records row0 + its row in
+// st->fail_index and returns false; the strict upper triangle is zeroed.
+// The same routine serves NB = 32.
 // ---------------------------------------------------------------------------
 template <int NB>
 struct PotrfSmem {
     double S[NB][NB + 1];
+    double rd[NB];  // 1 / L_jj
     int fail_j;
 };
 using Potrf64Smem = PotrfSmem<64>;
@@ -147,19 +62,21 @@ __device__ __forceinline__ bool potrf_smem_s(PotrfSmem<NB> &sm, double *A, int l
         // 1. the 16 x 16 diagonal block, column by column, by warp 0 (lane i < 16 owns row p0 + i)
         if (tid < 32) {
             for (int j = 0; j < kPW; ++j) {
-                double d = 0.0;
-                if (lane == j) {
-                    d = S[p0 + j][p0 + j];
-                    if (d > 0.0) S[p0 + j][p0 + j] = sqrt(d);
-                }
-                d = __shfl_sync(0xffffffffu, d, j);
+                // every lane forms 1 / sqrt(d) (a warp-wide FP64 instruction
+                // costs the same for one lane or 32), so the column is scaled
+                // by a multiplication instead of a division
+                const double d = S[p0 + j][p0 + j];
                 if (!(d > 0.0)) {
                     if (lane == 0) fail_j = p0 + j;
                     break;
                 }
+                const double rs = rsqrt(d);
                 __syncwarp();
-                const double ljj = S[p0 + j][p0 + j];
-                if (lane > j && lane < kPW) S[p0 + lane][p0 + j] /= ljj;
+                if (lane == j) {
+                    S[p0 + j][p0 + j] = d * rs;
+                    sm.rd[p0 + j] = rs;
+                }
+                if (lane > j && lane < kPW) S[p0 + lane][p0 + j] *= rs;
                 __syncwarp();
                 if (lane > j && lane < kPW) {
                     const double lij = S[p0 + lane][p0 + j];
@@ -183,7 +100,7 @@ __device__ __forceinline__ bool potrf_smem_s(PotrfSmem<NB> &sm, double *A, int l
                 double v = S[i][p0 + j];
 #pragma unroll
                 for (int l = 0; l < j; ++l) v -= x[l] * S[p0 + j][p0 + l];
-                x[j] = v / S[p0 + j][p0 + j];
+                x[j] = v * sm.rd[p0 + j];
             }
 #pragma unroll
             for (int j = 0; j < kPW; ++j) S[i][p0 + j] = x[j];
@@ -343,6 +260,49 @@ __device__ __forceinline__ void trsm_rows(const double *Lp, int ldl, TX *Xp, int
 {
     __shared__ TrsmSmem<RB, TX> sm;
     trsm_rows_s<RB, TX>(sm, Lp, ldl, Xp, ldx, ncols, cstart);
+}
+
+// ---------------------------------------------------------------------------
+// X L^T = A for one 32 x 32 block (the TRSM tasks of the diagonal-tile task
+// graphs): X and A at Xp (row stride ldx, solved in place), L lower at Lp
+// (row stride ldl).  Four threads per row split each dot product over the
+// solved columns (l = q mod 4) and combine it with two shuffles in a fixed
+// order, so 4 warps (one per SM sub-partition) share the substitution and
+// the row's chain per column is about j / 4 FMAs, two additions and a
+// multiplication by 1 / L_jj.  256 threads (warps 4-7 only stage the block).
+// ---------------------------------------------------------------------------
+struct Trsm32Smem {
+    double X[32][33];
+    double L[32][33];
+    double rd[32];
+};
+
+__device__ __forceinline__ void trsm32_s(Trsm32Smem &sm, const double *Lp, int ldl, double *Xp, int ldx)
+{
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 32 * 32; e += 256) {
+        const int r = e >> 5, c = e & 31;
+        sm.X[r][c] = Xp[(size_t)r * ldx + c];
+        sm.L[r][c] = c <= r ? Lp[(size_t)r * ldl + c] : 0.0;
+    }
+    if (tid < 32) sm.rd[tid] = 1.0 / Lp[(size_t)tid * ldl + tid];
+    __syncthreads();
+    if (tid < 128) {
+        const int r = tid >> 2, q = tid & 3;
+        for (int j = 0; j < 32; ++j) {
+            double part = 0.0;
+            for (int l = q; l < j; l += 4) part = fma(sm.X[r][l], sm.L[j][l], part);
+            part += __shfl_xor_sync(0xffffffffu, part, 1);
+            part += __shfl_xor_sync(0xffffffffu, part, 2);
+            const double x = (sm.X[r][j] - part) * sm.rd[j];
+            __syncwarp();
+            if (q == 0) sm.X[r][j] = x;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < 32 * 32; e += 256) Xp[(size_t)(e >> 5) * ldx + (e & 31)] = sm.X[e >> 5][e & 31];
+    __syncthreads();  // sm is free for the next block
 }
 
 // ---------------------------------------------------------------------------

@@ -96,7 +96,7 @@ __device__ bool diag_wait(const unsigned *c, unsigned target, DevStatus *st)
 
 union DiagSmem {
     PotrfSmem<32> potrf;
-    TrsmSmem<32, double> trsm;
+    Trsm32Smem trsm;
     Gemm32Smem gemm;
 };
 
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256) k_potrf_tile_dag(Tiles tl, int k, unsigne
                 Bmp[(size_t)r * b + 32 + c] = 0.0;
             }
         } else if (type == 1) {
-            trsm_rows_s<32>(sm.trsm, A + (size_t)p * 32 * b + p * 32, b, Bmp, b, 32);
+            trsm32_s(sm.trsm, A + (size_t)p * 32 * b + p * 32, b, Bmp, b);
         } else {
             gemm_sub32_s(sm.gemm, Bmp, b, A + (size_t)n * 32 * b + p * 32, b, 32, A + (size_t)m * 32 * b + n * 32, b);
         }
