@@ -500,14 +500,16 @@ __device__ __forceinline__ void trsv_bwd_tile(const double *__restrict__ L, int 
 __device__ __forceinline__ double col_dot(const double *__restrict__ A, int b, int c, int g, const double *xs,
                                           const float *)
 {
-    // four independent partial sums (rows g + 4 u mod 16) keep four loads in
-    // flight; they are combined in a fixed order
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int r = g; r < b; r += 16) {
+    // eight independent partial sums (rows g + 4 u mod 32) keep eight loads
+    // in flight; they are combined in a fixed order
+    double s[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s[u] = fma(A[(size_t)(r + 4 * u) * b + c], xs[r + 4 * u], s[u]);
+    for (int u = 0; u < 8; ++u) s[u] = 0.0;
+    for (int r = g; r < b; r += 32) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s[u] = fma(A[(size_t)(r + 4 * u) * b + c], xs[r + 4 * u], s[u]);
     }
-    return (s[0] + s[1]) + (s[2] + s[3]);
+    return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
 // Off-band (FP32) tiles: products and the partial sum in FP32 (the tile is
@@ -515,12 +517,14 @@ __device__ __forceinline__ double col_dot(const double *__restrict__ A, int b, i
 __device__ __forceinline__ double col_dot(const float *__restrict__ A, int b, int c, int g, const double *,
                                           const float *xs32)
 {
-    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int r = g; r < b; r += 16) {
+    float s[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s[u] = fmaf(A[(size_t)(r + 4 * u) * b + c], xs32[r + 4 * u], s[u]);
+    for (int u = 0; u < 8; ++u) s[u] = 0.0f;
+    for (int r = g; r < b; r += 32) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s[u] = fmaf(A[(size_t)(r + 4 * u) * b + c], xs32[r + 4 * u], s[u]);
     }
-    return (double)((s[0] + s[1]) + (s[2] + s[3]));
+    return (double)(((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
 }
 
 // vj[c0 .. c0+63] -= (L_kj^T xk)[c0 .. c0+63] for one tile (FP64 or FP32):

@@ -494,31 +494,44 @@ __global__ void __launch_bounds__(256) k_logdet_tiles(Tiles tl, double *__restri
     if (threadIdx.x == 0) partials[k] = tot;
 }
 
-// out_k = V_k^T rhs_k (= L_kk^-1 rhs_k): 16 columns x 16 row groups per CTA
-// (b / 16 CTAs: the product is FP64-bound, so it is spread over many SMs),
-// rows r <= c only (V_k is upper triangular), fixed-order reduction.
+// out_k = V_k^T rhs_k (= L_kk^-1 rhs_k): 8 columns per CTA (b / 8 CTAs).  The
+// CTA stages its column strip of V_k 256 rows at a time in shared memory
+// (rows r <= c only: V_k is upper triangular), every load of a chunk in
+// flight at once, then 32 row groups x 8 columns multiply and reduce in a
+// fixed order.
 __global__ void __launch_bounds__(256) k_fwd_inv(const double *__restrict__ V, int b, int k,
                                                  const double *__restrict__ rhs, double *__restrict__ out,
                                                  const DevStatus *st)
 {
     if (mfailed(st)) return;
-    __shared__ double xs[1024];
-    __shared__ double red[16][17];
+    __shared__ double vs[256][8];
+    __shared__ double red[32][9];
     const double *Vk = V + (size_t)k * b * b;
-    const int c0 = (int)blockIdx.x * 16, tx = threadIdx.x & 15, g = threadIdx.x >> 4;
-    for (int r = threadIdx.x; r < c0 + 16; r += 256) xs[r] = rhs[(size_t)k * b + r];
-    __syncthreads();
-    const int c = c0 + tx;
+    const double *xk = rhs + (size_t)k * b;
+    const int c0 = (int)blockIdx.x * 8, tx = threadIdx.x & 7, g = threadIdx.x >> 3;
+    const int rend = c0 + 8;  // rows beyond the strip's last column are zero
     double sacc = 0.0;
-#pragma unroll 4
-    for (int r = g; r < c0 + 16; r += 16) sacc = fma(Vk[(size_t)r * b + c], xs[r], sacc);
+    for (int r0 = 0; r0 < rend; r0 += 256) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = r0 + g + 32 * i;
+            vs[g + 32 * i][tx] = r < rend ? Vk[(size_t)r * b + c0 + tx] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = r0 + g + 32 * i;
+            if (r < rend) sacc = fma(vs[g + 32 * i][tx], xk[r], sacc);
+        }
+        __syncthreads();
+    }
     red[g][tx] = sacc;
     __syncthreads();
     if (g == 0) {
         double t = red[0][tx];
 #pragma unroll
-        for (int q = 1; q < 16; ++q) t += red[q][tx];
-        out[(size_t)k * b + c] = t;
+        for (int q = 1; q < 32; ++q) t += red[q][tx];
+        out[(size_t)k * b + c0 + tx] = t;
     }
 }
 // out_k = V_k rhs_k (= L_kk^-T rhs_k): one row per warp (b / 8 CTAs), columns
@@ -816,7 +829,7 @@ cudaError_t forward_solve_inv(const Tiles &tl, const double *V, double *rhs, dou
                               cudaStream_t s, KernelTimer *kt)
 {
     for (int k = 0; k < tl.T; ++k) {
-        EGS_LAUNCH(kt, KC_TRSV, s, k_fwd_inv<<<(unsigned)(tl.b / 16), 256, 0, s>>>(V, tl.b, k, rhs, out, st));
+        EGS_LAUNCH(kt, KC_TRSV, s, k_fwd_inv<<<(unsigned)(tl.b / 8), 256, 0, s>>>(V, tl.b, k, rhs, out, st));
         cudaError_t e = launch_gemv_panel(tl, k, out, rhs, st, s, kt);
         if (e != cudaSuccess) return e;
     }
