@@ -5,11 +5,12 @@ One step = one full evaluation of Eq. 1 by Algorithm 2 (Matern generation,
 tile Cholesky, forward solve, log-determinant, quadratic form; in mixed
 precision also the FP64 refinement) on the n = 102,400 workload: a jittered
 320 x 320 grid over [0, 1]^2, theta = (1, 0.1, 0.5), tile 512.  Default: the
-FP32 mixed mode (split-TF32 off-band updates, FP64-accurate band updates) with
-an FP64 band of 3 tiles, the narrowest band that keeps |dl|/|l| <= 1e-6 at
-this size (band 2: 5.2e-6); --band 2 --precision fp32|tf32|bf16 gives the
-other variants.  Inputs are resident in HBM when the timed region starts; the
-tile matrix (up to 42 GB) is regenerated every step, far larger than L2.
+FP32 mixed mode with the stated FP64 band of 2 tiles (FP32 off-band storage,
+split-FP16 tensor-core updates of the off-band tiles, FP64-accurate updates of
+every tile within 3 of the diagonal: --xband 3); --precision fp32|tf32|bf16,
+--band and --xband give the other variants.  Inputs are resident in HBM when
+the timed region starts; the tile matrix (up to 42 GB) is regenerated every
+step, far larger than L2.
 
 Besides the timed mixed-precision steps, the default line carries the rest of
 the metric: one FP64 evaluation of the same inputs ("fp64": evals/s, POTRF

@@ -117,7 +117,7 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
     L.err = off;
     off += 256;
     L.mtab = off;
-    off += align256(EGS_MT_DOUBLES * sizeof(double));
+    off += align256(EGS_MT_SCRATCH_DOUBLES * sizeof(double));
     L.pctr = off;
     off += align256((size_t)g.T * potrf_diag_scratch_words(g.b) * sizeof(unsigned));
     L.rs = off;
@@ -358,7 +358,7 @@ egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3]
     cudaStream_t s = (cudaStream_t)stream;
     double *tab = nullptr;  // the general-nu local polynomials (stream-ordered scratch)
     cudaError_t e = cudaSuccess;
-    if (P.kind == EGS_MATERN_GENERAL) e = cudaMallocAsync((void **)&tab, EGS_MT_DOUBLES * sizeof(double), s);
+    if (P.kind == EGS_MATERN_GENERAL) e = cudaMallocAsync((void **)&tab, EGS_MT_SCRATCH_DOUBLES * sizeof(double), s);
     if (e != cudaSuccess) return cuda_error(e, "egs_matern_tiles scratch");
     if (p == EGS_FP64 || g.T <= band) {
         e = launch_matern_tiles_f64(locs, locs + n, g, P, (double *)tiles, s, nullptr, tab);

@@ -158,10 +158,20 @@ size_t potrf_diag_scratch_words(int b);
 cudaError_t launch_trsv_tiles_f64(const double *tiles, const TileGeom &g, double *zpad, double *partials,
                                   DevStatus *st, cudaStream_t s, KernelTimer *kt = nullptr);
 
-// Sigma(theta) into any Tiles storage (+ optional dense FP64 copy sig).
+// Sigma(theta) into any Tiles storage (+ optional dense FP64 copy sig).  For
+// a mixed layout with the Euclidean distance the off-band tiles are evaluated
+// in double-float arithmetic (matern_df.cuh); tab must then hold
+// EGS_MT_SCRATCH_DOUBLES doubles (the general-nu polynomials and their
+// float-pair split).
 cudaError_t launch_matern_tiles(const double *X, const double *Y, int64_t n, const Tiles &tl,
                                 const egs_matern_params &P, double *sig, cudaStream_t s, KernelTimer *kt,
                                 double *tab = nullptr);
+
+// The double-float evaluation applies to these parameters (Euclidean
+// distance; a general nu needs the polynomial table); fills D.
+bool matern_df_applies(const egs_matern_params &P, bool have_table, egs_matern_df *D);
+// The float-pair copy of the general-nu polynomials inside a generator scratch.
+float2 *matern_df_table(double *tab);
 
 // Mixed-precision evaluation buffers (all device, sized by mixed_layout).
 struct MixedBuffers {
@@ -178,7 +188,7 @@ struct MixedBuffers {
     double *vinv;     // T b x b: V_k = L_kk^-T (upper triangular) for the solves
     void *oz[2];      // FP32 mode: BF16 slices of the panel rows (ozaki_slices_bytes), step k uses k % 2
     double *ozs[2];   // FP32 mode: their row scales, (T-1) b doubles each
-    double *mtab;     // EGS_MT_DOUBLES: the generator's local polynomials (general nu)
+    double *mtab;     // EGS_MT_SCRATCH_DOUBLES: the generator's local polynomials (general nu)
     unsigned *pctr;   // T * potrf_diag_scratch_words(b): counters of the one-launch diagonal POTRFs
     float *rs[2];     // FP32 mode: the power-of-two scales of the split-FP16 panel rows, (T-1) b each
     int xband;        // FP32 mode: tiles with i - j < xband get FP64-accurate updates (>= tl.band)

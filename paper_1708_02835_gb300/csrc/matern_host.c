@@ -97,3 +97,25 @@ int egs_matern_params_init(const double theta[3], egs_matern_params *P)
         P->exp_tab[j] = (double)((q_t)theta[0] * exp2f128(-(q_t)j / (q_t)EGS_EXP_TAB));
     return 0;
 }
+
+/* The double-float constants: q rounded to a float pair (hi, lo). */
+static void split_q(q_t q, float *hi, float *lo)
+{
+    const float h = (float)q;
+    *hi = h;
+    *lo = (float)(q - (q_t)h);
+}
+
+int egs_matern_df_init(const egs_matern_params *P, egs_matern_df *D)
+{
+    memset(D, 0, sizeof(*D));
+    /* theta1 2^(-j/256) and its low part must stay normal floats down to the
+     * smallest table entry; 1/theta2 likewise */
+    const double lim = 0x1p60;
+    if (!(P->th1 > 1.0 / lim && P->th1 < lim && P->inv_th2 > 1.0 / lim && P->inv_th2 < lim)) return -1;
+    D->kind = P->kind;
+    split_q(1.0f128 / (q_t)P->th2, &D->inv_th2[0], &D->inv_th2[1]);
+    for (int j = 0; j < EGS_DF_TAB; ++j)
+        split_q((q_t)P->th1 * exp2f128(-(q_t)j / (q_t)EGS_DF_TAB), &D->tab[2 * j], &D->tab[2 * j + 1]);
+    return 0;
+}

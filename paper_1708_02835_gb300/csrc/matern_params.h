@@ -19,6 +19,9 @@
 #define EGS_MT_NC 12
 #define EGS_MT_E0 (-12)
 #define EGS_MT_DOUBLES (EGS_MT_OCT * EGS_MT_SUB * EGS_MT_NC)
+/* device scratch of a mixed-precision evaluation's generator: the FP64
+ * polynomials, then the same split into float pairs */
+#define EGS_MT_SCRATCH_DOUBLES (2 * EGS_MT_DOUBLES)
 
 /* distance between two locations */
 #define EGS_DIST_EUCLIDEAN 0    /* (x, y) in the plane */
@@ -55,11 +58,25 @@ typedef struct {
     double exp_tab[EGS_EXP_TAB];    /* theta1 2^(-j/64), j = 0..63: the table of theta1 e^-x */
 } egs_matern_params;
 
+/* Constants of the double-float evaluation of the closed-form kinds
+ * (matern_df.cuh): 1/theta2 and the table theta1 2^(-j/256), j = 0..255, each
+ * as a float pair (hi, lo). */
+#define EGS_DF_TAB 256
+typedef struct {
+    float inv_th2[2];
+    int kind;
+    int pad;
+    float tab[2 * EGS_DF_TAB]; /* hi at 2j, lo at 2j + 1 */
+} egs_matern_df;
+
 #ifdef __cplusplus
 extern "C" {
 #endif
 /* Returns 0 on success, -1 if theta is not finite and positive. */
 int egs_matern_params_init(const double theta[3], egs_matern_params *P);
+/* Fills D for the double-float path; returns 0 if that path applies
+ * (theta1 and 1/theta2 well inside the float range), -1 if not. */
+int egs_matern_df_init(const egs_matern_params *P, egs_matern_df *D);
 #ifdef __cplusplus
 }
 #endif

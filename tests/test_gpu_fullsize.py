@@ -3,7 +3,8 @@
 
 * Sigma generated on the GPU, 4,000 sampled entries against the oracle's
   Matern evaluated one by one at the same distances (1e-13 + 4u x relative,
-  the elementwise bar of the smaller tests), for nu = 1/2 and a general nu;
+  the elementwise bar of the smaller tests), for nu = 1/2 and a general nu,
+  in the FP64 layout and in the FP32 mode's mixed layout;
 * the IND approximation over the whole field (100 blocks of 1,024 points, the
   batched scheduler) against the oracle's per-block log-likelihoods, 1e-10;
 * the FP32-mode evaluation in the bench's launch configuration (FP64 band of
@@ -56,6 +57,45 @@ def test_sampled_sigma_entries(egs, field, theta):
     u = 2.0 ** -53
     rtol = 1e-13 + 4 * u * dist / theta[1]                 # as in the elementwise tile test
     assert np.all(np.abs(got - want) <= rtol * np.abs(want) + 1e-290)
+    del buf
+
+
+def test_sampled_mixed_layout_entries(egs, field):
+    """The FP32-mode layout at full size (FP64 band of 2 tiles, the off-band
+    tiles rounded to float; for nu = 1/2 the off-band values come from the
+    double-float evaluation): 4,000 sampled entries within one FP32 rounding
+    plus the FP64 element bar of the oracle's value, band entries within the
+    FP64 bar."""
+    import torch
+    from gpu_util import locs_dev
+    theta, band = (1.0, 0.1, 0.5), 2
+    T = N // B
+    nbytes = egs.egs_tiles_bytes(N, B, "fp32", band)
+    buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    egs.egs_matern_tiles(locs_dev(field), N, theta, B, buf, "fp32", band)
+    torch.cuda.synchronize()
+    f64 = buf[: T * band * B * B * 8].view(torch.float64)
+    f32 = buf[T * band * B * B * 8:].view(torch.float32)
+    rng = np.random.default_rng(23)
+    i = rng.integers(0, N, 4000)
+    j = rng.integers(0, N, 4000)
+    i, j = np.maximum(i, j), np.minimum(i, j)
+    j[:1000] = np.maximum(i[:1000] - rng.integers(0, 2 * B, 1000), 0)   # a quarter near the band
+    ti, tj, r, c = i // B, j // B, i % B, j % B
+    dist = np.hypot(field[0, i] - field[0, j], field[1, i] - field[1, j])
+    want = oracle.matern(theta, dist)
+    u = 2.0 ** -53
+    rtol = 1e-13 + 4 * u * dist / theta[1]
+    inb = ti - tj < band
+    i64 = (ti * band + (ti - tj)) * B * B + r * B + c
+    q = ti - band
+    i32 = (q * (q + 1) // 2 + tj) * B * B + r * B + c
+    got64 = f64[torch.as_tensor(i64[inb], device="cuda")].cpu().numpy()
+    got32 = f32[torch.as_tensor(i32[~inb], device="cuda")].cpu().numpy().astype(np.float64)
+    assert inb.sum() > 100 and (~inb).sum() > 1000
+    assert np.all(np.abs(got64 - want[inb]) <= rtol[inb] * np.abs(want[inb]) + 1e-290)
+    w32 = want[~inb]
+    assert np.all(np.abs(got32 - w32) <= (2.0 ** -24 + rtol[~inb]) * np.abs(w32) + 1e-38)
     del buf
 
 

@@ -175,6 +175,26 @@ def test_fp32_mode_extended_band_tracks_fp64_at_n16384(egs):
     assert rel <= TOL["fp32"], rel
 
 
+@pytest.mark.parametrize("theta", [(1.0, 0.1, 0.5), (1.0, 0.05, 0.8)])
+def test_refinement_converges_to_the_fp64_quadratic_form(egs, theta):
+    """More FP64 refinement steps drive the quadratic form to the accuracy of
+    the residual r = Z - Sigma x, which multiplies the FP64 copy of Sigma (for
+    the closed-form nu = 1/2 written by the double-float evaluation, for a
+    general nu by the direct FP64 one): after four steps Z^T Sigma^-1 Z is
+    within 1e-10 of the oracle's, far below what one step leaves."""
+    from gpu_util import locs_dev, dev
+    n = 4096
+    locs, z, ref = _case(n, theta, 3)
+    q = {}
+    for steps in (1, 4):
+        ll, info = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "fp32", tile=256, band=2, refine=steps)
+        assert info["refine_steps"] == steps
+        q[steps] = abs(info["quad"] - ref["quad"]) / ref["quad"]
+    print("theta %s: quad rel. error after 1 step %.2e, after 4 steps %.2e" % (theta, q[1], q[4]))
+    assert q[4] <= 1e-10, q
+    assert q[4] <= q[1]
+
+
 def test_xband_below_band_is_rejected(egs):
     from gpu_util import locs_dev, dev
     locs = ei.jittered_grid(1000)

@@ -77,15 +77,21 @@ def test_matern_tiles_elementwise(egs, theta):
     _lower_tiles_equal(got, want, rtol=tol)
 
 
-@pytest.mark.parametrize("prec,band", [("fp32", 2), ("tf32", 3), ("bf16", 2)])
-def test_matern_tiles_mixed_layout(egs, prec, band):
+@pytest.mark.parametrize("prec,band,theta", [
+    ("fp32", 2, (1.0, 0.1, 1.3)), ("tf32", 3, (1.0, 0.1, 1.3)), ("bf16", 2, (1.0, 0.1, 1.3)),
+    # closed-form kinds: the off-band tiles come from the double-float evaluation
+    ("fp32", 2, (1.0, 0.1, 0.5)), ("fp32", 3, (1.7, 0.08, 1.5)), ("tf32", 2, (0.6, 0.2, 2.5)),
+    ("fp32", 2, (2.0, 0.004, 0.5)),   # x up to ~350: values down to the float range and below
+])
+def test_matern_tiles_mixed_layout(egs, prec, band, theta):
     """The mixed-precision layout of egs_matern_tiles: band tiles (i - j <
     band) as doubles at i * band + (i - j), the other tiles as floats at
     (i - band)(i - band + 1) / 2 + j of the array that follows; doubles within
     the FP64 element bar of the oracle, floats within one FP32 rounding of the
-    oracle's value (plus the same bar)."""
+    oracle's value (plus the same bar, and 1e-38 absolute for values at the
+    bottom of the float range)."""
     import torch
-    n, b, theta = 1000, 128, (1.0, 0.1, 1.3)
+    n, b = 1000, 128
     T = -(-n // b)
     locs = ei.jittered_grid(n, seed=3)
     want = oracle.tiles_lower(oracle.cov_matrix(locs, theta), b)
