@@ -77,10 +77,12 @@ typedef enum {
 typedef enum {
     EGS_FP64 = 0,     /* everything in double */
     EGS_MIX_FP32 = 1, /* FP64 band; off-band tiles FP32; updates of band tiles
-                         FP64-accurate (DFMA, or exact BF16 slice products on
-                         tcgen05), of off-band tiles on tcgen05 as split TF32
-                         (lo hi' + hi lo' + hi hi', FP32-accurate products);
-                         the off-band TRSM as the split-TF32 product with the
+                         (and of the tiles within egs_opts.xband of the
+                         diagonal) FP64-accurate (DFMA, or exact BF16 slice
+                         products on tcgen05), of the other off-band tiles on
+                         tcgen05 as split FP16 (lo hi' + hi lo' + hi hi' of
+                         row-scaled FP16 halves, FP32-accurate products); the
+                         off-band TRSM as the split-TF32 product with the
                          FP64 inverse of the diagonal tile */
     EGS_MIX_TF32 = 2, /* FP64 band; off-band tiles FP32, updates on tcgen05 TF32 */
     EGS_MIX_BF16 = 3  /* FP64 band; off-band operands BF16, FP32 accumulation */
@@ -180,7 +182,9 @@ size_t egs_loglik_workspace_bytes(int64_t n, int32_t tile, egs_precision p, int3
  * into the lower-tile layout of precision p (egs_tiles_bytes): EGS_FP64 every
  * tile double; the mixed precisions the band tiles (i - j < band, band <= 0
  * meaning 2) as doubles and the other tiles rounded to float in the second
- * array (all double when T <= band).  Every value is computed in FP64.
+ * array (all double when T <= band).  FP64 tiles are computed in FP64; the
+ * float tiles of a mixed layout, under the Euclidean distance, in double-float
+ * arithmetic (float pairs, about 1e-14 relative) and rounded once.
  *   locs   device, 2n doubles (x then y)
  *   tiles  device, egs_tiles_bytes(n, tile, p, band) bytes, written
  * Entries with r = 0 take the limit C(0) = theta1.  Asynchronous on stream.
@@ -259,8 +263,12 @@ egs_status egs_loglik(const double *locs, const double *z, const double theta[3]
                       egs_precision p, double *out_loglik, egs_info *info, void *stream);
 
 /* egs_loglik with options (tile, band, refinement, caller workspace).
- * Mixed precision with refine >= 1 returns EGS_ERR_INACCURATE (out_loglik
- * untouched, info filled) when the refinement step does not contract. */
+ * Mixed precisions: each refinement step forms the FP64 residual
+ * Z - Sigma x with every entry of Sigma(theta) regenerated tile by tile (no
+ * copy of Sigma is stored; Euclidean distance: double-float entries within
+ * about 1e-14 relative, great-circle distance: the FP64 evaluation).  With
+ * refine >= 1 the call returns EGS_ERR_INACCURATE (out_loglik untouched,
+ * info filled) when the first step does not contract. */
 egs_status egs_loglik_ex(const double *locs, const double *z, const double theta[3], int64_t n,
                          egs_precision p, const egs_opts *opts, double *out_loglik, egs_info *info,
                          void *stream);

@@ -90,8 +90,8 @@ static MixedLayout make_mixed_layout(const TileGeom &g, int band, egs_precision 
     off += align256(Tiles::f64_tiles(g.T, band) * bb * sizeof(double));
     L.f32 = off;
     off += align256(Tiles::f32_tiles(g.T, band) * bb * sizeof(float));
-    L.sig = off;
-    off += align256(g.ntiles() * bb * sizeof(double));
+    L.slots = off;
+    off += align256(symv_slots_bytes(g.b, g.T));
     L.panel = off;
     off += 2 * align256(panel_buffer_bytes(g.b, g.T, mix_fmt(p)));
     L.oz = off;
@@ -203,7 +203,7 @@ cudaError_t eval_enqueue(const EvalSetup &es, const double *dlocs, const double 
         MixedBuffers mb;
         const MixedLayout &ML = es.ML;
         mb.tl = Tiles{(double *)(ws + ML.f64), (float *)(ws + ML.f32), g.b, g.T, es.band};
-        mb.sig = (double *)(ws + ML.sig);
+        mb.slots = (double *)(ws + ML.slots);
         mb.panel[0] = ws + ML.panel;
         mb.panel[1] = ws + ML.panel + align256(panel_buffer_bytes(g.b, g.T, mix_fmt(es.p)));
         double *v = (double *)(ws + ML.vec);
@@ -332,10 +332,7 @@ size_t egs_loglik_workspace_bytes(int64_t n, int32_t tile, egs_precision p, int3
     if (n < 1 || !tile_ok(tile)) return 0;
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
     if (p == EGS_FP64 || (mixed_p(p) && g.T <= band)) return make_layout(g).total;
-    if (mixed_p(p) && tile % 256 == 0) {
-        const size_t a = make_mixed_layout(g, band, p).total, b = make_layout(g).total;
-        return a > b ? a : b;
-    }
+    if (mixed_p(p) && tile % 256 == 0) return make_mixed_layout(g, band, p).total;
     return 0;
 }
 

@@ -176,7 +176,7 @@ float2 *matern_df_table(double *tab);
 // Mixed-precision evaluation buffers (all device, sized by mixed_layout).
 struct MixedBuffers {
     Tiles tl;
-    double *sig;      // dense FP64 lower tiles of Sigma (for the refinement residual)
+    double *slots;    // 2 T * T b doubles: per-tile row and column sums of the refinement residual
     void *panel[2];   // two operand buffers of panel_buffer_bytes each, step k uses k % 2
     double *zp, *y, *x, *d, *res, *rows, *cols;  // T*b vectors
     double *partials; // 2T
@@ -194,6 +194,15 @@ struct MixedBuffers {
     int xband;        // FP32 mode: tiles with i - j < xband get FP64-accurate updates (>= tl.band)
 };
 
+// The refinement residual d = zp - Sigma x (T b padded vectors) with Sigma(theta)
+// regenerated tile by tile (symv_regen.cu): no stored copy of Sigma.  slots:
+// symv_slots_bytes(b, T) of device scratch; tab: the generator's scratch of
+// this evaluation (general nu: its polynomials, built by the generation).
+size_t symv_slots_bytes(int b, int T);
+cudaError_t launch_residual_regen(const double *X, const double *Y, int64_t n, int b, int T,
+                                  const egs_matern_params &P, double *tab, const double *x, const double *zp,
+                                  double *slots, double *d, const DevStatus *st, cudaStream_t s, KernelTimer *kt);
+
 // One mixed-precision evaluation (fmt 3 = split TF32, 2 = TF32, 1 = BF16); the
 // result lands in st->result (loglik, logdet, quad refined, quad unrefined).
 cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, int64_t n, const egs_matern_params &P,
@@ -205,7 +214,7 @@ struct Layout {
     size_t tiles, locs, z, zpad, partials, status, mtab, pctr, total;
 };
 struct MixedLayout {
-    size_t f64, f32, sig, panel, oz, l32, wsp, vinv, locs, z, vec, partials, status, err, mtab, pctr, rs, total;
+    size_t f64, f32, slots, panel, oz, l32, wsp, vinv, locs, z, vec, partials, status, err, mtab, pctr, rs, total;
 };
 struct EvalSetup {
     TileGeom g;

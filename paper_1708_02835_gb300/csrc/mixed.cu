@@ -21,8 +21,8 @@
 //          on tcgen05 as lo hi^T + hi lo^T + hi hi^T (FP32-accurate products).
 // The log-determinant 2 sum log L_ii is reduced in FP64 from the FP64
 // diagonal tiles.  The quadratic form Z^T Sigma^-1 Z is won back in FP64 by
-// iterative refinement: x0 = L^-T L^-1 Z, r = Z - Sigma x0 with Sigma the FP64
-// copy written by the generator, x1 = x0 + L^-T L^-1 r, quad = Z^T x1.
+// iterative refinement: x0 = L^-T L^-1 Z, r = Z - Sigma x0 with Sigma
+// regenerated tile by tile (symv_regen.cu), x1 = x0 + L^-T L^-1 r, quad = Z^T x1.
 #include "blocks.cuh"
 #include "slices.cuh"
 
@@ -555,58 +555,6 @@ __global__ void __launch_bounds__(256) k_bwd_inv(const double *__restrict__ V, i
     if (lane == 0) out[(size_t)k * b + r] = sacc;
 }
 
-// Sigma x, row part: rows[i*b + r] = sum_{j <= i} Sigma_ij[r][:] . x_j over the
-// dense FP64 copy (diagonal tiles are stored whole).  grid = (T, b/8), warp per row.
-__global__ void __launch_bounds__(256) k_symv_rows(const double *__restrict__ sig, int b, int T,
-                                                   const double *__restrict__ x, double *__restrict__ out,
-                                                   const DevStatus *st)
-{
-    if (mfailed(st)) return;
-    const int i = (int)blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r = (int)blockIdx.y * 8 + warp;
-    const size_t bb = (size_t)b * b;
-    double s = 0.0;
-    for (int j = 0; j <= i; ++j) {
-        const double *row = sig + (size_t)tile_linear(i, j) * bb + (size_t)r * b;
-        const double *xj = x + (size_t)j * b;
-        for (int c = lane; c < b; c += 32) s = fma(row[c], xj[c], s);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) out[(size_t)i * b + r] = s;
-}
-
-// Sigma x, column part: cols[i*b + c] = sum_{m > i} Sigma_mi[:, c] . x_m.
-// grid = (T, b/64); 64 columns x 4 row groups, fixed-order reduction.
-__global__ void __launch_bounds__(256) k_symv_cols(const double *__restrict__ sig, int b, int T,
-                                                   const double *__restrict__ x, double *__restrict__ out,
-                                                   const DevStatus *st)
-{
-    if (mfailed(st)) return;
-    __shared__ double red[4][64];
-    const int i = (int)blockIdx.x, c0 = (int)blockIdx.y * 64;
-    const int tx = threadIdx.x & 63, g = threadIdx.x >> 6;
-    const size_t bb = (size_t)b * b;
-    double s = 0.0;
-    for (int m = i + 1; m < T; ++m) {
-        const double *A = sig + (size_t)tile_linear(m, i) * bb + c0 + tx;
-        const double *xm = x + (size_t)m * b;
-        for (int r = g; r < b; r += 4) s = fma(A[(size_t)r * b], xm[r], s);
-    }
-    red[g][tx] = s;
-    __syncthreads();
-    if (g == 0) out[(size_t)i * b + c0 + tx] = ((red[0][tx] + red[1][tx]) + red[2][tx]) + red[3][tx];
-}
-
-// res = z - (rows + cols); d = res (the right-hand side of the correction solve)
-__global__ void k_residual(const double *__restrict__ zp, const double *__restrict__ rows,
-                           const double *__restrict__ cols, double *__restrict__ d, int64_t npad, const DevStatus *st)
-{
-    if (mfailed(st)) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < npad) d[i] = zp[i] - (rows[i] + cols[i]);
-}
-
 __global__ void k_axpy(double *__restrict__ x, const double *__restrict__ d, int64_t npad, const DevStatus *st)
 {
     if (mfailed(st)) return;
@@ -860,7 +808,7 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     const int64_t npad = (int64_t)T * b;
     const unsigned vb = (unsigned)((npad + 255) / 256);
     if (ev) cudaEventRecord(ev[0], s);
-    cudaError_t e = launch_matern_tiles(X, Y, n, tl, P, mb.sig, s, kt, mb.mtab);
+    cudaError_t e = launch_matern_tiles(X, Y, n, tl, P, nullptr, s, kt, mb.mtab);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
     // update maps (FP32 mode: split FP16 over the panel buffers) and, in the
@@ -897,11 +845,9 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     e = backward_solve_inv(tl, mb.vinv, mb.d, mb.x, st, s, kt);
     if (e != cudaSuccess) return e;
     for (int it = 0; it < refine; ++it) {
-        EGS_LAUNCH(kt, KC_OTHER, s,
-                   k_symv_rows<<<dim3((unsigned)T, (unsigned)(b / 8)), 256, 0, s>>>(mb.sig, b, T, mb.x, mb.rows, st));
-        EGS_LAUNCH(kt, KC_OTHER, s,
-                   k_symv_cols<<<dim3((unsigned)T, (unsigned)(b / 64)), 256, 0, s>>>(mb.sig, b, T, mb.x, mb.cols, st));
-        EGS_LAUNCH(kt, KC_OTHER, s, k_residual<<<vb, 256, 0, s>>>(mb.zp, mb.rows, mb.cols, mb.d, npad, st));
+        // d = z - Sigma x with Sigma regenerated tile by tile (no stored copy)
+        e = launch_residual_regen(X, Y, n, b, T, P, mb.mtab, mb.x, mb.zp, mb.slots, mb.d, st, s, kt);
+        if (e != cudaSuccess) return e;
         // correction: y = L^-1 d, rows = L^-T y (rows is free once d is formed)
         e = forward_solve_inv(tl, mb.vinv, mb.d, mb.y, st, s, kt);
         if (e != cudaSuccess) return e;

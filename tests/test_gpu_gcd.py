@@ -36,3 +36,26 @@ def test_gcd_loglik_matches_oracle(egs, n, theta, tile):
     except egs.NotPositiveDefinite:
         return
     assert abs(le - ll) > 1e-3 * abs(ll)
+
+
+def test_gcd_fp32_mode_matches_oracle(egs):
+    """The FP32 mixed mode under the great-circle distance: the generator and
+    the refinement residual take the direct FP64 evaluation (the double-float
+    path covers the Euclidean distance only); l within the FP32-mode bar of
+    the oracle, and several refinement steps bring the quadratic form to the
+    FP64 bar."""
+    from gpu_util import locs_dev, dev
+    n, theta = 3000, (1.0, 80.0, 0.5)
+    locs = ei.jittered_grid(n, seed=22, origin=(-95.0, 30.0), side=10.0)
+    S = oracle.cov_matrix_gcd(locs, theta)
+    z = np.linalg.cholesky(S) @ ei.normal(22, n)
+    ref = oracle.loglik_gcd(locs, z, theta)
+    ll, info = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "fp32", tile=256, band=2,
+                                 distance="great_circle")
+    rel = abs(ll - ref["loglik"]) / abs(ref["loglik"])
+    _, i4 = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "fp32", tile=256, band=2, refine=4,
+                              distance="great_circle")
+    q4 = abs(i4["quad"] - ref["quad"]) / ref["quad"]
+    print("gcd fp32 n=%d rel l %.2e, quad after 4 refinement steps %.2e" % (n, rel, q4))
+    assert rel <= 1e-6
+    assert q4 <= 1e-10

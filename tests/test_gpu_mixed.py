@@ -178,10 +178,10 @@ def test_fp32_mode_extended_band_tracks_fp64_at_n16384(egs):
 @pytest.mark.parametrize("theta", [(1.0, 0.1, 0.5), (1.0, 0.05, 0.8)])
 def test_refinement_converges_to_the_fp64_quadratic_form(egs, theta):
     """More FP64 refinement steps drive the quadratic form to the accuracy of
-    the residual r = Z - Sigma x, which multiplies the FP64 copy of Sigma (for
-    the closed-form nu = 1/2 written by the double-float evaluation, for a
-    general nu by the direct FP64 one): after four steps Z^T Sigma^-1 Z is
-    within 1e-10 of the oracle's, far below what one step leaves."""
+    the residual r = Z - Sigma x, whose entries are regenerated tile by tile in
+    double-float arithmetic (the closed form at nu = 1/2, the local
+    polynomials at nu = 0.8): after four steps Z^T Sigma^-1 Z is within 1e-10
+    of the oracle's, and not worse than after one."""
     from gpu_util import locs_dev, dev
     n = 4096
     locs, z, ref = _case(n, theta, 3)
@@ -193,6 +193,23 @@ def test_refinement_converges_to_the_fp64_quadratic_form(egs, theta):
     print("theta %s: quad rel. error after 1 step %.2e, after 4 steps %.2e" % (theta, q[1], q[4]))
     assert q[4] <= 1e-10, q
     assert q[4] <= q[1]
+
+
+def test_fp32_mode_with_theta1_outside_the_float_pair_range(egs):
+    """theta1 = 1e-20 (below the 2^-60 the double-float generator accepts):
+    the FP32 tiles and the refinement residual come from the direct FP64
+    evaluation, and l, which the scale changes only by known terms, stays
+    within the FP32-mode bar of the oracle."""
+    from gpu_util import locs_dev, dev
+    n, theta = 3000, (1e-20, 0.05, 0.5)
+    p = ei.Problem(n=n, theta=theta, seed=9)
+    locs = p.locations()
+    z = oracle.simulate_z(locs, theta, p.e())
+    ref = oracle.loglik_lapack(locs, z, theta)
+    ll, info = egs.egs_loglik_ex(locs_dev(locs), dev(z), theta, n, "fp32", tile=256, band=2)
+    rel = abs(ll - ref["loglik"]) / abs(ref["loglik"])
+    print("theta1 1e-20 fp32: rel l %.2e" % rel)
+    assert rel <= TOL["fp32"], rel
 
 
 def test_xband_below_band_is_rejected(egs):
