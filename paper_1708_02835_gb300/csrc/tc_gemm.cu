@@ -330,19 +330,27 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             tc::prefetch_tmap(&mapA);
             tc::prefetch_tmap(&mapB);
             int g = 0, r = 0;
+            // dynamic schedule: the next unclaimed item (CTAs that start late,
+            // behind kernels of the other stream, simply take fewer).  The
+            // claim of item t + 1 is issued before item t's operand loads, so
+            // the atomic's round trip overlaps them instead of opening a gap
+            // in the ring at every item boundary.
+            int64_t claimed = (int64_t)atomicAdd(next, 1ull);
             while (!abort_flag) {
-                // dynamic schedule: the next unclaimed item (CTAs that start
-                // late, behind kernels of the other stream, simply take fewer)
-                const int64_t item = (int64_t)atomicAdd(next, 1ull);
+                const int64_t item = claimed;
                 WorkItem wi;
                 const bool valid = item < nitems && work.decode(item, wi);
-                if (item < nitems && !valid) continue;
+                if (item < nitems && !valid) {
+                    claimed = (int64_t)atomicAdd(next, 1ull);
+                    continue;
+                }
                 const int slot = r % RING;
                 if (!tc::mbar_wait(&rempty[slot], ((uint32_t)(r / RING) & 1u) ^ 1u, &abort_flag)) break;
                 ring[slot] = valid ? item : -1;
                 tc::mbar_arrive(&rfull[slot]);
                 ++r;
                 if (!valid) break;
+                claimed = (int64_t)atomicAdd(next, 1ull);
                 for (int c = 0; c < kchunks; ++c, ++g) {
                     const int s = g % STAGES;
                     const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
@@ -677,7 +685,8 @@ extern "C" egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, 
     if (e == cudaSuccess) e = make_map(&mb, B, fmt, (uint64_t)K, (uint64_t)N, BN);
     if (e != cudaSuccess) return set_error(EGS_ERR_CUDA, "egs_tc_gemm_test: tensor map encoding failed");
     int *err = nullptr;
-    e = cudaMallocAsync((void **)&err, 16, s);  // error flag + work counter
+    const Allocator Al = current_allocator();
+    e = dev_alloc(Al, (void **)&err, 256, s);  // error flag + work counter
     if (e != cudaSuccess) return set_error(EGS_ERR_OOM, "egs_tc_gemm_test: workspace");
     cudaMemsetAsync(err, 0, 16, s);
     DenseWork w{C, N, M / BM, N / BN};
@@ -686,7 +695,7 @@ extern "C" egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, 
     else e = launch_gemm<1>(ma, mb, ma, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(err, s);
+    dev_free(Al, err, 256, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_error(EGS_ERR_CUDA, "egs_tc_gemm_test: %s", cudaGetErrorString(e));
     if (herr) return set_error(EGS_ERR_TIMEOUT, "egs_tc_gemm_test: a pipeline wait timed out");
