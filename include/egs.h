@@ -156,6 +156,32 @@ typedef struct {
  * cap > 0.  Host-only; no GPU work. */
 egs_status egs_trace_last(egs_trace_rec *out, int64_t cap, int64_t *count);
 
+/*
+ * egs_set_allocator - the device memory of the library's calls (per-call
+ * workspaces, serving slots and fields, batch plans) from the caller's
+ * allocator, for example a framework's caching allocator, instead of
+ * cudaMallocAsync / cudaFreeAsync on the call's stream.
+ *   alloc(bytes, stream, ctx)   returns device memory of at least bytes
+ *                               bytes, usable in stream order on stream
+ *                               (a cudaStream_t), aligned to 256 bytes; NULL
+ *                               when it cannot (the call then fails with
+ *                               EGS_ERR_OOM)
+ *   free(ptr, bytes, stream, ctx)  returns it; work already enqueued on
+ *                               stream may still use ptr, so the allocator
+ *                               must not hand it out to another stream
+ *                               before that work has finished
+ * Both NULL restores cudaMallocAsync / cudaFreeAsync; one NULL is
+ * EGS_ERR_ARG.  Memory is always returned to the allocator that provided it,
+ * also when the allocator is replaced in the meantime.  The library may call
+ * the hooks from its serving thread, with its internal locks held: a hook
+ * must not call back into the library.  A server or batch keeps the
+ * allocator that was set when it was created.  Process-wide; host-only, no
+ * GPU work.
+ */
+typedef void *(*egs_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*egs_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+egs_status egs_set_allocator(egs_alloc_fn alloc, egs_free_fn free_fn, void *ctx);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char *egs_last_error(void);
 

@@ -16,4 +16,5 @@ from .binding import (  # noqa: F401
     egs_last_error, egs_version, egs_default_tile, egs_tiles_bytes, egs_loglik_workspace_bytes,
     egs_matern_tiles, egs_potrf_tiles, egs_trsv_tiles, egs_loglik, egs_loglik_ex, egs_loglik_ind, egs_predict, egs_tc_gemm_test, egs_ozaki_gemm_test,
     egs_batch, egs_batch_autotune, egs_batch_tuned_tile, egs_loglik_batched, egs_server, egs_trsv_tiles_noalloc, egs_simulate, egs_trace_last, TRACE_CLASSES,
+    egs_set_allocator, use_torch_allocator,
 )

@@ -80,6 +80,15 @@ class egs_serve_stats(ctypes.Structure):
 
 _lib = None
 
+# egs_set_allocator's hook types: alloc(bytes, stream, ctx) -> device pointer,
+# free(ptr, bytes, stream, ctx)
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+# Every pair of ctypes callbacks ever installed stays alive for the life of
+# the process: a server or batch keeps calling the hooks it was created with
+# after the allocator has been replaced.
+_hooks_alive = []
+
 
 def library_path() -> str:
     return _build.LIB
@@ -136,6 +145,7 @@ def load_library(build_if_missing: bool = True):
         "egs_serve_wait": (c.c_int, [vp, i64, i32, pd, c.POINTER(egs_info)]),
         "egs_serve_stats": (c.c_int, [vp, c.POINTER(egs_serve_stats)]),
         "egs_serve_destroy": (c.c_int, [vp]),
+        "egs_set_allocator": (c.c_int, [_ALLOC_FN, _FREE_FN, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -190,6 +200,49 @@ def _prec(p) -> int:
 
 def egs_last_error() -> str:
     return load_library().egs_last_error().decode()
+
+
+def egs_set_allocator(alloc=None, free=None):
+    """Route the library's device allocations through the caller's functions:
+    alloc(nbytes, stream) returns a device pointer (an int; 0 when it cannot),
+    usable in stream order on stream (a cudaStream_t as an int, 0 = legacy);
+    free(ptr, nbytes, stream) returns it.  Both None restores the library's
+    own cudaMallocAsync.  The library may call them from its serving thread,
+    and servers and batches keep the hooks they were created with (the
+    callbacks are therefore never released)."""
+    lib = load_library()
+    if alloc is None and free is None:
+        _check(lib.egs_set_allocator(_ALLOC_FN(), _FREE_FN(), None))
+        return
+    if alloc is None or free is None:
+        _check(lib.egs_set_allocator(_ALLOC_FN(lambda n, st, c: None) if alloc else _ALLOC_FN(),
+                                     _FREE_FN(lambda p, n, st, c: None) if free else _FREE_FN(), None))
+        return
+
+    def a(nbytes, stream, ctx):
+        return alloc(int(nbytes), int(stream or 0)) or None
+
+    def f(ptr, nbytes, stream, ctx):
+        free(int(ptr), int(nbytes), int(stream or 0))
+
+    hooks = (_ALLOC_FN(a), _FREE_FN(f))
+    _hooks_alive.append(hooks)
+    _check(lib.egs_set_allocator(hooks[0], hooks[1], None))
+
+
+def use_torch_allocator():
+    """egs_set_allocator with PyTorch's caching allocator on the current device."""
+    import torch
+
+    dev = torch.cuda.current_device()
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, dev, stream)
+
+    def free(ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    egs_set_allocator(alloc, free)
 
 
 def egs_trace_last() -> list:

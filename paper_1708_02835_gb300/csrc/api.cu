@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "egs_internal.cuh"
 
@@ -30,6 +31,35 @@ egs_status cuda_error(cudaError_t e, const char *what)
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static std::mutex g_alloc_mu;
+static Allocator g_alloc{nullptr, nullptr, nullptr};
+
+Allocator current_allocator()
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    return g_alloc;
+}
+
+cudaError_t dev_alloc(const Allocator &A, void **p, size_t bytes, cudaStream_t s)
+{
+    if (!A.alloc) return cudaMallocAsync(p, bytes, s);
+    *p = A.alloc(bytes, (void *)s, A.ctx);
+    if (!*p) return cudaErrorMemoryAllocation;
+    if (((uintptr_t)*p & 255) != 0) {  // the layouts need 256-byte alignment
+        A.free(*p, bytes, (void *)s, A.ctx);
+        *p = nullptr;
+        return cudaErrorMisalignedAddress;
+    }
+    return cudaSuccess;
+}
+
+void dev_free(const Allocator &A, void *p, size_t bytes, cudaStream_t s)
+{
+    if (!p) return;
+    if (!A.alloc) cudaFreeAsync(p, s);
+    else A.free(p, bytes, (void *)s, A.ctx);
+}
 
 static bool tile_ok(int32_t b) { return b >= 64 && b <= 1024 && (b % 64) == 0; }
 
@@ -301,6 +331,16 @@ extern "C" {
 
 const char *egs_last_error(void) { return g_err; }
 
+egs_status egs_set_allocator(egs_alloc_fn alloc, egs_free_fn free_fn, void *ctx)
+{
+    g_err[0] = 0;
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return set_error(EGS_ERR_ARG, "egs_set_allocator: give both hooks, or neither to restore cudaMallocAsync");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = Allocator{alloc, free_fn, alloc ? ctx : nullptr};
+    return EGS_OK;
+}
+
 egs_status egs_trace_last(egs_trace_rec *out, int64_t cap, int64_t *count)
 {
     if (!count) return set_error(EGS_ERR_ARG, "egs_trace_last: count is NULL");
@@ -355,7 +395,9 @@ egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3]
     cudaStream_t s = (cudaStream_t)stream;
     double *tab = nullptr;  // the general-nu local polynomials (stream-ordered scratch)
     cudaError_t e = cudaSuccess;
-    if (P.kind == EGS_MATERN_GENERAL) e = cudaMallocAsync((void **)&tab, EGS_MT_SCRATCH_DOUBLES * sizeof(double), s);
+    const Allocator A = current_allocator();
+    const size_t tab_bytes = EGS_MT_SCRATCH_DOUBLES * sizeof(double);
+    if (P.kind == EGS_MATERN_GENERAL) e = dev_alloc(A, (void **)&tab, tab_bytes, s);
     if (e != cudaSuccess) return cuda_error(e, "egs_matern_tiles scratch");
     if (p == EGS_FP64 || g.T <= band) {
         e = launch_matern_tiles_f64(locs, locs + n, g, P, (double *)tiles, s, nullptr, tab);
@@ -366,7 +408,7 @@ egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3]
         const Tiles tl{f64, f32, g.b, g.T, band};
         e = launch_matern_tiles(locs, locs + n, n, tl, P, nullptr, s, nullptr, tab);
     }
-    if (tab) cudaFreeAsync(tab, s);
+    dev_free(A, tab, tab_bytes, s);
     if (e != cudaSuccess) return cuda_error(e, "egs_matern_tiles launch");
     return EGS_OK;
 }
@@ -382,13 +424,15 @@ egs_status egs_potrf_tiles(void *tiles, int64_t n, int32_t tile, int64_t *fail_i
     TileGeom g{n, tile, (int)((n + tile - 1) / tile)};
     DevStatus *st = nullptr;
     const size_t sbytes = align256(sizeof(DevStatus));
-    cudaError_t e = cudaMallocAsync((void **)&st, sbytes + (size_t)g.T * potrf_diag_scratch_words(g.b) * sizeof(unsigned), s);
+    const Allocator A = current_allocator();
+    const size_t wbytes = sbytes + (size_t)g.T * potrf_diag_scratch_words(g.b) * sizeof(unsigned);
+    cudaError_t e = dev_alloc(A, (void **)&st, wbytes, s);
     if (e != cudaSuccess) return cuda_error(e, "egs_potrf_tiles workspace");
     status_init(st, s);
     e = launch_potrf_tiles_f64((double *)tiles, g, st, s, nullptr, (unsigned *)((char *)st + sbytes));
     DevStatus h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(st, s);
+    dev_free(A, st, wbytes, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "egs_potrf_tiles");
     if (h.timeout) return set_error(EGS_ERR_TIMEOUT, "egs_potrf_tiles: a dependency wait of the diagonal POTRF timed out");
@@ -412,7 +456,8 @@ egs_status egs_trsv_tiles(const void *tiles, int64_t n, int32_t tile, const doub
     const size_t npad = (size_t)g.T * g.b;
     char *ws = nullptr;
     const size_t bytes = align256(npad * sizeof(double)) + align256(2 * g.T * sizeof(double)) + align256(sizeof(DevStatus));
-    cudaError_t e = cudaMallocAsync((void **)&ws, bytes, s);
+    const Allocator A = current_allocator();
+    cudaError_t e = dev_alloc(A, (void **)&ws, bytes, s);
     if (e != cudaSuccess) return cuda_error(e, "egs_trsv_tiles workspace");
     double *zpad = (double *)ws;
     double *partials = (double *)(ws + align256(npad * sizeof(double)));
@@ -423,7 +468,7 @@ egs_status egs_trsv_tiles(const void *tiles, int64_t n, int32_t tile, const doub
     if (e == cudaSuccess) e = cudaMemcpyAsync(y, zpad, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
     DevStatus h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(ws, s);
+    dev_free(A, ws, bytes, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "egs_trsv_tiles");
     if (logdet) *logdet = h.result[1];
@@ -450,12 +495,13 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
     char *ws = nullptr;
     bool own = false;
     cudaError_t e = cudaSuccess;
+    const Allocator A = current_allocator();
     if (opts && opts->workspace) {
         if (opts->workspace_bytes < es.need)
             return set_error(EGS_ERR_ARG, "workspace of %zu bytes < %zu needed", opts->workspace_bytes, es.need);
         ws = (char *)opts->workspace;
     } else {
-        e = cudaMallocAsync((void **)&ws, es.need, s);
+        e = dev_alloc(A, (void **)&ws, es.need, s);
         if (e != cudaSuccess) return cuda_error(e, "egs_loglik workspace");
         own = true;
     }
@@ -476,7 +522,7 @@ egs_status egs_loglik_ex(const double *locs, const double *z, const double theta
     int herr = 0;
     if (e == cudaSuccess && es.mixed) e = cudaMemcpyAsync(&herr, ws + es.ML.err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, eval_status(es, ws), sizeof(h), cudaMemcpyDeviceToHost, s);
-    if (own) cudaFreeAsync(ws, s);
+    if (own) dev_free(A, ws, es.need, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     float ms[3] = {0, 0, 0};
     if (timing) {
@@ -527,7 +573,8 @@ egs_status egs_simulate(const double *locs, const double *e, const double theta[
     cudaStream_t s = (cudaStream_t)stream;
     const TileGeom &g = es.g;
     char *ws = nullptr;
-    cudaError_t err = cudaMallocAsync((void **)&ws, es.need, s);
+    const Allocator A = current_allocator();
+    cudaError_t err = dev_alloc(A, (void **)&ws, es.need, s);
     if (err != cudaSuccess) return cuda_error(err, "egs_simulate workspace");
     double *tiles = (double *)(ws + es.L.tiles);
     double *epad = (double *)(ws + es.L.zpad);
@@ -542,7 +589,8 @@ egs_status egs_simulate(const double *locs, const double *e, const double theta[
         err = cudaMemcpyAsync((void *)de, e, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s);
     }
     double *zfull = nullptr;
-    if (err == cudaSuccess) err = cudaMallocAsync((void **)&zfull, (size_t)g.T * g.b * sizeof(double), s);
+    const size_t zbytes = (size_t)g.T * g.b * sizeof(double);
+    if (err == cudaSuccess) err = dev_alloc(A, (void **)&zfull, zbytes, s);
     if (err == cudaSuccess) {
         status_init(st, s);
         err = launch_matern_tiles_f64(dlocs, dlocs + n, g, es.P, tiles, s, nullptr, (double *)(ws + es.L.mtab));
@@ -553,8 +601,8 @@ egs_status egs_simulate(const double *locs, const double *e, const double theta[
     if (err == cudaSuccess) err = cudaMemcpyAsync(z, zfull, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
     DevStatus h;
     if (err == cudaSuccess) err = cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s);
-    if (zfull) cudaFreeAsync(zfull, s);
-    cudaFreeAsync(ws, s);
+    dev_free(A, zfull, zbytes, s);
+    dev_free(A, ws, es.need, s);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) return cuda_error(err, "egs_simulate");
     if (h.timeout) return set_error(EGS_ERR_TIMEOUT, "egs_simulate: a bounded device wait timed out");

@@ -432,6 +432,7 @@ struct egs_batch {
     std::vector<int> T;
     char *ws = nullptr;
     size_t ws_bytes = 0;
+    Allocator alloc{};  // the allocator that provided ws
     BatchProblem *d_probs = nullptr;
     egs_matern_params *d_params = nullptr;
     DevStatus *d_status = nullptr;
@@ -691,7 +692,14 @@ egs_status egs_batch_create(int32_t nprob, const int64_t *n, int32_t tile, egs_p
     const size_t ctl_off = off;
     off += a256(sizeof(DagCtl));
     B->ws_bytes = off;
-    cudaError_t e = cudaMalloc((void **)&B->ws, off);
+    B->alloc = current_allocator();
+    cudaError_t e;
+    if (!B->alloc.alloc) {
+        e = cudaMalloc((void **)&B->ws, off);
+    } else {  // the caller's hook, on the legacy stream (the batch outlives any call's stream)
+        e = dev_alloc(B->alloc, (void **)&B->ws, off, nullptr);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    }
     if (e != cudaSuccess) {
         delete B;
         return cuda_error(e, "egs_batch_create workspace");
@@ -919,7 +927,10 @@ egs_status egs_batch_destroy(egs_batch *B)
     if (B->ev_in) cudaEventDestroy(B->ev_in);
     if (B->ev_out) cudaEventDestroy(B->ev_out);
     if (B->cs) cudaStreamDestroy(B->cs);
-    if (B->ws) cudaFree(B->ws);
+    if (B->ws) {
+        if (!B->alloc.alloc) cudaFree(B->ws);
+        else dev_free(B->alloc, B->ws, B->ws_bytes, nullptr);
+    }
     if (B->h_probs) cudaFreeHost(B->h_probs);
     if (B->h_params) cudaFreeHost(B->h_params);
     if (B->h_status) cudaFreeHost(B->h_status);

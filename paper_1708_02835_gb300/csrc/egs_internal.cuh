@@ -126,6 +126,18 @@ void store_trace(const KernelTimer &kt, cudaEvent_t origin);
         if (kt) (kt)->end((cls), (s));   \
     } while (0)
 
+// Device memory of the library's calls: the caller's hooks (egs_set_allocator)
+// or cudaMallocAsync / cudaFreeAsync.  An allocation is freed with the
+// Allocator value that made it.
+struct Allocator {
+    egs_alloc_fn alloc;  // NULL: cudaMallocAsync
+    egs_free_fn free;
+    void *ctx;
+};
+Allocator current_allocator();
+cudaError_t dev_alloc(const Allocator &A, void **p, size_t bytes, cudaStream_t s);
+void dev_free(const Allocator &A, void *p, size_t bytes, cudaStream_t s);
+
 // True for device (or managed) memory; host pointers are staged by the calls.
 bool is_device_ptr(const void *p);
 

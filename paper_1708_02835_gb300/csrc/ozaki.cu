@@ -462,7 +462,8 @@ extern "C" egs_status egs_ozaki_gemm_test(const double *A, const double *B, int3
     const size_t sa = (size_t)OS * M * K * 2, sb = (size_t)OS * N * K * 2;
     char *ws = nullptr;
     const size_t bytes = sa + sb + (size_t)(M + N) * 8 + 256;
-    cudaError_t e = cudaMallocAsync((void **)&ws, bytes, s);
+    const Allocator Al = current_allocator();
+    cudaError_t e = dev_alloc(Al, (void **)&ws, bytes, s);
     if (e != cudaSuccess) return set_error(EGS_ERR_OOM, "egs_ozaki_gemm_test: workspace");
     __nv_bfloat16 *oa = (__nv_bfloat16 *)ws, *ob = (__nv_bfloat16 *)(ws + sa);
     double *sca = (double *)(ws + sa + sb), *scb = sca + M;
@@ -480,7 +481,7 @@ extern "C" egs_status egs_ozaki_gemm_test(const double *A, const double *B, int3
     if (e == cudaSuccess) e = launch_ozaki(ma, mb, w, sca, scb, M, N, (int64_t)(M / OBM) * (N / OBN), K / OKC, err, s);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(ws, s);
+    dev_free(Al, ws, bytes, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_error(EGS_ERR_CUDA, "egs_ozaki_gemm_test: %s", cudaGetErrorString(e));
     if (herr) return set_error(EGS_ERR_TIMEOUT, "egs_ozaki_gemm_test: a pipeline wait timed out");

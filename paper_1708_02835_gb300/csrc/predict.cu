@@ -82,7 +82,9 @@ extern "C" egs_status egs_predict(const double *locs_obs, const double *z_obs, i
     auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t extra_new = a256((size_t)2 * m * sizeof(double)), extra_out = a256((size_t)m * sizeof(double));
     char *ws = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&ws, es.need + extra_new + extra_out, s);
+    const Allocator A = current_allocator();
+    const size_t wbytes = es.need + extra_new + extra_out;
+    cudaError_t e = dev_alloc(A, (void **)&ws, wbytes, s);
     if (e != cudaSuccess) return cuda_error(e, "egs_predict workspace");
     const double *dlocs = locs_obs, *dz = z_obs, *dnew = locs_new;
     double *dout = z_new;
@@ -116,7 +118,7 @@ extern "C" egs_status egs_predict(const double *locs_obs, const double *z_obs, i
     int herr = 0;
     if (e == cudaSuccess && es.mixed) e = cudaMemcpyAsync(&herr, ws + es.ML.err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, eval_status(es, ws), sizeof(h), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(ws, s);
+    dev_free(A, ws, wbytes, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "egs_predict");
     if (herr || h.timeout) return set_error(EGS_ERR_TIMEOUT, "egs_predict: a bounded device wait timed out");

@@ -76,6 +76,7 @@ struct egs_server {
     bool stop = false;
     std::thread worker;
     int device = 0;
+    egs::Allocator alloc{};  // device memory of fields and workspaces (fixed at creation)
     // statistics
     std::vector<double> lat_ms;
     int64_t completed = 0, failed = 0, rejected = 0, fallbacks = 0;
@@ -86,9 +87,26 @@ struct egs_server {
 
 namespace {
 
+// Fields live as long as the server: cudaMalloc, or the caller's hook on the
+// legacy stream.
+cudaError_t field_alloc(const egs::Allocator &A, double **p, size_t bytes)
+{
+    if (!A.alloc) return cudaMalloc((void **)p, bytes);
+    cudaError_t e = egs::dev_alloc(A, (void **)p, bytes, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    return e;
+}
+
+void field_free(const egs::Allocator &A, double *p, size_t bytes)
+{
+    if (!p) return;
+    if (!A.alloc) cudaFree(p);
+    else egs::dev_free(A, p, bytes, nullptr);
+}
+
 void release_slot(egs_server *S, Slot &sl)
 {
-    cudaFreeAsync(sl.ws, sl.stream);
+    egs::dev_free(S->alloc, sl.ws, sl.es.need, sl.stream);
     sl.ws = nullptr;
     S->used -= sl.es.need;
     sl.busy = false;
@@ -180,7 +198,7 @@ bool admit_one(egs_server *S, std::unique_lock<std::mutex> &lk)
     }
     Slot &sl = *free_slot;
     char *ws = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&ws, es.need, sl.stream);
+    cudaError_t e = egs::dev_alloc(S->alloc, (void **)&ws, es.need, sl.stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -254,6 +272,7 @@ egs_status egs_serve_create(const egs_serve_config *cfg, egs_server **out)
         return set_error(EGS_ERR_ARG, "egs_serve_create: max_inflight in [1, 64] and a nonzero budget required");
     egs_server *S = new egs_server;
     S->cfg = *cfg;
+    S->alloc = egs::current_allocator();
     cudaGetDevice(&S->device);
     S->slots.resize(cfg->max_inflight);
     for (auto &sl : S->slots) {
@@ -284,15 +303,15 @@ egs_status egs_serve_add_field(egs_server *S, const double *locs, const double *
         S->used += f.bytes;
         S->used_peak = std::max(S->used_peak, S->used);
     }
-    cudaError_t e = cudaMalloc((void **)&f.locs, (size_t)2 * n * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&f.z, (size_t)n * sizeof(double));
+    cudaError_t e = field_alloc(S->alloc, &f.locs, (size_t)2 * n * sizeof(double));
+    if (e == cudaSuccess) e = field_alloc(S->alloc, &f.z, (size_t)n * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(f.locs, locs, (size_t)2 * n * sizeof(double), cudaMemcpyDefault);
     if (e == cudaSuccess) e = cudaMemcpy(f.z, z, (size_t)n * sizeof(double), cudaMemcpyDefault);
     std::lock_guard<std::mutex> lk(S->mu);
     if (e != cudaSuccess) {
         S->used -= f.bytes;
-        if (f.locs) cudaFree(f.locs);
-        if (f.z) cudaFree(f.z);
+        field_free(S->alloc, f.locs, (size_t)2 * n * sizeof(double));
+        field_free(S->alloc, f.z, (size_t)n * sizeof(double));
         return cuda_error(e, "egs_serve_add_field");
     }
     S->fields.push_back(f);
@@ -387,7 +406,7 @@ egs_status egs_serve_destroy(egs_server *S)
     if (S->worker.joinable()) S->worker.join();
     for (auto &sl : S->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
-        if (sl.ws) cudaFreeAsync(sl.ws, sl.stream);
+        if (sl.ws) egs::dev_free(S->alloc, sl.ws, sl.es.need, sl.stream);
         if (sl.stream) {
             cudaStreamSynchronize(sl.stream);
             cudaStreamDestroy(sl.stream);
@@ -397,8 +416,8 @@ egs_status egs_serve_destroy(egs_server *S)
         if (sl.h_err) cudaFreeHost(sl.h_err);
     }
     for (auto &f : S->fields) {
-        if (f.locs) cudaFree(f.locs);
-        if (f.z) cudaFree(f.z);
+        field_free(S->alloc, f.locs, (size_t)2 * f.n * sizeof(double));
+        field_free(S->alloc, f.z, (size_t)f.n * sizeof(double));
     }
     delete S;
     return EGS_OK;
