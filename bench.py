@@ -310,7 +310,7 @@ def run_mle(a, egs):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = mle.fit(dl, dz, n, prec, start=start, max_evals=a.evals, tile=0 if prec == "fp64" else 512,
-                    band=0 if prec == "fp64" else a.band)
+                    band=0 if prec == "fp64" else a.band, xband=a.xband)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         out[prec] = {"theta_hat": list(r.theta), "loglik": r.loglik, "evals": r.evals, "seconds": dt,
@@ -319,7 +319,7 @@ def run_mle(a, egs):
             "unit": "evals/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "n=%d (160x160 jittered grid), theta=%s, Z by Algorithm 1 on the GPU, "
                                    "bounded Nelder-Mead from %s over [0.01,5]^3" % (n, tuple(theta), start), "n": n,
-                       "band": a.band},
+                       "band": a.band, "xband": a.xband if a.precision == "fp32" else None},
             "runs": out, "theta_true": list(theta)}
     if len(out) > 1:
         f, m = out["fp64"]["theta_hat"], out[a.precision]["theta_hat"]

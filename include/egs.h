@@ -480,6 +480,19 @@ egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, int32_t N, 
                             void *stream);
 
 /*
+ * egs_tc_gemm_test_withhold - failure detection of the tensor-core pipeline:
+ * egs_tc_gemm_test with the TMA loads of one ring stage (withhold_stage >= 0,
+ * counted over the whole launch of one CTA) never issued.  The MMA warp's
+ * wait for that stage runs out after its bound (2 s), the kernel unwinds
+ * (in-flight loads land, TMEM is freed) and the call returns EGS_ERR_TIMEOUT
+ * with the context still usable; C is undefined.  The paper has no
+ * counterpart: this is a test of the bounded waits every tcgen05 kernel of
+ * the library uses.  EGS_ERR_ARG if withhold_stage < 0.
+ */
+egs_status egs_tc_gemm_test_withhold(const void *A, const void *B, int32_t M, int32_t N, int32_t K, egs_precision p,
+                                     float *C, int64_t withhold_stage, void *stream);
+
+/*
  * egs_ozaki_gemm_test - the FP64-accurate product of the EGS_MIX_FP32 band
  * updates on its own: C = A B^T with every row of A and B cut into five exact
  * BF16 slices (row scale a power of two) and the 15 slice products of levels

@@ -14,7 +14,7 @@ from .binding import (  # noqa: F401
     EGS_ERR_UNIMPLEMENTED, EGS_FP64, EGS_MIX_FP32, EGS_MIX_TF32, EGS_MIX_BF16, PRECISIONS,
     EgsError, NotPositiveDefinite, MixedInaccurate, egs_info, egs_opts, load_library, library_path,
     egs_last_error, egs_version, egs_default_tile, egs_tiles_bytes, egs_loglik_workspace_bytes,
-    egs_matern_tiles, egs_potrf_tiles, egs_trsv_tiles, egs_loglik, egs_loglik_ex, egs_loglik_ind, egs_predict, egs_tc_gemm_test, egs_ozaki_gemm_test,
+    egs_matern_tiles, egs_potrf_tiles, egs_trsv_tiles, egs_loglik, egs_loglik_ex, egs_loglik_ind, egs_predict, egs_tc_gemm_test, egs_tc_gemm_test_withhold, egs_ozaki_gemm_test,
     egs_batch, egs_batch_autotune, egs_batch_tuned_tile, egs_loglik_batched, egs_server, egs_trsv_tiles_noalloc, egs_simulate, egs_trace_last, TRACE_CLASSES,
     egs_set_allocator, use_torch_allocator,
 )

@@ -121,6 +121,7 @@ def load_library(build_if_missing: bool = True):
         "egs_loglik": (c.c_int, [vp, vp, pd, i64, c.c_int, pd, c.POINTER(egs_info), vp]),
         "egs_loglik_ex": (c.c_int, [vp, vp, pd, i64, c.c_int, c.POINTER(egs_opts), pd, c.POINTER(egs_info), vp]),
         "egs_tc_gemm_test": (c.c_int, [vp, vp, i32, i32, i32, c.c_int, vp, vp]),
+        "egs_tc_gemm_test_withhold": (c.c_int, [vp, vp, i32, i32, i32, c.c_int, vp, i64, vp]),
         "egs_ozaki_gemm_test": (c.c_int, [vp, vp, i32, i32, i32, vp, vp]),
         "egs_batch_create": (c.c_int, [i32, c.POINTER(i64), i32, c.c_int, c.POINTER(vp)]),
         "egs_batch_run": (c.c_int, [vp, c.POINTER(vp), c.POINTER(vp), pd, pd, c.POINTER(c.c_int), vp]),
@@ -345,6 +346,15 @@ def egs_tc_gemm_test(A, B, C, precision="tf32", stream=None):
     M, K = A.shape
     N = B.shape[0]
     _check(load_library().egs_tc_gemm_test(_ptr(A), _ptr(B), M, N, K, _prec(precision), _ptr(C), _stream(stream)))
+
+
+def egs_tc_gemm_test_withhold(A, B, C, precision="tf32", withhold_stage=0, stream=None):
+    """egs_tc_gemm_test with one ring stage's loads never issued: raises
+    EgsError(EGS_ERR_TIMEOUT) once the bounded wait for it runs out."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(load_library().egs_tc_gemm_test_withhold(_ptr(A), _ptr(B), M, N, K, _prec(precision), _ptr(C),
+                                                    int(withhold_stage), _stream(stream)))
 
 
 def egs_ozaki_gemm_test(A, B, C, stream=None):

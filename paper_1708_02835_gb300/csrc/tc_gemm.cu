@@ -285,7 +285,8 @@ constexpr uint32_t TMEM_COLS2 = 2 * TMEM_COLS;
 template <int FMT, class Work>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-          const __grid_constant__ CUtensorMap mapC, Work work, int64_t nitems, int kchunks, int *err)
+          const __grid_constant__ CUtensorMap mapC, Work work, int64_t nitems, int kchunks, int *err,
+          int64_t withhold)
 {
     constexpr int STAGES = Cfg<FMT>::STAGES_;
     constexpr int STAGE_BYTES = Cfg<FMT>::STAGE_BYTES;
@@ -354,6 +355,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 for (int c = 0; c < kchunks; ++c, ++g) {
                     const int s = g % STAGES;
                     const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+                    // test hook: the stage `withhold` is never loaded, so the
+                    // MMA warp's bounded wait for it runs out and the kernel
+                    // unwinds (-1 in every real launch)
+                    if (g == withhold) continue;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1u, &abort_flag)) break;
                     tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                     uint8_t *st = smem + s * STAGE_BYTES;
@@ -564,7 +569,7 @@ int num_sms()
 // factorisation's critical chain runs beside the update).
 template <int FMT, class Work>
 cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const CUtensorMap &mc, const Work &w,
-                        int64_t items, int kchunks, int *err, cudaStream_t s, int reserve = 0)
+                        int64_t items, int kchunks, int *err, cudaStream_t s, int reserve = 0, int64_t withhold = -1)
 {
     constexpr int SMEM_BYTES = Cfg<FMT>::SMEM_BYTES;
     cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<FMT, Work>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -574,7 +579,8 @@ cudaError_t launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const CUte
     // err[0] is the error flag; the 8 bytes at err + 2 hold the work counter
     e = cudaMemsetAsync(err + 2, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    k_tc_gemm<FMT, Work><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, mc, w, items, kchunks, err);
+    k_tc_gemm<FMT, Work><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(ma, mb, mc, w, items, kchunks, err,
+                                                                         withhold);
     return cudaGetLastError();
 }
 
@@ -671,8 +677,8 @@ cudaError_t launch_update_tc(const CUtensorMap &mapA, const CUtensorMap &mapB, c
 
 using namespace egs;
 
-extern "C" egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, int32_t N, int32_t K, egs_precision p,
-                                       float *C, void *stream)
+static egs_status tc_gemm_test(const void *A, const void *B, int32_t M, int32_t N, int32_t K, egs_precision p,
+                               float *C, int64_t withhold, void *stream)
 {
     if (M <= 0 || N <= 0 || K <= 0 || M % BM || N % BN || K % 64)
         return set_error(EGS_ERR_ARG, "egs_tc_gemm_test: M %% 128, N %% 256, K %% 64 must be 0");
@@ -691,8 +697,8 @@ extern "C" egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, 
     cudaMemsetAsync(err, 0, 16, s);
     DenseWork w{C, N, M / BM, N / BN};
     const int kchunks = K / (fmt == 2 ? 32 : 64);
-    if (fmt == 2) e = launch_gemm<2>(ma, mb, ma, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s);
-    else e = launch_gemm<1>(ma, mb, ma, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s);
+    if (fmt == 2) e = launch_gemm<2>(ma, mb, ma, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s, 0, withhold);
+    else e = launch_gemm<1>(ma, mb, ma, w, (int64_t)(M / BM) * (N / BN), kchunks, err, s, 0, withhold);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     dev_free(Al, err, 256, s);
@@ -700,4 +706,19 @@ extern "C" egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, 
     if (e != cudaSuccess) return set_error(EGS_ERR_CUDA, "egs_tc_gemm_test: %s", cudaGetErrorString(e));
     if (herr) return set_error(EGS_ERR_TIMEOUT, "egs_tc_gemm_test: a pipeline wait timed out");
     return EGS_OK;
+}
+
+extern "C" egs_status egs_tc_gemm_test(const void *A, const void *B, int32_t M, int32_t N, int32_t K, egs_precision p,
+                                       float *C, void *stream)
+{
+    clear_error();
+    return tc_gemm_test(A, B, M, N, K, p, C, -1, stream);
+}
+
+extern "C" egs_status egs_tc_gemm_test_withhold(const void *A, const void *B, int32_t M, int32_t N, int32_t K,
+                                                egs_precision p, float *C, int64_t withhold_stage, void *stream)
+{
+    clear_error();
+    if (withhold_stage < 0) return set_error(EGS_ERR_ARG, "egs_tc_gemm_test_withhold: withhold_stage must be >= 0");
+    return tc_gemm_test(A, B, M, N, K, p, C, withhold_stage, stream);
 }

@@ -129,7 +129,7 @@ def nelder_mead_bounded(f, x0, lower, upper, max_evals=50, step=0.5, trace_path=
 
 def fit(locs, z, n: int, precision="fp64", start=(0.5, 0.05, 0.5), lower=(0.01, 0.01, 0.01),
         upper=(5.0, 5.0, 5.0), max_evals: int = 50, tile: int = 0, band: int = 0, trace_path=None,
-        stream=None, fallback_fp64: bool = True) -> FitResult:
+        stream=None, fallback_fp64: bool = True, xband: int = 0) -> FitResult:
     """Maximum-likelihood estimate of theta with every l(theta) evaluated on the GPU.
 
     locs (2n doubles, x then y) and z (n doubles) should be device tensors so
@@ -146,7 +146,8 @@ def fit(locs, z, n: int, precision="fp64", start=(0.5, 0.05, 0.5), lower=(0.01, 
 
     def loglik(theta):
         try:
-            ll, _ = egs.egs_loglik_ex(locs, z, theta, n, precision, tile=tile, band=band, stream=stream)
+            ll, _ = egs.egs_loglik_ex(locs, z, theta, n, precision, tile=tile, band=band, stream=stream,
+                                      xband=xband if precision == "fp32" else 0)
             return ll
         except (egs.NotPositiveDefinite, egs.MixedInaccurate):
             if precision == "fp64" or not fallback_fp64:

@@ -90,3 +90,36 @@ def test_ozaki_gemm_exact_on_small_integers():
     C = torch.empty((256, 64), dtype=torch.float64, device="cuda")
     egs.egs_ozaki_gemm_test(torch.as_tensor(a).cuda(), torch.as_tensor(b).cuda(), C)
     assert np.array_equal(C.cpu().numpy(), a @ b.T)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_withheld_stage_times_out_and_the_context_stays_usable(prec):
+    """Failure detection of the tensor-core pipeline: one ring stage is never
+    loaded, so the MMA warp's bounded wait for it runs out (2 s), the kernel
+    unwinds (its in-flight loads land, TMEM is freed) and the call returns
+    EGS_ERR_TIMEOUT; the next call on the same context gives the right
+    product."""
+    import torch
+    import paper_1708_02835_gb300 as egs
+    M, N, K = 256, 512, 512
+    rng = np.random.default_rng(7)
+    a = _tf32_exact(rng, (M, K))
+    b = _tf32_exact(rng, (N, K))
+    if prec == "bf16":
+        A = torch.as_tensor(a).to(torch.bfloat16).cuda()
+        B = torch.as_tensor(b).to(torch.bfloat16).cuda()
+        a64 = A.float().cpu().numpy().astype(np.float64)
+        b64 = B.float().cpu().numpy().astype(np.float64)
+    else:
+        A = torch.as_tensor(a).cuda()
+        B = torch.as_tensor(b).cuda()
+        a64, b64 = a.astype(np.float64), b.astype(np.float64)
+    C = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    with pytest.raises(egs.EgsError) as e:
+        egs.egs_tc_gemm_test_withhold(A, B, C, prec, withhold_stage=3)
+    assert e.value.status == egs.EGS_ERR_TIMEOUT
+    C2 = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    egs.egs_tc_gemm_test(A, B, C2, prec)
+    got = C2.cpu().numpy().astype(np.float64)
+    ref = a64 @ b64.T
+    assert np.all(np.abs(got - ref) <= 2.0 ** -16 * (np.abs(a64) @ np.abs(b64).T))

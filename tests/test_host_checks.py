@@ -105,3 +105,11 @@ def test_solves_reject_host_pointers():
     assert st == egs.EGS_ERR_ARG and "device" in msg
     st, msg = _status(egs.egs_matern_tiles, np.zeros(128), 64, GOOD, 64, tiles)
     assert st == egs.EGS_ERR_ARG and "device" in msg
+
+
+def test_withheld_stage_must_be_a_stage():
+    a = np.zeros((128, 64), dtype=np.float32)
+    b = np.zeros((256, 64), dtype=np.float32)
+    c = np.zeros((128, 256), dtype=np.float32)
+    st, msg = _status(egs.egs_tc_gemm_test_withhold, a, b, c, "tf32", -1)
+    assert st == egs.EGS_ERR_ARG and "withhold" in msg
