@@ -406,7 +406,7 @@ egs_status egs_matern_tiles(const double *locs, int64_t n, const double theta[3]
         double *f64 = (double *)tiles;
         float *f32 = (float *)(f64 + Tiles::f64_tiles(g.T, band) * g.tile_elems());
         const Tiles tl{f64, f32, g.b, g.T, band};
-        e = launch_matern_tiles(locs, locs + n, n, tl, P, nullptr, s, nullptr, tab);
+        e = launch_matern_tiles(locs, locs + n, n, tl, P, s, nullptr, tab);
     }
     dev_free(A, tab, tab_bytes, s);
     if (e != cudaSuccess) return cuda_error(e, "egs_matern_tiles launch");

@@ -170,14 +170,13 @@ size_t potrf_diag_scratch_words(int b);
 cudaError_t launch_trsv_tiles_f64(const double *tiles, const TileGeom &g, double *zpad, double *partials,
                                   DevStatus *st, cudaStream_t s, KernelTimer *kt = nullptr);
 
-// Sigma(theta) into any Tiles storage (+ optional dense FP64 copy sig).  For
+// Sigma(theta) into any Tiles storage.  For
 // a mixed layout with the Euclidean distance the off-band tiles are evaluated
 // in double-float arithmetic (matern_df.cuh); tab must then hold
 // EGS_MT_SCRATCH_DOUBLES doubles (the general-nu polynomials and their
 // float-pair split).
 cudaError_t launch_matern_tiles(const double *X, const double *Y, int64_t n, const Tiles &tl,
-                                const egs_matern_params &P, double *sig, cudaStream_t s, KernelTimer *kt,
-                                double *tab = nullptr);
+                                const egs_matern_params &P, cudaStream_t s, KernelTimer *kt, double *tab = nullptr);
 
 // The double-float evaluation applies to these parameters (Euclidean
 // distance; a general nu needs the polynomial table); fills D.

@@ -33,16 +33,14 @@ __device__ __forceinline__ void tile_decode(int64_t t, int &i, int &j)
 }
 
 // Writes tile blockIdx.x (lower-tile order) of Sigma into tl: as double when
-// the tile is FP64 in tl, else rounded to float.  If sig is not NULL the
-// double values are also written to sig in the dense lower-tile layout (the
-// FP64 copy the mixed-precision refinement multiplies with).
+// the tile is FP64 in tl, else rounded to float.
 // tab: the local polynomials of a general nu (built by k_matern_table before
 // this launch), staged in shared memory; NULL for the closed forms.
 // band_only: blockIdx.x enumerates only the FP64 band tiles of a mixed
 // layout, as i * band + (i - j) (slots with j < 0 exit at once).
 __global__ void __launch_bounds__(256)
 k_matern_tiles(const double *__restrict__ X, const double *__restrict__ Y, int64_t n, Tiles tl,
-               const __grid_constant__ egs_matern_params Pg, double *__restrict__ sig, const double *__restrict__ tab,
+               const __grid_constant__ egs_matern_params Pg, const double *__restrict__ tab,
                int band_only)
 {
     const int b = tl.b;
@@ -74,7 +72,6 @@ k_matern_tiles(const double *__restrict__ X, const double *__restrict__ Y, int64
     const bool is64 = tl.is64(ti, tj);
     double *t64 = is64 ? tl.t64(ti, tj) : nullptr;
     float *t32 = is64 ? nullptr : tl.t32(ti, tj);
-    double *tsig = sig ? sig + (size_t)tile_linear(ti, tj) * (size_t)b * (size_t)b : nullptr;
     for (int rr = 0; rr < 16; ++rr) {
         const int r = sr * 64 + ty + 4 * rr;
         const int64_t gi = (int64_t)ti * b + r;
@@ -89,7 +86,6 @@ k_matern_tiles(const double *__restrict__ X, const double *__restrict__ Y, int64
         const size_t off = (size_t)r * b + sc * 64 + tx;
         if (is64) t64[off] = v;
         else t32[off] = (float)v;
-        if (tsig) tsig[off] = v;
     }
 }
 
@@ -105,14 +101,14 @@ __device__ __forceinline__ float4 split_point(double x, double y)
 // general nu, ctab.  grid = (off-band tiles in their storage order, b / 64);
 // a CTA covers 64 columns and all b rows of one tile: thread (ty, tx) writes
 // column tx of rows ty, ty + 4, ... (coalesced 128-byte FP32 stores per warp
-// and row; 256-byte FP64 stores into the copy sig when it is not NULL).
+// and row).
 // Off-band tiles hold no diagonal entry; entries in padding rows or columns
 // are 0.
 template <bool GENERAL>
 __global__ void __launch_bounds__(256)
 k_matern_tiles_df(const double *__restrict__ X, const double *__restrict__ Y, int64_t n, Tiles tl,
                   const __grid_constant__ egs_matern_df Dg, const __grid_constant__ egs_matern_params Pg,
-                  const float2 *__restrict__ ctab_g, double *__restrict__ sig)
+                  const float2 *__restrict__ ctab_g)
 {
     __shared__ float etab[2 * EGS_DF_TAB];
     __shared__ float2 ctab[GENERAL ? EGS_MT_DOUBLES : 1];
@@ -136,13 +132,11 @@ k_matern_tiles_df(const double *__restrict__ X, const double *__restrict__ Y, in
     const float4 pj = gj < n ? split_point(X[gj], Y[gj]) : make_float4(0.f, 0.f, 0.f, 0.f);
     const int64_t rlim = n - (int64_t)ti * b;  // rows r < rlim are real locations
     float *t32 = tl.t32(ti, tj) + c;
-    double *tsig = sig ? sig + (size_t)tile_linear(ti, tj) * tl.bb() + c : nullptr;
     for (int r = ty; r < b; r += 4) {
         df::F2 v{0.0f, 0.0f};
         if (r < rlim && gj < n) v = df::matern_entry_df<GENERAL>(C, rows[r], pj, etab, ctab, &Pg);
         const size_t off = (size_t)r * b;
         t32[off] = v.h;
-        if (tsig) tsig[off] = df::to_double(v);
     }
 }
 
@@ -185,7 +179,7 @@ cudaError_t launch_matern_table(const egs_matern_params &P, double *tab, cudaStr
 }
 
 cudaError_t launch_matern_tiles(const double *X, const double *Y, int64_t n, const Tiles &tl,
-                                const egs_matern_params &P, double *sig, cudaStream_t s, KernelTimer *kt, double *tab)
+                                const egs_matern_params &P, cudaStream_t s, KernelTimer *kt, double *tab)
 {
     const double *t = nullptr;
     if (tab && P.kind == EGS_MATERN_GENERAL) {
@@ -196,22 +190,22 @@ cudaError_t launch_matern_tiles(const double *X, const double *Y, int64_t n, con
     const unsigned nsub = (unsigned)((tl.b / 64) * (tl.b / 64));
     egs_matern_df D;
     if (!tl.dense() && matern_df_applies(P, tab != nullptr, &D)) {
-        // mixed layout: FP64 band tiles directly, the FP32 off-band tiles (and
-        // their part of the copy) in double-float
+        // mixed layout: FP64 band tiles directly, the FP32 off-band tiles in
+        // double-float
         EGS_LAUNCH(kt, KC_GEN, s,
-                   k_matern_tiles<<<dim3((unsigned)(tl.T * tl.band), nsub), 256, 0, s>>>(X, Y, n, tl, P, sig, t, 1));
+                   k_matern_tiles<<<dim3((unsigned)(tl.T * tl.band), nsub), 256, 0, s>>>(X, Y, n, tl, P, t, 1));
         const dim3 grid((unsigned)Tiles::f32_tiles(tl.T, tl.band), (unsigned)(tl.b / 64));
         if (P.kind == EGS_MATERN_GENERAL) {
             float2 *ctab = matern_df_table(tab);
             EGS_LAUNCH(kt, KC_GEN, s, k_split_table<<<(EGS_MT_DOUBLES + 255) / 256, 256, 0, s>>>(tab, ctab));
-            EGS_LAUNCH(kt, KC_GEN, s, k_matern_tiles_df<true><<<grid, 256, 0, s>>>(X, Y, n, tl, D, P, ctab, sig));
+            EGS_LAUNCH(kt, KC_GEN, s, k_matern_tiles_df<true><<<grid, 256, 0, s>>>(X, Y, n, tl, D, P, ctab));
         } else {
-            EGS_LAUNCH(kt, KC_GEN, s, k_matern_tiles_df<false><<<grid, 256, 0, s>>>(X, Y, n, tl, D, P, nullptr, sig));
+            EGS_LAUNCH(kt, KC_GEN, s, k_matern_tiles_df<false><<<grid, 256, 0, s>>>(X, Y, n, tl, D, P, nullptr));
         }
         return cudaGetLastError();
     }
     const size_t ntiles = (size_t)tl.T * (tl.T + 1) / 2;
-    EGS_LAUNCH(kt, KC_GEN, s, k_matern_tiles<<<dim3((unsigned)ntiles, nsub), 256, 0, s>>>(X, Y, n, tl, P, sig, t, 0));
+    EGS_LAUNCH(kt, KC_GEN, s, k_matern_tiles<<<dim3((unsigned)ntiles, nsub), 256, 0, s>>>(X, Y, n, tl, P, t, 0));
     return cudaGetLastError();
 }
 
@@ -220,7 +214,7 @@ cudaError_t launch_matern_tiles_f64(const double *X, const double *Y, const Tile
                                     double *tab)
 {
     const Tiles tl{tiles, nullptr, g.b, g.T, g.T};
-    return launch_matern_tiles(X, Y, g.n, tl, P, nullptr, s, kt, tab);
+    return launch_matern_tiles(X, Y, g.n, tl, P, s, kt, tab);
 }
 
 }  // namespace egs

@@ -5,8 +5,8 @@
 // operations 64 times faster than FP64 ones, so ~130 single-precision
 // operations per entry cost a fraction of the ~28 FP64 operations of the
 // direct evaluation; the result is accurate to about 1e-14 relative, enough
-// for the mixed precisions (FP32 storage of the off-band tiles, the FP64
-// copy of Sigma that the refinement residual multiplies).
+// for the mixed precisions (FP32 storage of the off-band tiles, and the
+// refinement residual, which regenerates Sigma while it multiplies).
 //
 // Building blocks are the error-free transformations of Knuth (TwoSum),
 // Dekker (FastTwoSum; TwoProduct, here by one fused multiply-add), and the
@@ -224,25 +224,6 @@ __device__ __forceinline__ F2 matern_entry_df(const Consts &C, const float4 &pi,
     const double v = matern_eval(P, (double)x.h + (double)x.l, nullptr);
     const float vh = __double2float_rn(v);
     return {vh, __double2float_rn(v - (double)vh)};
-}
-
-// h + l as a double, the conversions done with integer operations (exact for
-// normal floats; zero and subnormal parts give 0, below 2^-126 theta1-scale
-// values that do not matter at double precision of the sum) and one FP64 add.
-__device__ __forceinline__ double f32_bits_to_f64(float f)
-{
-    const unsigned b = __float_as_uint(f);
-    const unsigned mag = b & 0x7FFFFFFFu;
-    if (mag < 0x00800000u) return 0.0;  // zero or subnormal
-    if (mag >= 0x7F800000u) return (double)f;  // infinity or NaN
-    const unsigned hi = (b & 0x80000000u) | ((mag >> 3) + (896u << 20));
-    const unsigned lo = mag << 29;
-    return __hiloint2double((int)hi, (int)lo);
-}
-
-__device__ __forceinline__ double to_double(F2 v)
-{
-    return f32_bits_to_f64(v.h) + f32_bits_to_f64(v.l);
 }
 
 }  // namespace df

@@ -808,7 +808,7 @@ cudaError_t run_loglik_mixed(const double *X, const double *Y, const double *z, 
     const int64_t npad = (int64_t)T * b;
     const unsigned vb = (unsigned)((npad + 255) / 256);
     if (ev) cudaEventRecord(ev[0], s);
-    cudaError_t e = launch_matern_tiles(X, Y, n, tl, P, nullptr, s, kt, mb.mtab);
+    cudaError_t e = launch_matern_tiles(X, Y, n, tl, P, s, kt, mb.mtab);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
     // update maps (FP32 mode: split FP16 over the panel buffers) and, in the
