@@ -160,7 +160,8 @@ egs_status egs_trace_last(egs_trace_rec *out, int64_t cap, int64_t *count);
  * egs_set_allocator - the device memory of the library's calls (per-call
  * workspaces, serving slots and fields, batch plans) from the caller's
  * allocator, for example a framework's caching allocator, instead of
- * cudaMallocAsync / cudaFreeAsync on the call's stream.
+ * cudaMallocAsync / cudaFreeAsync on the call's stream.  The paper has no
+ * counterpart: this is the boundary's memory-management convention.
  *   alloc(bytes, stream, ctx)   returns device memory of at least bytes
  *                               bytes, usable in stream order on stream
  *                               (a cudaStream_t), aligned to 256 bytes; NULL
